@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Throughput of pROST's per-frame update (arXiv:1302.2073) on GB300.
+
+One step = one frame through the whole hot path: n_cg residual/gradient
+passes with the CG steps, the final pass with the rank-one SVD and geodesic
+angle, and the update/label pass with the folded Cholesky-QR (n_cg + 2 kernel
+launches).  Workload: the 640x480 RGB, k = 10, uint8 synthetic stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (under torchrun) every rank runs its own independent stream
+(replicas; the method has no data-parallel exchange), the slowest rank's time
+counts and rank 0 prints one JSON line.  --impl reference times the FP64 CPU
+oracle on the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "640x480 k=10 frames/s & achieved GB/s vs peak; batched BF16 vs FP32 at stated err"
+UNIT = "frames/s"
+WORKLOAD = "rgb640x480_k10"
+FLUSH_BYTES = 256 << 20  # larger than the 126.5 MB L2
+PROFILE = os.path.join(ROOT, "profiles", "k_pass_rgb640x480_k10.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1302_2073_gb300", "csrc", "prost_kernels.cuh")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0,
+                    help="budget of the oracle CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---- distributed plumbing (replicas) -----------------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, torch, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self, torch=None):
+        if self.pg:
+            if torch is not None and torch.cuda.is_available():
+                self.pg.barrier(device_ids=[self.local])
+            else:
+                self.pg.barrier()
+
+    def max(self, torch, v: float) -> float:
+        if not self.pg:
+            return v
+        dev = "cuda" if torch.cuda.is_available() and self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---- clocks during the timed region ------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the CG pass from the committed ncu summary, if
+    the kernel source is unchanged since the capture (else None)."""
+    try:
+        text = open(PROFILE).read()
+        src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---- the oracle on the host cores --------------------------------------------
+
+def oracle_sample(name, budget_s, min_frames=2, max_frames=1000):
+    """Frames/s of the FP64 oracle on the first frames of the workload."""
+    import oracle
+    import synth
+    vid, wp = synth.make_workload(name)
+    prm = oracle.params(**wp)
+    st = oracle.initial_state(synth.random_orthonormal(vid.m, vid.k, 1), vid.P)
+    frames = []
+    t_total, n = 0.0, 0
+    while n < max_frames and (n < min_frames or t_total < budget_s):
+        f, _ = vid.frame(n % vid.n_frames)
+        t0 = time.perf_counter()
+        oracle.frame_step(prm, st, f, want_residual=False)
+        t_total += time.perf_counter() - t0
+        frames.append(n)
+        n += 1
+    return n / t_total, n, t_total
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return 0
+    budget = min(180.0, max(20.0, 1.0 * (args.steps + args.warmup)))
+    fps, n, secs = oracle_sample(args.workload, budget, min_frames=max(2, min(args.steps, 3)),
+                                 max_frames=args.steps)
+    import synth
+    vid, wp = synth.make_workload(args.workload)
+    sample = (f"first {n} frames of the {args.workload} stream through the single-threaded "
+              f"FP64 C oracle ({secs:.1f} s)")
+    out = {"metric": METRIC, "value": fps, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+           "steps": n, "warmup": 0, "ms_per_step": 1000.0 / fps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": _config(args, vid, wp, n),
+           "cpu_baseline": {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": fps, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def _config(args, vid, wp, steps):
+    return {"workload": args.workload, "width": vid.width, "height": vid.height,
+            "channels": vid.channels, "k": vid.k, "n_cg": wp["n_cg"], "frame_dtype": vid.dtype,
+            "u_dtype": "f32", "frames_timed": steps,
+            "l2": "flushed by a 256 MiB write before every timed frame; per-frame CUDA events",
+            "replicas": args.gpus}
+
+
+# ---- our implementation ------------------------------------------------------
+
+def run_ours(args, dist):
+    import torch
+
+    import synth
+    import paper_1302_2073_gb300 as pg
+
+    assert torch.cuda.is_available(), "bench.py needs a CUDA GPU"
+    torch.cuda.set_device(dist.local)
+    dist.init(torch, "nccl")
+    dev = torch.device("cuda", dist.local)
+    stream = torch.cuda.Stream(device=dev)
+
+    vid, wp = synth.make_workload(args.workload, seed=synth.WORKLOADS[args.workload]["video"]["seed"] + dist.rank)
+    K, W = args.steps, args.warmup
+    n_frames = min(K + W, vid.n_frames)
+    host = vid.frames(0, n_frames)
+    frames = torch.from_numpy(host).to(dev)  # resident in HBM before the timed region
+    pinned = torch.from_numpy(host).pin_memory()
+    masks = torch.empty((2, vid.P), dtype=torch.uint8, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    n_cg = wp["n_cg"]
+    launches_per_step = n_cg + 2
+
+    h = pg.prost_init(pg.make_params(**wp, seed=dist.rank + 1), stream=stream)
+    try:
+        pg.prost_set_timing(h, True)
+        with torch.cuda.stream(stream):
+            for t in range(W):
+                pg.prost_step(h, frames[t % n_frames], masks[t % 2])
+        torch.cuda.synchronize()
+        dist.barrier(torch)
+        torch.cuda.synchronize()
+
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        kern = []
+        clocks = ClockSampler(dist.local)
+        clocks.start()
+        with torch.cuda.stream(stream):
+            for t in range(K):
+                flush.fill_(t & 0xFF)
+                ev0[t].record(stream)
+                pg.prost_step(h, frames[(W + t) % n_frames], masks[t % 2])
+                ev1[t].record(stream)
+                kern.append(pg.prost_get_timing(h))  # waits for this frame
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        rc = pg.prost_sync(h)
+        assert rc == pg.PROST_OK, rc
+        step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        total_ms = dist.max(torch, sum(step_ms))
+        dist.barrier(torch)
+
+        # end to end through the C ABI with host buffers (pinned frame in, mask out)
+        hmask = torch.empty(vid.P, dtype=torch.uint8).pin_memory()
+        pg.prost_set_timing(h, False)
+        e2e_s = 0.0
+        for t in range(K):
+            with torch.cuda.stream(stream):
+                flush.fill_(t & 0xFF)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            st = pg.prost_step(h, pinned[(W + t) % n_frames].numpy(), hmask.numpy())
+            e2e_s += time.perf_counter() - t0
+            assert st == pg.PROST_OK
+        e2e_s = dist.max(torch, e2e_s)
+    finally:
+        pg.prost_destroy(h)
+
+    n = dist.world
+    ms_per_step = total_ms / K
+    value = n * K / (total_ms / 1000.0)
+    e2e_value = n * K / e2e_s
+
+    # roofline of the dominant kernel: the CG pass (n_cg of the launches)
+    kern = np.array(kern)  # K x (n_cg + 2)
+    pass_ms = float(kern[:, :n_cg].mean()) if n_cg > 0 else float(kern[:, 0].mean())
+    m, P, k = vid.m, vid.P, vid.k
+    sx = 1 if vid.dtype == "u8" else 4
+    pass_bytes = m * k * 4 + m * sx + P  # U read, frame read, label read
+    peak, peak_src = measured_peak_hbm()
+    achieved = pass_bytes / (pass_ms * 1e-3) / 1e9
+    frame_bytes = (n_cg + 2) * m * k * 4 + m * k * 4 + (n_cg + 2) * (m * sx + P) + P
+    share = {"cg_pass": float(kern[:, :n_cg].sum() / kern.sum()),
+             "final_pass": float(kern[:, n_cg].sum() / kern.sum()),
+             "update_pass": float(kern[:, n_cg + 1].sum() / kern.sum())}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n, "steps": K, "warmup": W,
+           "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": _config(args, vid, wp, K),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "traffic": profiled_traffic(),
+                        "kernel": f"k_pass<{k},u8,M> (CG pass)", "bytes_per_launch": pass_bytes,
+                        "launch_ms": pass_ms, "peak_source": f"{peak_src} hbm_gbs"},
+           "frame": {"algorithmic_bytes": frame_bytes,
+                     "effective_gbs": frame_bytes / (ms_per_step * 1e-3) / 1e9,
+                     "frac_of_hbm_peak": frame_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
+                     "pixels_per_s": value * P, "kernel_time_share": share},
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": m * sx,
+                   "d2h_bytes_per_step": P + 4},
+           "gpu_launches": K * launches_per_step,
+           "clocks": clk}
+
+    if dist.rank == 0 and n == 1 and not args.no_cpu_baseline:
+        fps, nf, secs = oracle_sample(args.workload, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",
+                               "sample": f"first {nf} frames of the same stream, single-threaded "
+                                         f"FP64 C oracle, {secs:.1f} s"}
+    if dist.rank == 0:
+        print(json.dumps(out), flush=True)
+    dist.close()
+    return 0
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    if args.impl == "reference":
+        return run_reference(args, dist)
+    return run_ours(args, dist)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,207 @@
+/*
+ * prost.h -- C ABI of the GB300 implementation of pROST's per-frame update
+ * (Seidel, Hage, Kleinsteuber, arXiv:1302.2073).
+ *
+ * One handle tracks one video stream: a subspace U (m x k, orthonormal
+ * columns, Eq. stiefeldef), the coefficients y of the last frame and the
+ * labels of the last frame (which become the weights of the next, Eq.
+ * pixelweighting).  prost_step() runs Steps 1-3 of Section 3.3 for one frame
+ * on the GPU:
+ *   Step 1  y = argmin_y h_{mu,w}(x - U y)            (Eq. onlinestep1)
+ *           by n_cg nonlinear conjugate-gradient iterations (Polak-Ribiere+,
+ *           majorise-minimise line step), warm-started at the previous y;
+ *   Step 2  one geodesic step on the Grassmannian along the projected
+ *           rank-one gradient pi(eta) y^T (Eqs. gproject, svd, geodesic) with
+ *           t = max(exp(-tau i) t_init, t_min) (Section 3.4);
+ *   Step 3  pixel labels  F_q = [max_c |x_{c,q} - u_{c,q}^T y| >= delta]
+ *           (Section 3.4) and weights w_q = omega if F_q else 1 for the next
+ *           frame (Eq. pixelweighting).
+ * The cost is the weighted smoothed l_p norm of the residual,
+ *   h_{mu,w}(x - U y) = sum_e w_e ((x_e - u_e^T y)^2 + mu)^(p/2)
+ * (Eqs. smoothlpnorm, weightedLPnorm, spcacost).  After each frame the
+ * representative U is re-orthonormalised by Cholesky-QR (U <- U R^{-1},
+ * y <- R y); this is not in the paper and is the identity in exact arithmetic.
+ *
+ * Layouts.  A frame is channel-planar: channels planes of height x width
+ * pixels, row-major, so entry e = c*P + q for pixel q of channel c (the colour
+ * stacking x = [x_R; x_G; x_B] of Section 3.4), m = channels*P.  Frames are
+ * uint8 or float32 (prost_params.frame_dtype); the entry used by the method is
+ * x_e = in_scale * frame_e - in_offset.  Subspaces cross the ABI as float32
+ * m x k row-major (row e is u_e^T); y as k doubles.  Labels/masks are P bytes,
+ * 1 = foreground.
+ *
+ * Streams and memory.  prost_init() takes a cudaStream_t (as void*; NULL is
+ * the legacy default stream) on which every later call is ordered.  The
+ * library allocates and owns its device state (released by prost_destroy());
+ * the caller owns every buffer it passes.  Calls with on_device = 0 take host
+ * pointers, copy through the stream and return after the stream has
+ * synchronised.  Calls with on_device = 1 take device pointers of the current
+ * device and only enqueue work; errors found on the device (a frame with a
+ * non-finite entry, a Gram matrix that is not positive definite) are then
+ * reported by prost_sync() or prost_get_stats().  A handle is not thread safe.
+ *
+ * Errors.  Every int-returning call returns PROST_OK (0) or a negative code
+ * below; prost_strerror() names it and prost_last_error() gives the detail of
+ * the last failure on a handle.  A call that fails with PROST_EINVAL changes
+ * nothing.
+ */
+#ifndef PROST_H
+#define PROST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PROST_OK 0
+#define PROST_EINVAL (-1)     /* bad argument or parameter; nothing changed */
+#define PROST_ENOMEM (-2)     /* device or host allocation failed */
+#define PROST_ECUDA (-3)      /* a CUDA call failed; see prost_last_error() */
+#define PROST_EBADFRAME (-4)  /* frame had a non-finite entry; the frame was skipped,
+                                 state (U, y, labels, frame counter) unchanged */
+#define PROST_ETIMEOUT (-5)   /* a bounded device-side wait gave up */
+#define PROST_ENOTSPD (-6)    /* Gram matrix of the subspace not positive definite;
+                                 the previous re-orthonormalisation is kept */
+
+#define PROST_U8 0   /* frame entries uint8 */
+#define PROST_F32 1  /* frame entries float32; subspace storage float32 */
+
+#define PROST_MASK_POST_UPDATE 0 /* Step 3 uses the subspace after Step 2 (default) */
+#define PROST_MASK_PRE_UPDATE 1  /* Step 3 uses the subspace before Step 2 */
+
+#define PROST_MAX_K 16
+#define PROST_MAX_CG 32
+
+typedef struct prost_handle prost_handle;
+
+typedef struct prost_params {
+    int32_t width, height, channels; /* frame size; m = channels*width*height, channels <= 4 */
+    int32_t k;                       /* subspace dimension, 1 <= k <= min(m, PROST_MAX_K) */
+    double p;                        /* l_p exponent, 0 < p <= 2 (Eq. smoothlpnorm; p >= 1 as in Section 5.3) */
+    double mu;                       /* smoothing, mu > 0; 0 selects delta^2 (1 - p) (Eq. opt_mu2, needs p < 1) */
+    double delta;                    /* label threshold, delta > 0 */
+    double omega;                    /* weight of pixels labelled foreground, 0 <= omega <= 1 */
+    double t_init, t_min;            /* step sizes, > 0 (Section 3.4) */
+    int32_t i_init;                  /* frames of the initialisation phase, >= 1: tau = ln(t_init/t_min)/i_init */
+    int32_t n_cg;                    /* CG iterations per frame, 0 <= n_cg <= PROST_MAX_CG (paper: 5) */
+    double in_scale, in_offset;      /* x = in_scale * frame - in_offset */
+    int32_t frame_dtype;             /* PROST_U8 or PROST_F32 */
+    int32_t u_dtype;                 /* PROST_F32 */
+    int32_t mask_from;               /* PROST_MASK_POST_UPDATE or PROST_MASK_PRE_UPDATE */
+    int32_t reserved;                /* must be 0 */
+    uint64_t seed;                   /* seed of the random initial subspace (Section 3.4) */
+} prost_params;
+
+typedef struct prost_stats {
+    int64_t frames;                  /* frames processed (the step counter i of the next frame) */
+    int64_t bad_frames;              /* frames skipped as PROST_EBADFRAME since init */
+    int32_t n_cg;                    /* CG iterations of the last frame */
+    int32_t status;                  /* status of the last frame (PROST_OK, PROST_EBADFRAME, ...) */
+    double cost[PROST_MAX_CG + 1];   /* h_{mu,w}(x - U y_j) at each CG iterate j = 0..n_cg */
+    double gnorm[PROST_MAX_CG + 1];  /* |grad_y h| at each CG iterate */
+    double alpha[PROST_MAX_CG];      /* line step of CG iteration j */
+    double beta[PROST_MAX_CG + 1];   /* PR+ coefficient at iterate j (beta[0] = 0; beta[n_cg] unused by Step 1) */
+    double pi_norm;                  /* |pi(eta)| at the final y (Eq. gproject) */
+    double y_norm;                   /* |y| */
+    double sigma;                    /* sigma_1 = |pi(eta)| |y| (Eq. svd) */
+    double t;                        /* step size of the frame */
+    double theta;                    /* geodesic angle sigma_1 t; 0 when the step was skipped */
+    int32_t updated;                 /* 0 when |y| = 0 or |pi(eta)| = 0 skipped Step 2 */
+    int32_t pad0;
+    int64_t n_foreground;            /* pixels labelled foreground in the last frame */
+    double orth_err;                 /* max |U^T U - I| of the stored subspace before its
+                                        re-orthonormalisation at the end of the last frame */
+} prost_stats;
+
+/* Sizes of the device state of a handle with these parameters (bytes, device
+ * memory).  Returns PROST_EINVAL for bad parameters. */
+int prost_state_bytes(const prost_params *prm, size_t *bytes);
+
+/* Create a stream tracker.  Validates prm, allocates the device state, draws
+ * the initial subspace as the orthonormal factor of a seeded Gaussian m x k
+ * matrix (Section 3.4, "Initialization"), sets y = 0, all labels background
+ * and the frame counter to 0.  stream: cudaStream_t as void* (NULL = default
+ * stream).  On success *out owns the state until prost_destroy(). */
+int prost_init(const prost_params *prm, void *stream, prost_handle **out);
+
+/* Process one frame (Steps 1-3).  frame: m entries of prm.frame_dtype,
+ * channel-planar.  mask_out (nullable): P bytes, this frame's labels.
+ * background_out (nullable): m floats, U y + in_offset with the subspace the
+ * labels used (the reconstruction in the units of in_scale*frame).
+ * on_device = 1: all three are device pointers and the call only enqueues the
+ * work on the handle's stream (returns PROST_OK; device-detected errors are
+ * reported by prost_sync()).  on_device = 0: all three are host pointers; the
+ * frame is copied to the device, the outputs back, and the call returns the
+ * frame's status after the stream synchronised.  A frame with a non-finite
+ * entry (float32 frames only) leaves the state unchanged and its outputs
+ * unwritten (status PROST_EBADFRAME). */
+int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_out,
+               float *background_out);
+
+/* Synchronise the handle's stream.  Returns PROST_EBADFRAME if a frame was
+ * skipped since the previous prost_sync(), PROST_ENOTSPD / PROST_ETIMEOUT if
+ * one of those was raised, else PROST_OK, and clears these flags. */
+int prost_sync(prost_handle *h);
+
+/* Copy out the current subspace (the re-orthonormalised representative,
+ * m x k row-major float32) and y (k doubles).  Either pointer may be NULL.
+ * on_device selects device or host pointers; synchronises when on_device = 0. */
+int prost_get_subspace(prost_handle *h, float *U_out, double *y_out, int on_device);
+
+/* Replace the subspace and y (used to restart a stream or to hand the
+ * tracker a known state).  U: m x k row-major float32 with linearly
+ * independent columns (re-orthonormalised by Cholesky-QR on the device, y
+ * transformed so that U y is kept); y: k doubles or NULL for y = 0. */
+int prost_set_subspace(prost_handle *h, const float *U, const double *y, int on_device);
+
+/* Replace the previous frame's labels (P bytes, nonzero = foreground); they
+ * set the weights of the next frame.  NULL clears them (all weights 1). */
+int prost_set_labels(prost_handle *h, const uint8_t *labels, int on_device);
+
+/* Set the frame counter i used by the step-size rule of the next frame. */
+int prost_set_frame_index(prost_handle *h, int64_t i);
+
+/* Statistics of the last frame (synchronises the stream). */
+int prost_get_stats(prost_handle *h, prost_stats *out);
+
+/* Checkpoint.  prost_get_state() with buf = NULL stores the needed size in
+ * *len; otherwise writes the complete state (parameters, subspace, y,
+ * re-orthonormalisation factors, labels, counters) into buf (host memory,
+ * *len bytes available) and sets *len to the bytes written.  A handle
+ * restored by prost_set_state() from that buffer continues bit-identically.
+ * prost_set_state() fails with PROST_EINVAL when the buffer is malformed or
+ * was made with other sizes, k, dtypes or step parameters. */
+int prost_get_state(prost_handle *h, void *buf, size_t *len);
+int prost_set_state(prost_handle *h, const void *buf, size_t len);
+
+/* Tracing.  enable = 1 makes every later prost_step() record a CUDA event on
+ * the handle's stream before its first kernel and after each of its n_cg + 2
+ * kernel launches; enable = 0 stops it.  Costs one event record per launch. */
+int prost_set_timing(prost_handle *h, int enable);
+
+/* Device time between the events of the last traced prost_step(): ms[j] for
+ * launch j (j < n_cg: CG passes that also sum the line-step terms; j = n_cg:
+ * the final pass; j = n_cg + 1: the update/label pass).  ms holds at least
+ * n_cg + 2 floats; *n gets n_cg + 2.  Synchronises on the last event.
+ * PROST_EINVAL if timing is off or no traced frame ran yet. */
+int prost_get_timing(prost_handle *h, float *ms, int *n);
+
+/* Release the device state (synchronises the stream first).  NULL is a no-op. */
+void prost_destroy(prost_handle *h);
+
+/* Name of an error code (static string). */
+const char *prost_strerror(int code);
+
+/* Detail of the last error on this handle (static until the next call on
+ * the handle); "" if none.  h = NULL gives the last error of prost_init(). */
+const char *prost_last_error(const prost_handle *h);
+
+/* ABI version: 100 * major + minor. */
+int prost_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PROST_H */

@@ -1,0 +1,5 @@
+"""pROST's per-frame update (arXiv:1302.2073) on GB300: CUDA kernels for
+sm_103a behind the C ABI of include/prost.h, with a ctypes binding."""
+
+from .prost import *  # noqa: F401,F403
+from .prost import ProstError, lib, make_params, header_functions  # noqa: F401

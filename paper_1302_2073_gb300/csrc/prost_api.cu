@@ -1,0 +1,600 @@
+// Host side of the C ABI declared in include/prost.h: argument checking,
+// device state, the launch sequence of one frame, copies and checkpoints.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <string>
+
+#include "prost.h"
+#include "prost_device.h"
+
+using namespace prost;
+
+struct prost_handle {
+    prost_params prm;
+    DevParams dp;
+    const KernelOps *ops;
+    cudaStream_t stream;
+    int device;
+    int num_sms;
+    int grid_pass_m, grid_pass, grid_ustep, grid_gram;
+    float *U;              // stored subspace (k x C x Pp floats)
+    uint8_t *labels;       // previous labels (Pp bytes)
+    KState *ks;
+    float *partials;
+    unsigned int *counter;
+    void *frame_buf;       // staging of host frames
+    float *bg_buf;         // staging of the background for host outputs
+    float *u_buf;          // staging of subspaces crossing the ABI from/to host memory
+    int32_t *h_word;       // pinned scratch for small device -> host reads
+    size_t partial_floats;
+    int timing;            // record events around every kernel of prost_step()
+    int timed_frames;      // traced frames since timing was enabled
+    cudaEvent_t ev[CGMAX + 3];
+    std::string err;
+};
+
+namespace {
+
+std::string g_init_err;
+const KernelOps *g_ops[KMAX + 1];
+std::once_flag g_ops_once;
+
+void load_ops()
+{
+    std::call_once(g_ops_once, [] {
+        for (int i = 0; i <= KMAX; ++i) g_ops[i] = nullptr;
+        register_ops_k01_04(g_ops);
+        register_ops_k05_08(g_ops);
+        register_ops_k09_12(g_ops);
+        register_ops_k13_16(g_ops);
+    });
+}
+
+// restores the caller's current device on scope exit
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (dev >= 0 && dev != prev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+#define CK(h, call)                                                                   \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            (h)->err = std::string(#call) + ": " + cudaGetErrorString(e_);            \
+            return e_ == cudaErrorMemoryAllocation ? PROST_ENOMEM : PROST_ECUDA;      \
+        }                                                                             \
+    } while (0)
+
+int fail(prost_handle *h, int code, const std::string &msg)
+{
+    if (h) h->err = msg;
+    return code;
+}
+
+int64_t m_of(const prost_params &p) { return (int64_t)p.channels * p.width * p.height; }
+
+// parameter check; on success fills dp (except vec)
+int check_params(const prost_params *prm, DevParams *dp, std::string *why)
+{
+    if (!prm) { *why = "params is NULL"; return PROST_EINVAL; }
+    const prost_params &p = *prm;
+    if (p.width <= 0 || p.height <= 0) { *why = "width and height must be positive"; return PROST_EINVAL; }
+    if (p.channels < 1 || p.channels > 4) { *why = "channels must be 1..4"; return PROST_EINVAL; }
+    const int64_t P = (int64_t)p.width * p.height, m = m_of(p);
+    if (m > (int64_t)1 << 30) { *why = "frame too large (m > 2^30)"; return PROST_EINVAL; }
+    if (p.k < 1 || p.k > KMAX || (int64_t)p.k > m) { *why = "k must be in 1..min(m, 16)"; return PROST_EINVAL; }
+    if (!(p.p > 0.0 && p.p <= 2.0)) { *why = "p must be in (0, 2]"; return PROST_EINVAL; }
+    if (!(p.delta > 0.0) || !isfinite(p.delta)) { *why = "delta must be positive"; return PROST_EINVAL; }
+    double mu = p.mu;
+    if (mu == 0.0) mu = p.delta * p.delta * (1.0 - p.p);  // Eq. (opt_mu2)
+    if (!(mu > 0.0) || !isfinite(mu)) { *why = "mu must be positive (mu = 0 selects delta^2 (1-p), which needs p < 1)"; return PROST_EINVAL; }
+    if (!(p.omega >= 0.0 && p.omega <= 1.0)) { *why = "omega must be in [0, 1]"; return PROST_EINVAL; }
+    if (!(p.t_init > 0.0) || !(p.t_min > 0.0) || !isfinite(p.t_init) || !isfinite(p.t_min)) { *why = "t_init and t_min must be positive"; return PROST_EINVAL; }
+    if (p.i_init < 1) { *why = "i_init must be >= 1"; return PROST_EINVAL; }
+    if (p.n_cg < 0 || p.n_cg > CGMAX) { *why = "n_cg must be in 0..32"; return PROST_EINVAL; }
+    if (!isfinite(p.in_scale) || !isfinite(p.in_offset)) { *why = "in_scale and in_offset must be finite"; return PROST_EINVAL; }
+    if (p.frame_dtype != PROST_U8 && p.frame_dtype != PROST_F32) { *why = "frame_dtype must be PROST_U8 or PROST_F32"; return PROST_EINVAL; }
+    if (p.u_dtype != PROST_F32) { *why = "u_dtype must be PROST_F32"; return PROST_EINVAL; }
+    if (p.mask_from != PROST_MASK_POST_UPDATE && p.mask_from != PROST_MASK_PRE_UPDATE) { *why = "mask_from must be 0 or 1"; return PROST_EINVAL; }
+    if (p.reserved != 0) { *why = "reserved must be 0"; return PROST_EINVAL; }
+    if (dp) {
+        memset(dp, 0, sizeof(*dp));
+        dp->P = P;
+        dp->Pp = (P + 63) / 64 * 64;
+        dp->C = p.channels;
+        dp->k = p.k;
+        dp->n_cg = p.n_cg;
+        dp->mask_pre = p.mask_from == PROST_MASK_PRE_UPDATE;
+        dp->p = (float)p.p;
+        dp->mu = (float)mu;
+        dp->delta = (float)p.delta;
+        dp->omega = (float)p.omega;
+        dp->in_scale = (float)p.in_scale;
+        dp->in_offset = (float)p.in_offset;
+        dp->e = (float)(0.5 * p.p - 1.0);
+        dp->pd = p.p;
+        dp->t_init = p.t_init;
+        dp->t_min = p.t_min;
+        dp->tau = -log(p.t_min / p.t_init) / (double)p.i_init; // Section 3.4
+    }
+    return PROST_OK;
+}
+
+size_t frame_elem_bytes(const prost_params &p) { return p.frame_dtype == PROST_U8 ? 1 : 4; }
+
+// partial rows of the widest kernel: pass with M has k + k(k+1)/2 + 3 floats
+size_t partial_row(int k) { return (size_t)k + (size_t)k * (k + 1) / 2 + 3; }
+
+int grid_of(int occ, int sms, int64_t items)
+{
+    int64_t need = (items + THREADS - 1) / THREADS;
+    int64_t g = (int64_t)occ * sms;
+    if (need < g) g = need;
+    return (int)(g > 0 ? g : 1);
+}
+
+void free_state(prost_handle *h)
+{
+    if (h->U) cudaFree(h->U);
+    if (h->labels) cudaFree(h->labels);
+    if (h->ks) cudaFree(h->ks);
+    if (h->partials) cudaFree(h->partials);
+    if (h->counter) cudaFree(h->counter);
+    if (h->frame_buf) cudaFree(h->frame_buf);
+    if (h->bg_buf) cudaFree(h->bg_buf);
+    if (h->u_buf) cudaFree(h->u_buf);
+    if (h->h_word) cudaFreeHost(h->h_word);
+    for (int i = 0; i < CGMAX + 3; ++i)
+        if (h->ev[i]) cudaEventDestroy(h->ev[i]);
+    for (int i = 0; i < CGMAX + 3; ++i) h->ev[i] = nullptr;
+    h->U = nullptr; h->labels = nullptr; h->ks = nullptr; h->partials = nullptr;
+    h->counter = nullptr; h->frame_buf = nullptr; h->bg_buf = nullptr; h->u_buf = nullptr;
+    h->h_word = nullptr;
+}
+
+int run_gram(prost_handle *h)
+{
+    GramArgs ga;
+    ga.U = h->U;
+    ga.ks = h->ks;
+    ga.partials = h->partials;
+    ga.counter = h->counter;
+    ga.prm = h->dp;
+    CK(h, h->ops->gram(ga, h->grid_gram, h->stream));
+    return PROST_OK;
+}
+
+int read_status(prost_handle *h, int *status)
+{
+    CK(h, cudaMemcpyAsync(h->h_word, &h->ks->last_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *status = h->h_word[0];
+    return PROST_OK;
+}
+
+struct StateHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    prost_params prm;
+    uint64_t u_bytes, ks_bytes, label_bytes;
+};
+
+} // namespace
+
+extern "C" {
+
+int prost_version(void) { return 100; }
+
+const char *prost_strerror(int code)
+{
+    switch (code) {
+    case PROST_OK: return "ok";
+    case PROST_EINVAL: return "invalid argument";
+    case PROST_ENOMEM: return "out of memory";
+    case PROST_ECUDA: return "CUDA error";
+    case PROST_EBADFRAME: return "frame has a non-finite entry";
+    case PROST_ETIMEOUT: return "device wait timed out";
+    case PROST_ENOTSPD: return "Gram matrix not positive definite";
+    default: return "unknown error";
+    }
+}
+
+const char *prost_last_error(const prost_handle *h) { return h ? h->err.c_str() : g_init_err.c_str(); }
+
+int prost_state_bytes(const prost_params *prm, size_t *bytes)
+{
+    DevParams dp;
+    std::string why;
+    int rc = check_params(prm, &dp, &why);
+    if (rc) return rc;
+    if (!bytes) return PROST_EINVAL;
+    const int64_t m = m_of(*prm);
+    size_t b = (size_t)prm->k * dp.C * dp.Pp * sizeof(float) + (size_t)dp.Pp + sizeof(KState) +
+               sizeof(unsigned int) + (size_t)4096 * partial_row(prm->k) * sizeof(float) +
+               (size_t)m * frame_elem_bytes(*prm);
+    *bytes = b;
+    return PROST_OK;
+}
+
+int prost_init(const prost_params *prm, void *stream, prost_handle **out)
+{
+    if (!out) { g_init_err = "out is NULL"; return PROST_EINVAL; }
+    *out = nullptr;
+    DevParams dp;
+    std::string why;
+    int rc = check_params(prm, &dp, &why);
+    if (rc) { g_init_err = why; return rc; }
+    load_ops();
+    const KernelOps *ops = g_ops[prm->k];
+    if (!ops) { g_init_err = "no kernel set for this k"; return PROST_EINVAL; }
+
+    prost_handle *h = new (std::nothrow) prost_handle();
+    if (!h) { g_init_err = "host allocation failed"; return PROST_ENOMEM; }
+    h->prm = *prm;
+    h->dp = dp;
+    h->ops = ops;
+    h->stream = (cudaStream_t)stream;
+    h->U = nullptr; h->labels = nullptr; h->ks = nullptr; h->partials = nullptr;
+    h->counter = nullptr; h->frame_buf = nullptr; h->bg_buf = nullptr; h->u_buf = nullptr;
+    h->h_word = nullptr;
+    h->timing = 0;
+    h->timed_frames = 0;
+    for (int i = 0; i < CGMAX + 3; ++i) h->ev[i] = nullptr;
+
+    auto bail = [&](int code) {
+        g_init_err = h->err;
+        free_state(h);
+        delete h;
+        return code;
+    };
+#define CKI(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                   \
+            return bail(e_ == cudaErrorMemoryAllocation ? PROST_ENOMEM : PROST_ECUDA);     \
+        }                                                                                  \
+    } while (0)
+
+    CKI(cudaGetDevice(&h->device));
+    CKI(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+    const int fdt = prm->frame_dtype;
+    const int64_t groups = dp.Pp / ops->vw;
+    h->grid_pass_m = grid_of(ops->occupancy(0, fdt), h->num_sms, (int64_t)dp.C * groups);
+    h->grid_pass = grid_of(ops->occupancy(1, fdt), h->num_sms, (int64_t)dp.C * groups);
+    h->grid_ustep = grid_of(ops->occupancy(2, fdt), h->num_sms, dp.Pp / ops->vwu);
+    h->grid_gram = grid_of(ops->occupancy(3, fdt), h->num_sms, (int64_t)dp.C * groups);
+    int gmax = h->grid_pass_m;
+    if (h->grid_pass > gmax) gmax = h->grid_pass;
+    if (h->grid_ustep > gmax) gmax = h->grid_ustep;
+    if (h->grid_gram > gmax) gmax = h->grid_gram;
+    h->partial_floats = (size_t)gmax * partial_row(prm->k);
+
+    const int64_t m = m_of(*prm);
+    CKI(cudaMalloc(&h->U, (size_t)prm->k * dp.C * dp.Pp * sizeof(float)));
+    CKI(cudaMalloc(&h->labels, (size_t)dp.Pp));
+    CKI(cudaMalloc(&h->ks, sizeof(KState)));
+    CKI(cudaMalloc(&h->partials, h->partial_floats * sizeof(float)));
+    CKI(cudaMalloc(&h->counter, sizeof(unsigned int)));
+    CKI(cudaMalloc(&h->frame_buf, (size_t)m * frame_elem_bytes(*prm)));
+    CKI(cudaMallocHost(&h->h_word, 64));
+    // the frame planes allow vector loads when every plane starts on a VW boundary
+    h->dp.vec = (dp.P % ops->vw) == 0 && (dp.P % ops->vwu) == 0 ? 1 : 0;
+
+    CKI(cudaMemsetAsync(h->labels, 0, (size_t)dp.Pp, h->stream));
+    CKI(cudaMemsetAsync(h->ks, 0, sizeof(KState), h->stream));
+    CKI(cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), h->stream));
+    CKI(launch_init_gauss(h->U, h->dp, prm->seed, h->stream));
+    rc = run_gram(h);
+    if (rc) return bail(rc);
+    int st = 0;
+    rc = read_status(h, &st);
+    if (rc) return bail(rc);
+    if (st != 0) { h->err = "initial subspace not full rank"; return bail(PROST_ENOTSPD); }
+#undef CKI
+    *out = h;
+    return PROST_OK;
+}
+
+int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_out,
+               float *background_out)
+{
+    if (!h) return PROST_EINVAL;
+    if (!frame) return fail(h, PROST_EINVAL, "frame is NULL");
+    DeviceGuard dg(h->device);
+    const int64_t m = m_of(h->prm);
+    const int fdt = h->prm.frame_dtype;
+    const void *fptr = frame;
+    if (!on_device) {
+        CK(h, cudaMemcpyAsync(h->frame_buf, frame, (size_t)m * frame_elem_bytes(h->prm),
+                              cudaMemcpyHostToDevice, h->stream));
+        fptr = h->frame_buf;
+    }
+    // vector frame loads need planes on VW boundaries and an aligned base pointer
+    const uintptr_t fa = (uintptr_t)fptr;
+    const size_t eb = frame_elem_bytes(h->prm);
+    PassArgs pa;
+    pa.U = h->U;
+    pa.frame = fptr;
+    pa.labels = h->labels;
+    pa.ks = h->ks;
+    pa.partials = h->partials;
+    pa.counter = h->counter;
+    pa.pad = 0;
+    pa.prm = h->dp;
+    pa.prm.vec = h->dp.vec && fa % (eb * (size_t)h->ops->vw) == 0;
+    if (h->timing) CK(h, cudaEventRecord(h->ev[0], h->stream));
+    for (int j = 0; j <= h->prm.n_cg; ++j) {
+        pa.pass = j;
+        const bool wm = j < h->prm.n_cg;
+        CK(h, h->ops->pass(pa, wm, fdt, wm ? h->grid_pass_m : h->grid_pass, h->stream));
+        if (h->timing) CK(h, cudaEventRecord(h->ev[j + 1], h->stream));
+    }
+    float *bg_dev = nullptr;
+    if (background_out) {
+        if (on_device) {
+            bg_dev = background_out;
+        } else {
+            if (!h->bg_buf) CK(h, cudaMalloc(&h->bg_buf, (size_t)m * sizeof(float)));
+            bg_dev = h->bg_buf;
+        }
+    }
+    UstepArgs ua;
+    ua.U = h->U;
+    ua.frame = fptr;
+    ua.labels = h->labels;
+    ua.mask_out = on_device ? mask_out : nullptr;
+    ua.bg_out = bg_dev;
+    ua.ks = h->ks;
+    ua.partials = h->partials;
+    ua.counter = h->counter;
+    ua.prm = h->dp;
+    ua.prm.vec = h->dp.vec && fa % (eb * (size_t)h->ops->vwu) == 0;
+    CK(h, h->ops->ustep(ua, fdt, h->grid_ustep, h->stream));
+    if (h->timing) {
+        CK(h, cudaEventRecord(h->ev[h->prm.n_cg + 2], h->stream));
+        h->timed_frames += 1;
+    }
+    if (on_device) return PROST_OK;
+    if (mask_out)
+        CK(h, cudaMemcpyAsync(mask_out, h->labels, (size_t)h->dp.P, cudaMemcpyDeviceToHost, h->stream));
+    if (background_out)
+        CK(h, cudaMemcpyAsync(background_out, h->bg_buf, (size_t)m * sizeof(float),
+                              cudaMemcpyDeviceToHost, h->stream));
+    int st = 0;
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    return st;
+}
+
+int prost_sync(prost_handle *h)
+{
+    if (!h) return PROST_EINVAL;
+    DeviceGuard dg(h->device);
+    CK(h, cudaMemcpyAsync(h->h_word, &h->ks->err_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemsetAsync(&h->ks->err_flags, 0, sizeof(uint32_t), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const uint32_t f = (uint32_t)h->h_word[0];
+    if (f & ERR_TIMEOUT) return PROST_ETIMEOUT;
+    if (f & ERR_NOTSPD) return PROST_ENOTSPD;
+    if (f & ERR_BADFRAME) return PROST_EBADFRAME;
+    return PROST_OK;
+}
+
+int prost_get_subspace(prost_handle *h, float *U_out, double *y_out, int on_device)
+{
+    if (!h) return PROST_EINVAL;
+    DeviceGuard dg(h->device);
+    const int64_t m = m_of(h->prm);
+    const int k = h->prm.k;
+    if (U_out) {
+        float *dst = U_out;
+        if (!on_device) {
+            if (!h->u_buf) CK(h, cudaMalloc(&h->u_buf, (size_t)m * k * sizeof(float)));
+            dst = h->u_buf;
+        }
+        CK(h, h->ops->export_u(h->U, h->ks, dst, h->dp, h->stream));
+        if (!on_device)
+            CK(h, cudaMemcpyAsync(U_out, h->u_buf, (size_t)m * k * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    }
+    if (y_out)
+        CK(h, cudaMemcpyAsync(y_out, h->ks->y, (size_t)k * sizeof(double),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+    if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
+    return PROST_OK;
+}
+
+int prost_set_subspace(prost_handle *h, const float *U, const double *y, int on_device)
+{
+    if (!h) return PROST_EINVAL;
+    if (!U) return fail(h, PROST_EINVAL, "U is NULL");
+    DeviceGuard dg(h->device);
+    const int64_t m = m_of(h->prm);
+    const int k = h->prm.k;
+    const float *src = U;
+    if (!on_device) {
+        if (!h->u_buf) CK(h, cudaMalloc(&h->u_buf, (size_t)m * k * sizeof(float)));
+        CK(h, cudaMemcpyAsync(h->u_buf, U, (size_t)m * k * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        src = h->u_buf;
+    }
+    CK(h, launch_import_u(src, h->U, h->dp, h->stream));
+    if (y)
+        CK(h, cudaMemcpyAsync(h->ks->y, y, (size_t)k * sizeof(double),
+                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    else
+        CK(h, cudaMemsetAsync(h->ks->y, 0, (size_t)k * sizeof(double), h->stream));
+    int rc = run_gram(h);
+    if (rc) return rc;
+    int st = 0;
+    rc = read_status(h, &st);
+    if (rc) return rc;
+    if (st == PROST_ENOTSPD) return fail(h, PROST_ENOTSPD, "subspace columns are not linearly independent");
+    return PROST_OK;
+}
+
+int prost_set_labels(prost_handle *h, const uint8_t *labels, int on_device)
+{
+    if (!h) return PROST_EINVAL;
+    DeviceGuard dg(h->device);
+    const uint8_t *src = labels;
+    if (labels && !on_device) {
+        // stage through the frame buffer (at least P bytes)
+        CK(h, cudaMemcpyAsync(h->frame_buf, labels, (size_t)h->dp.P, cudaMemcpyHostToDevice, h->stream));
+        src = (const uint8_t *)h->frame_buf;
+    }
+    CK(h, launch_import_labels(src, h->labels, h->dp, h->stream));
+    if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
+    return PROST_OK;
+}
+
+int prost_set_frame_index(prost_handle *h, int64_t i)
+{
+    if (!h) return PROST_EINVAL;
+    if (i < 0) return fail(h, PROST_EINVAL, "frame index must be >= 0");
+    DeviceGuard dg(h->device);
+    int64_t *w = (int64_t *)h->h_word;
+    CK(h, cudaStreamSynchronize(h->stream));
+    w[0] = i;
+    CK(h, cudaMemcpyAsync(&h->ks->frame_index, w, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return PROST_OK;
+}
+
+int prost_get_stats(prost_handle *h, prost_stats *out)
+{
+    if (!h || !out) return PROST_EINVAL;
+    DeviceGuard dg(h->device);
+    KState ks;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(&ks, h->ks, sizeof(KState), cudaMemcpyDeviceToHost));
+    memset(out, 0, sizeof(*out));
+    out->frames = ks.frame_index;
+    out->bad_frames = ks.bad_frames;
+    out->n_cg = ks.n_cg_done;
+    out->status = ks.last_status;
+    for (int j = 0; j <= CGMAX; ++j) {
+        out->cost[j] = ks.cost[j];
+        out->gnorm[j] = ks.gnorm[j];
+        out->beta[j] = ks.beta[j];
+        if (j < CGMAX) out->alpha[j] = ks.alpha[j];
+    }
+    out->pi_norm = ks.pi_norm;
+    out->y_norm = ks.y_norm;
+    out->sigma = ks.sigma;
+    out->t = ks.t;
+    out->theta = ks.theta;
+    out->updated = ks.updated;
+    out->n_foreground = ks.n_fg;
+    out->orth_err = ks.orth_err;
+    return PROST_OK;
+}
+
+int prost_get_state(prost_handle *h, void *buf, size_t *len)
+{
+    if (!h || !len) return PROST_EINVAL;
+    DeviceGuard dg(h->device);
+    const DevParams &dp = h->dp;
+    const size_t plane = (size_t)dp.P * sizeof(float);
+    const size_t u_bytes = plane * dp.C * dp.k;
+    const size_t need = sizeof(StateHeader) + u_bytes + sizeof(KState) + (size_t)dp.P;
+    if (!buf) { *len = need; return PROST_OK; }
+    if (*len < need) return fail(h, PROST_EINVAL, "buffer too small");
+    StateHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "PROSTST1", 8);
+    hd.version = 1;
+    hd.header_bytes = sizeof(StateHeader);
+    hd.prm = h->prm;
+    hd.u_bytes = u_bytes;
+    hd.ks_bytes = sizeof(KState);
+    hd.label_bytes = (uint64_t)dp.P;
+    char *b = (char *)buf;
+    memcpy(b, &hd, sizeof(hd));
+    char *pu = b + sizeof(hd);
+    CK(h, cudaStreamSynchronize(h->stream));
+    // planes of the stored subspace without their padding
+    CK(h, cudaMemcpy2D(pu, plane, h->U, (size_t)dp.Pp * sizeof(float), plane, (size_t)dp.C * dp.k,
+                       cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(pu + u_bytes, h->ks, sizeof(KState), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(pu + u_bytes + sizeof(KState), h->labels, (size_t)dp.P, cudaMemcpyDeviceToHost));
+    *len = need;
+    return PROST_OK;
+}
+
+int prost_set_state(prost_handle *h, const void *buf, size_t len)
+{
+    if (!h || !buf) return PROST_EINVAL;
+    DeviceGuard dg(h->device);
+    const DevParams &dp = h->dp;
+    const size_t plane = (size_t)dp.P * sizeof(float);
+    const size_t u_bytes = plane * dp.C * dp.k;
+    const size_t need = sizeof(StateHeader) + u_bytes + sizeof(KState) + (size_t)dp.P;
+    if (len < sizeof(StateHeader)) return fail(h, PROST_EINVAL, "state buffer too short");
+    StateHeader hd;
+    memcpy(&hd, buf, sizeof(hd));
+    if (memcmp(hd.magic, "PROSTST1", 8) != 0 || hd.version != 1 || hd.header_bytes != sizeof(StateHeader))
+        return fail(h, PROST_EINVAL, "not a prost state buffer of this version");
+    prost_params a = hd.prm, b = h->prm;
+    a.seed = b.seed = 0;
+    if (memcmp(&a, &b, sizeof(prost_params)) != 0)
+        return fail(h, PROST_EINVAL, "state was made with other parameters");
+    if (len < need || hd.u_bytes != u_bytes || hd.ks_bytes != sizeof(KState) || hd.label_bytes != (uint64_t)dp.P)
+        return fail(h, PROST_EINVAL, "state buffer sizes do not match");
+    const char *pu = (const char *)buf + sizeof(hd);
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemset(h->U, 0, (size_t)dp.k * dp.C * dp.Pp * sizeof(float)));
+    CK(h, cudaMemcpy2D(h->U, (size_t)dp.Pp * sizeof(float), pu, plane, plane, (size_t)dp.C * dp.k,
+                       cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->ks, pu + u_bytes, sizeof(KState), cudaMemcpyHostToDevice));
+    CK(h, cudaMemset(h->labels, 0, (size_t)dp.Pp));
+    CK(h, cudaMemcpy(h->labels, pu + u_bytes + sizeof(KState), (size_t)dp.P, cudaMemcpyHostToDevice));
+    return PROST_OK;
+}
+
+int prost_set_timing(prost_handle *h, int enable)
+{
+    if (!h) return PROST_EINVAL;
+    DeviceGuard dg(h->device);
+    if (enable && !h->ev[0])
+        for (int i = 0; i < CGMAX + 3; ++i) CK(h, cudaEventCreate(&h->ev[i]));
+    h->timing = enable ? 1 : 0;
+    h->timed_frames = 0;
+    return PROST_OK;
+}
+
+int prost_get_timing(prost_handle *h, float *ms, int *n)
+{
+    if (!h || !ms || !n) return PROST_EINVAL;
+    if (!h->timing || h->timed_frames == 0) return fail(h, PROST_EINVAL, "no traced frame");
+    DeviceGuard dg(h->device);
+    const int nl = h->prm.n_cg + 2;
+    CK(h, cudaEventSynchronize(h->ev[nl]));
+    for (int j = 0; j < nl; ++j) CK(h, cudaEventElapsedTime(&ms[j], h->ev[j], h->ev[j + 1]));
+    *n = nl;
+    return PROST_OK;
+}
+
+void prost_destroy(prost_handle *h)
+{
+    if (!h) return;
+    {
+        DeviceGuard dg(h->device);
+        cudaStreamSynchronize(h->stream);
+        free_state(h);
+    }
+    delete h;
+}
+
+} // extern "C"

@@ -1,0 +1,96 @@
+// Kernels that do not depend on the subspace dimension: the seeded Gaussian
+// initial subspace and the layout conversions of the ABI.
+#include <math.h>
+#include <stdint.h>
+
+#include "prost_device.h"
+
+namespace prost {
+
+// splitmix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): a counter-based 64-bit mixer.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Standard normal draw number `ctr` of stream `seed` (Box-Muller on two
+// 24-bit uniforms in (0, 1)).
+__device__ __forceinline__ float gauss(uint64_t seed, uint64_t ctr)
+{
+    const uint64_t h1 = splitmix64(seed ^ splitmix64(2 * ctr));
+    const uint64_t h2 = splitmix64(seed ^ splitmix64(2 * ctr + 1));
+    const float u1 = ((float)(h1 >> 40) + 0.5f) * (1.0f / 16777216.0f);
+    const float u2 = ((float)(h2 >> 40) + 0.5f) * (1.0f / 16777216.0f);
+    return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// U_st = N(0, 1)/sqrt(m) per entry (pad rows 0); its Cholesky-QR (run next)
+// gives the orthonormal factor of a random m x k matrix (Section 3.4).
+__global__ void k_init_gauss(float *U, DevParams prm, uint64_t seed)
+{
+    const int64_t rows = (int64_t)prm.C * prm.Pp;
+    const int64_t n = rows * prm.k;
+    const float s = rsqrtf((float)((double)prm.C * (double)prm.P));
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / rows;
+        const int64_t rr = i - j * rows;
+        const int64_t c = rr / prm.Pp;
+        const int64_t q = rr - c * prm.Pp;
+        float v = 0.f;
+        if (q < prm.P) v = s * gauss(seed, (uint64_t)((c * prm.P + q) * prm.k + j));
+        U[i] = v;
+    }
+}
+
+// m x k row-major -> stored layout (column j, channel c at (j*C + c)*Pp).
+__global__ void k_import_u(const float *Urow, float *U, DevParams prm)
+{
+    const int64_t rows = (int64_t)prm.C * prm.Pp;
+    const int64_t n = rows * prm.k;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = i / rows;
+        const int64_t rr = i - j * rows;
+        const int64_t c = rr / prm.Pp;
+        const int64_t q = rr - c * prm.Pp;
+        U[i] = q < prm.P ? Urow[(c * prm.P + q) * prm.k + j] : 0.f;
+    }
+}
+
+__global__ void k_import_labels(const uint8_t *src, uint8_t *labels, DevParams prm)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < prm.Pp;
+         q += (int64_t)gridDim.x * blockDim.x)
+        labels[q] = (src && q < prm.P && src[q]) ? 1 : 0;
+}
+
+static int grid_for(int64_t n)
+{
+    const int64_t b = (n + THREADS - 1) / THREADS;
+    return (int)(b < 8192 ? (b > 0 ? b : 1) : 8192);
+}
+
+cudaError_t launch_init_gauss(float *U, DevParams prm, uint64_t seed, cudaStream_t s)
+{
+    k_init_gauss<<<grid_for((int64_t)prm.C * prm.Pp * prm.k), THREADS, 0, s>>>(U, prm, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import_u(const float *Urow, float *U, DevParams prm, cudaStream_t s)
+{
+    k_import_u<<<grid_for((int64_t)prm.C * prm.Pp * prm.k), THREADS, 0, s>>>(Urow, U, prm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_import_labels(const uint8_t *src, uint8_t *labels, DevParams prm, cudaStream_t s)
+{
+    k_import_labels<<<grid_for(prm.Pp), THREADS, 0, s>>>(src, labels, prm);
+    return cudaGetLastError();
+}
+
+} // namespace prost

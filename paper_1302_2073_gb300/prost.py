@@ -1,0 +1,249 @@
+"""Python binding of libprost (include/prost.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Buffers may be
+torch tensors (device or host) or numpy arrays (host); ``on_device`` is taken
+from the tensors.  Negative return codes raise :class:`ProstError`, except
+the frame status PROST_EBADFRAME, which prost_step() and prost_sync() return.
+The library is built in-tree on first use; without it every call fails.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+PROST_OK, PROST_EINVAL, PROST_ENOMEM, PROST_ECUDA = 0, -1, -2, -3
+PROST_EBADFRAME, PROST_ETIMEOUT, PROST_ENOTSPD = -4, -5, -6
+PROST_U8, PROST_F32 = 0, 1
+PROST_MASK_POST_UPDATE, PROST_MASK_PRE_UPDATE = 0, 1
+PROST_MAX_K, PROST_MAX_CG = 16, 32
+
+HEADER = os.path.join(_build.INCLUDE, "prost.h")
+
+
+class ProstError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code})")
+        self.code = code
+
+
+class prost_params(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("channels", C.c_int32),
+                ("k", C.c_int32), ("p", C.c_double), ("mu", C.c_double), ("delta", C.c_double),
+                ("omega", C.c_double), ("t_init", C.c_double), ("t_min", C.c_double),
+                ("i_init", C.c_int32), ("n_cg", C.c_int32), ("in_scale", C.c_double),
+                ("in_offset", C.c_double), ("frame_dtype", C.c_int32), ("u_dtype", C.c_int32),
+                ("mask_from", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64)]
+
+
+class prost_stats(C.Structure):
+    _fields_ = [("frames", C.c_int64), ("bad_frames", C.c_int64), ("n_cg", C.c_int32),
+                ("status", C.c_int32), ("cost", C.c_double * (PROST_MAX_CG + 1)),
+                ("gnorm", C.c_double * (PROST_MAX_CG + 1)), ("alpha", C.c_double * PROST_MAX_CG),
+                ("beta", C.c_double * (PROST_MAX_CG + 1)), ("pi_norm", C.c_double),
+                ("y_norm", C.c_double), ("sigma", C.c_double), ("t", C.c_double),
+                ("theta", C.c_double), ("updated", C.c_int32), ("pad0", C.c_int32),
+                ("n_foreground", C.c_int64), ("orth_err", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (built in-tree if missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, sz = C.c_void_p, C.c_size_t
+        P = C.POINTER
+        L.prost_state_bytes.argtypes = [P(prost_params), P(sz)]
+        L.prost_init.argtypes = [P(prost_params), vp, P(vp)]
+        L.prost_step.argtypes = [vp, vp, C.c_int, vp, vp]
+        L.prost_sync.argtypes = [vp]
+        L.prost_get_subspace.argtypes = [vp, vp, vp, C.c_int]
+        L.prost_set_subspace.argtypes = [vp, vp, vp, C.c_int]
+        L.prost_set_labels.argtypes = [vp, vp, C.c_int]
+        L.prost_set_frame_index.argtypes = [vp, C.c_int64]
+        L.prost_get_stats.argtypes = [vp, P(prost_stats)]
+        L.prost_get_state.argtypes = [vp, vp, P(sz)]
+        L.prost_set_state.argtypes = [vp, vp, sz]
+        L.prost_set_timing.argtypes = [vp, C.c_int]
+        L.prost_get_timing.argtypes = [vp, P(C.c_float), P(C.c_int)]
+        L.prost_destroy.argtypes = [vp]
+        L.prost_destroy.restype = None
+        L.prost_strerror.argtypes = [C.c_int]
+        L.prost_strerror.restype = C.c_char_p
+        L.prost_last_error.argtypes = [vp]
+        L.prost_last_error.restype = C.c_char_p
+        L.prost_version.argtypes = []
+        _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of the entry points declared in include/prost.h."""
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(prost_[a-z_]+)\s*\(", src)))
+
+
+# ---- marshalling helpers ---------------------------------------------------
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _where(*bufs):
+    flags = {bool(b.is_cuda) for b in bufs if b is not None and _is_torch(b)}
+    flags |= {False for b in bufs if isinstance(b, np.ndarray)}
+    if len(flags) > 1:
+        raise ValueError("buffers must be all on the device or all on the host")
+    return 1 if flags == {True} else 0
+
+
+def _check(rc, h=None, allow=()):
+    if rc < 0 and rc not in allow:
+        detail = lib().prost_last_error(h).decode()
+        raise ProstError(rc, f"{prost_strerror(rc)}: {detail}" if detail else prost_strerror(rc))
+    return rc
+
+
+_DTYPES = {"u8": PROST_U8, "uint8": PROST_U8, "f32": PROST_F32, "float32": PROST_F32}
+
+
+def make_params(width, height, channels=1, k=5, p=0.25, mu=0.0, delta=0.35, omega=5e-5,
+                t_init=5e-3, t_min=1e-4, i_init=100, n_cg=5, in_scale=1.0, in_offset=0.0,
+                frame_dtype="u8", u_dtype="f32", mask_from=PROST_MASK_POST_UPDATE, seed=0,
+                **_ignored) -> prost_params:
+    fd = _DTYPES[frame_dtype] if isinstance(frame_dtype, str) else int(frame_dtype)
+    ud = _DTYPES[u_dtype] if isinstance(u_dtype, str) else int(u_dtype)
+    return prost_params(int(width), int(height), int(channels), int(k), float(p), float(mu),
+                        float(delta), float(omega), float(t_init), float(t_min), int(i_init),
+                        int(n_cg), float(in_scale), float(in_offset), fd, ud, int(mask_from), 0,
+                        int(seed))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+# ---- the C entry points ------------------------------------------------------
+
+def prost_version():
+    return lib().prost_version()
+
+
+def prost_strerror(code):
+    return lib().prost_strerror(int(code)).decode()
+
+
+def prost_last_error(h=None):
+    return lib().prost_last_error(h).decode()
+
+
+def prost_state_bytes(params):
+    n = C.c_size_t()
+    _check(lib().prost_state_bytes(C.byref(params), C.byref(n)))
+    return n.value
+
+
+def prost_init(params, stream=None):
+    h = C.c_void_p()
+    _check(lib().prost_init(C.byref(params), _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def prost_step(h, frame, mask_out=None, background_out=None):
+    """Steps 1-3 for one frame; returns PROST_OK or PROST_EBADFRAME (host
+    buffers: the frame's status; device buffers: PROST_OK once enqueued)."""
+    od = _where(frame, mask_out, background_out)
+    return _check(lib().prost_step(h, _ptr(frame), od, _ptr(mask_out), _ptr(background_out)), h,
+                  allow=(PROST_EBADFRAME,))
+
+
+def prost_sync(h):
+    return _check(lib().prost_sync(h), h, allow=(PROST_EBADFRAME,))
+
+
+def prost_get_subspace(h, U_out=None, y_out=None):
+    od = _where(U_out, y_out)
+    return _check(lib().prost_get_subspace(h, _ptr(U_out), _ptr(y_out), od), h)
+
+
+def prost_set_subspace(h, U, y=None):
+    od = _where(U, y)
+    return _check(lib().prost_set_subspace(h, _ptr(U), _ptr(y), od), h)
+
+
+def prost_set_labels(h, labels=None):
+    od = _where(labels)
+    return _check(lib().prost_set_labels(h, _ptr(labels), od), h)
+
+
+def prost_set_frame_index(h, i):
+    return _check(lib().prost_set_frame_index(h, int(i)), h)
+
+
+def prost_get_stats(h):
+    st = prost_stats()
+    _check(lib().prost_get_stats(h, C.byref(st)), h)
+    return st
+
+
+def prost_get_state(h):
+    n = C.c_size_t(0)
+    _check(lib().prost_get_state(h, None, C.byref(n)), h)
+    buf = (C.c_char * n.value)()
+    _check(lib().prost_get_state(h, buf, C.byref(n)), h)
+    return bytes(buf[: n.value])
+
+
+def prost_set_state(h, state: bytes):
+    buf = C.create_string_buffer(state, len(state))
+    return _check(lib().prost_set_state(h, buf, len(state)), h)
+
+
+def prost_set_timing(h, enable=True):
+    return _check(lib().prost_set_timing(h, 1 if enable else 0), h)
+
+
+def prost_get_timing(h):
+    """Per-launch device times (ms) of the last traced frame."""
+    buf = (C.c_float * (PROST_MAX_CG + 2))()
+    n = C.c_int(0)
+    _check(lib().prost_get_timing(h, buf, C.byref(n)), h)
+    return [buf[j] for j in range(n.value)]
+
+
+def prost_destroy(h):
+    if h:
+        lib().prost_destroy(h)
+
+
+__all__ = [n for n in dir() if n.startswith(("prost_", "PROST_"))] + [
+    "ProstError", "make_params", "header_functions", "lib"]

@@ -157,7 +157,7 @@ class SyntheticVideo:
             out = np.rint(255.0 * v).astype(np.uint8)
         else:
             out = v.astype(np.float32)
-        return out, fg
+        return np.ascontiguousarray(out), np.ascontiguousarray(fg)
 
     def frames(self, start: int, count: int) -> np.ndarray:
         """(count, C, H, W) stack of frames start .. start+count-1."""

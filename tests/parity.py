@@ -1,0 +1,114 @@
+"""Helpers of the GPU-vs-oracle parity tests (teacher forcing: both sides
+start a frame from the same state and advance it once)."""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+import oracle
+import paper_1302_2073_gb300 as pg
+
+# Tolerances (FP32 GPU vs FP64 oracle).  The residual and cost bound is the
+# stated acceptance bound; masks may differ only at pixels whose FP64 maximum
+# residual lies within MASK_BAND of delta.
+RES_RTOL = 1e-4
+COST_RTOL = 1e-4
+MASK_BAND = 1e-6
+# FP32 storage of U (relative rounding 6e-8 per entry) and FP32 per-row
+# arithmetic bound the coefficient and subspace differences well below these.
+Y_RTOL = 1e-5
+U_RTOL = 1e-5
+THETA_RTOL = 1e-4
+
+
+def oracle_params(wp: dict):
+    return oracle.params(**wp)
+
+
+def gpu_params(wp: dict, **over):
+    d = dict(wp)
+    d.update(over)
+    return pg.make_params(**d)
+
+
+@dataclass
+class GpuStep:
+    mask: np.ndarray
+    background: np.ndarray
+    U: np.ndarray
+    y: np.ndarray
+    stats: object
+    status: int
+
+
+def matched_start(U, y):
+    """The state both sides start from: FP32 rounding of U, re-orthonormalised
+    (what the GPU stores), and y transformed so that U y is kept."""
+    U32 = np.ascontiguousarray(U, dtype=np.float32)
+    U64, y64 = oracle.reorthonormalize(U32.astype(np.float64), np.asarray(y, dtype=np.float64))
+    return U32, U64, y64
+
+
+def gpu_step_from(h, U32, y, labels, i, frame, device=True, torch=None):
+    """Hand the GPU tracker a state, run one frame, read everything back."""
+    m, k = U32.shape
+    P = labels.size
+    pg.prost_set_subspace(h, U32, np.ascontiguousarray(y, dtype=np.float64))
+    pg.prost_set_labels(h, np.ascontiguousarray(labels, dtype=np.uint8))
+    pg.prost_set_frame_index(h, i)
+    if device:
+        f = torch.from_numpy(np.ascontiguousarray(frame)).cuda()
+        mask = torch.empty(P, dtype=torch.uint8, device="cuda")
+        bg = torch.empty(m, dtype=torch.float32, device="cuda")
+        pg.prost_step(h, f, mask, bg)
+        status = pg.prost_sync(h)
+        mask, bg = mask.cpu().numpy(), bg.cpu().numpy()
+    else:
+        mask = np.empty(P, dtype=np.uint8)
+        bg = np.empty(m, dtype=np.float32)
+        status = pg.prost_step(h, np.ascontiguousarray(frame), mask, bg)
+    stats = pg.prost_get_stats(h)
+    Ug = np.empty((m, k), dtype=np.float32)
+    yg = np.empty(k)
+    pg.prost_get_subspace(h, Ug, yg)
+    return GpuStep(mask, bg, Ug, yg, stats, status)
+
+
+def compare_step(prm_o, wp, U64, y64, labels, i, frame, g: GpuStep, n_cg=None):
+    """Run the oracle from the same state and assert parity; returns a dict of
+    the measured errors."""
+    st = oracle.OracleState(U64.copy(), y64.copy(), labels.copy(), i)
+    res = oracle.frame_step(prm_o, st, frame)
+    tr = res.trace
+    n = prm_o.n_cg if n_cg is None else n_cg
+    x = oracle.preprocess(prm_o, frame)
+    P = labels.size
+    C = x.size // P
+    err = {}
+    cg = np.array([g.stats.cost[j] for j in range(n + 1)])
+    co = np.array([tr.cost[j] for j in range(n + 1)])
+    err["cost"] = float(np.max(np.abs(cg - co) / np.abs(co)))
+    assert err["cost"] <= COST_RTOL, (cg, co)
+    err["y"] = float(np.linalg.norm(g.y - st.y) / max(np.linalg.norm(st.y), 1e-300))
+    assert err["y"] <= Y_RTOL, (g.y, st.y)
+    r_gpu = x - (g.background.astype(np.float64) - prm_o.in_offset)
+    err["res"] = float(np.linalg.norm(r_gpu - res.residual) / np.linalg.norm(res.residual))
+    assert err["res"] <= RES_RTOL
+    if tr.updated:
+        err["theta"] = abs(g.stats.theta - tr.theta) / tr.theta
+        assert err["theta"] <= THETA_RTOL, (g.stats.theta, tr.theta)
+    assert g.stats.updated == tr.updated
+    err["U"] = float(np.linalg.norm(g.U.astype(np.float64) - st.U) / np.linalg.norm(st.U))
+    assert err["U"] <= U_RTOL
+    maxres = np.abs(res.residual.reshape(C, P)).max(0)
+    diff = g.mask != res.labels
+    excused = np.abs(maxres - prm_o.delta) <= MASK_BAND
+    err["mask_diff"] = int(diff.sum())
+    err["mask_unexcused"] = int((diff & ~excused).sum())
+    assert err["mask_unexcused"] == 0, np.nonzero(diff & ~excused)[0][:10]
+    assert abs(int(g.stats.n_foreground) - int(tr.n_foreground)) <= int(diff.sum())
+    assert g.stats.frames == i + 1
+    assert abs(g.stats.t - tr.t) <= 1e-14 * tr.t
+    return err, st, res

@@ -1,0 +1,108 @@
+"""Parity of the CUDA path with the FP64 oracle (teacher forcing), through
+the C ABI, at sizes the oracle finishes in seconds: several CTA tiles, ragged
+plane tails, unaligned planes, and the edge cases of the method."""
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import paper_1302_2073_gb300 as pg
+from parity import compare_step, gpu_params, gpu_step_from, matched_start, oracle_params
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("these tests need a CUDA GPU")
+
+
+def _trajectory_states(wp, vid, n, seed=11):
+    """Oracle free-run from a seeded random subspace; the state before each frame."""
+    prm_o = oracle_params(wp)
+    st = oracle.initial_state(synth.random_orthonormal(vid.m, vid.k, seed), vid.P)
+    states = []
+    for t in range(n):
+        states.append(st.copy())
+        f, _ = vid.frame(t)
+        oracle.frame_step(prm_o, st, f)
+    return states
+
+
+def _run_case(wp, vid, frames, device=True, seed=11, **gover):
+    prm_o = oracle_params(dict(wp, **gover))
+    states = _trajectory_states(dict(wp, **gover), vid, max(frames) + 1, seed)
+    h = pg.prost_init(gpu_params(wp, **gover))
+    errs = []
+    try:
+        for t in frames:
+            s = states[t]
+            U32, U64, y64 = matched_start(s.U, s.y)
+            f, _ = vid.frame(t)
+            g = gpu_step_from(h, U32, s.y, s.labels, s.i, f, device=device, torch=torch)
+            assert g.status == pg.PROST_OK
+            e, _, _ = compare_step(prm_o, wp, U64, y64, s.labels, s.i, f, g)
+            errs.append(e)
+    finally:
+        pg.prost_destroy(h)
+    return errs
+
+
+def test_gray_160x120_k5_float_frames():
+    vid, wp = synth.make_workload("gray160x120_k5", n_frames=30)
+    errs = _run_case(wp, vid, [0, 1, 2, 25])
+    print(errs)
+
+
+def test_rgb_ragged_unaligned_planes_uint8():
+    # P = 37*29 = 1073: planes start off 4-byte boundaries, tails of every tile are ragged
+    vid = synth.SyntheticVideo(37, 29, 3, 3, n_frames=8, fg_fraction=0.1, shape="ellipse",
+                               jitter=1, seed=77, dtype="u8")
+    wp = synth.video._params(vid.m, vid.k, "u8")
+    wp.update(width=37, height=29, channels=3, frame_dtype="u8")
+    _run_case(wp, vid, [0, 1, 5])
+
+
+def test_rgb_64x48_k10_host_buffers_and_pre_update_labels():
+    vid, wp = synth.make_workload("rgb640x480_k10", width=64, height=48, n_frames=6)
+    _run_case(wp, vid, [0, 3], device=False)
+    _run_case(wp, vid, [0, 3], mask_from=pg.PROST_MASK_PRE_UPDATE)
+
+
+@pytest.mark.parametrize("k", [1, 2, 7, 12, 16])
+def test_subspace_dimensions(k):
+    vid = synth.SyntheticVideo(50, 40, 1, k, n_frames=4, fg_fraction=0.05, seed=100 + k, dtype="f32")
+    wp = synth.video._params(vid.m, k, "f32")
+    wp.update(width=50, height=40, channels=1, frame_dtype="f32")
+    _run_case(wp, vid, [0, 2])
+
+
+@pytest.mark.parametrize("n_cg", [0, 1, 12])
+def test_cg_iteration_counts(n_cg):
+    vid, wp = synth.make_workload("gray160x120_k5", width=40, height=30, n_frames=4)
+    _run_case(dict(wp, n_cg=n_cg), vid, [0, 2])
+
+
+@pytest.mark.parametrize("p,mu", [(2.0, 0.01), (1.0, 1e-3), (0.5, 0.05)])
+def test_cost_exponents(p, mu):
+    vid, wp = synth.make_workload("gray160x120_k5", width=40, height=30, n_frames=4)
+    _run_case(dict(wp, p=p, mu=mu), vid, [0, 2])
+
+
+def test_stats_report_the_step_size_rule():
+    vid, wp = synth.make_workload("gray160x120_k5", width=32, height=24, n_frames=2)
+    h = pg.prost_init(gpu_params(wp))
+    try:
+        f, _ = vid.frame(0)
+        prm_o = oracle_params(wp)
+        for i in (0, 7, 500):
+            pg.prost_set_frame_index(h, i)
+            assert pg.prost_step(h, f, np.empty(vid.P, np.uint8)) == pg.PROST_OK
+            st = pg.prost_get_stats(h)
+            assert abs(st.t - oracle.step_size(prm_o, i)) <= 1e-14 * st.t
+            assert st.frames == i + 1
+    finally:
+        pg.prost_destroy(h)

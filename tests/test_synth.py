@@ -19,6 +19,7 @@ def test_recipe_statistics():
     vid, prm = synth.make_workload("rgb640x480_k10", n_frames=4)
     f, gt = vid.frame(2)
     assert f.dtype == np.uint8 and f.shape == (3, 480, 640)
+    assert f.flags.c_contiguous and gt.flags.c_contiguous
     frac = gt.mean()
     assert 0.05 < frac < 0.09  # ~8% foreground (overlaps may lower it)
     b = vid.background(2) - vid.offset
