@@ -188,6 +188,48 @@ int prost_set_timing(prost_handle *h, int enable);
  * PROST_EINVAL if timing is off or no traced frame ran yet. */
 int prost_get_timing(prost_handle *h, float *ms, int *n);
 
+/* Cost and gradient of one frame without any device allocation.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not call cudaMalloc: code that runs while a CUDA graph is being
+ * captured, real-time pipelines that forbid allocation after start-up
+ * (cudaMalloc can synchronise the device and has no latency bound), and hosts
+ * whose device memory belongs to another allocator's pool.  They cannot
+ * create a handle with prost_init(), so this call takes everything from the
+ * caller and keeps its scratch (the per-CTA partial sums and the arrival
+ * counter of the reduction) in one file-scope static device array of about
+ * 74 KB, which every GPU that loads the library holds until the process
+ * exits.
+ *
+ * Computes, for the caller's subspace U and coefficients y, the weighted
+ * smoothed l_p cost h_{mu,w}(x - U y) (Eqs. weightedLPnorm, spcacost) and its
+ * gradient with respect to y, U^T eta with eta_e = -p w_e r_e (r_e^2 + mu)^(p/2 - 1)
+ * (Section 3.3), which is what the first residual pass of prost_step()
+ * computes at the warm-start y.  Uses prm's width, height, channels, k, p, mu,
+ * delta (for mu = 0), omega, in_scale, in_offset and frame_dtype.
+ *   U          device, m x k float32 row-major (used as given, not
+ *              re-orthonormalised)
+ *   y          host, k doubles
+ *   frame      device, m entries of prm->frame_dtype, channel-planar
+ *   labels     device, P bytes (nonzero = foreground, weight omega) or NULL
+ *              (all weights 1)
+ *   out        device, k + 1 doubles: out[0] = cost, out[1 + j] = gradient j
+ *   status_out device int32 or NULL: PROST_OK, or PROST_EBADFRAME when a
+ *              float32 frame has a non-finite entry (out is then not finite)
+ *   stream     cudaStream_t as void* (NULL = default stream)
+ * The call only enqueues work on the stream; read out after synchronising it.
+ * Limits: k <= PROST_MAX_K (the width of the static partial rows), m <= 2^30.
+ * Larger k, bad parameters or NULL pointers return PROST_EINVAL; a failed CUDA
+ * call returns PROST_ECUDA.  No detail string is recorded.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array, so calls that
+ * overlap on the GPU (other streams, other host threads) race: serialise
+ * them.  Each call clears the counter itself before its kernel runs. */
+int prost_cost_grad_static(const prost_params *prm, const float *U, const double *y,
+                           const void *frame, const uint8_t *labels, double *out,
+                           int32_t *status_out, void *stream);
+
 /* Release the device state (synchronises the stream first).  NULL is a no-op. */
 void prost_destroy(prost_handle *h);
 

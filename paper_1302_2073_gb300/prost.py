@@ -75,6 +75,8 @@ def lib():
         L.prost_set_state.argtypes = [vp, vp, sz]
         L.prost_set_timing.argtypes = [vp, C.c_int]
         L.prost_get_timing.argtypes = [vp, P(C.c_float), P(C.c_int)]
+        L.prost_cost_grad_static.argtypes = [P(prost_params), vp, P(C.c_double), vp, vp, vp,
+                                             vp, vp]
         L.prost_destroy.argtypes = [vp]
         L.prost_destroy.restype = None
         L.prost_strerror.argtypes = [C.c_int]
@@ -238,6 +240,16 @@ def prost_get_timing(h):
     n = C.c_int(0)
     _check(lib().prost_get_timing(h, buf, C.byref(n)), h)
     return [buf[j] for j in range(n.value)]
+
+
+def prost_cost_grad_static(params, U, y, frame, labels, out, status_out=None, stream=None):
+    """Cost and gradient of one frame with no device allocation (static
+    library scratch); U, frame, labels, out, status_out are device tensors,
+    y a sequence of k floats.  Enqueues only."""
+    yk = (C.c_double * max(1, len(y)))(*[float(v) for v in y])
+    return _check(lib().prost_cost_grad_static(C.byref(params), _ptr(U), yk, _ptr(frame),
+                                               _ptr(labels), _ptr(out), _ptr(status_out),
+                                               _stream_ptr(stream)))
 
 
 def prost_destroy(h):
