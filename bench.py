@@ -1,10 +1,10 @@
 #!/usr/bin/env python
 """Throughput of pROST's per-frame update (arXiv:1302.2073) on GB300.
 
-One step = one frame through the whole hot path: n_cg residual/gradient
-passes with the CG steps, the final pass with the rank-one SVD and geodesic
-angle, and the update/label pass with the folded Cholesky-QR (n_cg + 2 kernel
-launches).  Workload: the 640x480 RGB, k = 10, uint8 synthetic stream.
+One step = one frame through the whole hot path in one persistent kernel
+launch: n_cg residual/gradient passes with the CG steps, the final pass with
+the rank-one SVD and geodesic angle, and the update/label pass with the folded
+Cholesky-QR.  Workload: the 640x480 RGB, k = 10, uint8 synthetic stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -35,8 +35,8 @@ METRIC = "640x480 k=10 frames/s & achieved GB/s vs peak; batched BF16 vs FP32 at
 UNIT = "frames/s"
 WORKLOAD = "rgb640x480_k10"
 FLUSH_BYTES = 256 << 20  # larger than the 126.5 MB L2
-PROFILE = os.path.join(ROOT, "profiles", "k_pass_rgb640x480_k10.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_1302_2073_gb300", "csrc", "prost_kernels.cuh")
+PROFILE = os.path.join(ROOT, "profiles", "k_frame_rgb640x480_k10.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1302_2073_gb300", "csrc", "prost_frame.cuh")
 
 
 def parse():
@@ -148,8 +148,8 @@ def measured_peak_hbm():
 
 
 def profiled_traffic():
-    """DRAM bytes per launch of the CG pass from the committed ncu summary, if
-    the kernel source is unchanged since the capture (else None)."""
+    """DRAM bytes per launch of the frame kernel from the committed ncu
+    summary, if the kernel source is unchanged since the capture (else None)."""
     try:
         text = open(PROFILE).read()
         src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
@@ -241,7 +241,7 @@ def run_ours(args, dist):
     masks = torch.empty((2, vid.P), dtype=torch.uint8, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     n_cg = wp["n_cg"]
-    launches_per_step = n_cg + 2
+    launches_per_step = 1
 
     h = pg.prost_init(pg.make_params(**wp, seed=dist.rank + 1), stream=stream)
     try:
@@ -294,18 +294,18 @@ def run_ours(args, dist):
     value = n * K / (total_ms / 1000.0)
     e2e_value = n * K / e2e_s
 
-    # roofline of the dominant kernel: the CG pass (n_cg of the launches)
-    kern = np.array(kern)  # K x (n_cg + 2)
-    pass_ms = float(kern[:, :n_cg].mean()) if n_cg > 0 else float(kern[:, 0].mean())
+    # roofline of the dominant (only) kernel: one k_frame launch per frame
+    kern = np.array(kern)  # K x (n_cg + 2) phase times from the device clock
     m, P, k = vid.m, vid.P, vid.k
     sx = 1 if vid.dtype == "u8" else 4
-    pass_bytes = m * k * 4 + m * sx + P  # U read, frame read, label read
-    peak, peak_src = measured_peak_hbm()
-    achieved = pass_bytes / (pass_ms * 1e-3) / 1e9
     frame_bytes = (n_cg + 2) * m * k * 4 + m * k * 4 + (n_cg + 2) * (m * sx + P) + P
-    share = {"cg_pass": float(kern[:, :n_cg].sum() / kern.sum()),
-             "final_pass": float(kern[:, n_cg].sum() / kern.sum()),
-             "update_pass": float(kern[:, n_cg + 1].sum() / kern.sum())}
+    peak, peak_src = measured_peak_hbm()
+    launch_ms = float(np.mean(step_ms))
+    achieved = frame_bytes / (launch_ms * 1e-3) / 1e9
+    phase_ms = kern.mean(axis=0)
+    share = {"cg_passes": float(phase_ms[:n_cg].sum() / phase_ms.sum()),
+             "final_pass": float(phase_ms[n_cg] / phase_ms.sum()),
+             "update_pass": float(phase_ms[n_cg + 1] / phase_ms.sum())}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n, "steps": K, "warmup": W,
            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -313,12 +313,12 @@ def run_ours(args, dist):
            "config": _config(args, vid, wp, K),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": profiled_traffic(),
-                        "kernel": f"k_pass<{k},u8,M> (CG pass)", "bytes_per_launch": pass_bytes,
-                        "launch_ms": pass_ms, "peak_source": f"{peak_src} hbm_gbs"},
-           "frame": {"algorithmic_bytes": frame_bytes,
-                     "effective_gbs": frame_bytes / (ms_per_step * 1e-3) / 1e9,
-                     "frac_of_hbm_peak": frame_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
-                     "pixels_per_s": value * P, "kernel_time_share": share},
+                        "kernel": f"k_frame<{k},{vid.dtype}> (whole frame, one launch)",
+                        "bytes_per_launch": frame_bytes, "launch_ms": launch_ms,
+                        "peak_source": f"{peak_src} hbm_gbs"},
+           "frame": {"pixels_per_s": value * P,
+                     "phase_ms": [round(float(v), 5) for v in phase_ms],
+                     "phase_share": share},
            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": m * sx,
                    "d2h_bytes_per_step": P + 4},
            "gpu_launches": K * launches_per_step,

@@ -177,15 +177,18 @@ int prost_get_state(prost_handle *h, void *buf, size_t *len);
 int prost_set_state(prost_handle *h, const void *buf, size_t len);
 
 /* Tracing.  enable = 1 makes every later prost_step() record a CUDA event on
- * the handle's stream before its first kernel and after each of its n_cg + 2
- * kernel launches; enable = 0 stops it.  Costs one event record per launch. */
+ * the handle's stream before and after its frame launch; the frame kernel
+ * always stamps the device clock (%globaltimer) at the start of the frame, at
+ * the end of each residual pass and at the end of the frame.  enable = 0
+ * stops the events. */
 int prost_set_timing(prost_handle *h, int enable);
 
-/* Device time between the events of the last traced prost_step(): ms[j] for
- * launch j (j < n_cg: CG passes that also sum the line-step terms; j = n_cg:
- * the final pass; j = n_cg + 1: the update/label pass).  ms holds at least
- * n_cg + 2 floats; *n gets n_cg + 2.  Synchronises on the last event.
- * PROST_EINVAL if timing is off or no traced frame ran yet. */
+/* Device time of each phase of the last traced prost_step(): ms[j] for
+ * j < n_cg: CG pass j (residual, gradient, line-step sums and the CG step);
+ * j = n_cg: the final pass (gradient at the final y, rank-one SVD, angle);
+ * j = n_cg + 1: the update pass (geodesic update, labels, Cholesky-QR).  ms
+ * holds at least n_cg + 2 floats; *n gets n_cg + 2.  Synchronises on the
+ * frame's end event.  PROST_EINVAL if timing is off or no traced frame ran. */
 int prost_get_timing(prost_handle *h, float *ms, int *n);
 
 /* Cost and gradient of one frame without any device allocation.

@@ -19,13 +19,16 @@ struct prost_handle {
     cudaStream_t stream;
     int device;
     int num_sms;
-    int grid_pass_m, grid_pass, grid_ustep, grid_gram;
-    float *U;              // stored subspace (k x C x Pp floats)
+    int grid_frame, grid_gram;
+    float *U;              // stored subspace (C x npt tile blocks of k x TILE_P floats)
     uint8_t *labels;       // previous labels (Pp bytes)
     KState *ks;
     float *partials;
     unsigned int *counter;
-    void *frame_buf;       // staging of host frames
+    GridBar *bar;          // grid barrier of the frame kernel
+    uint32_t steps_since_rebase; // frame launches since the stored rows were last rebased
+    unsigned long long bar_base; // bar->count before the next launch
+    void *frame_buf;       // staging of host or unaligned frames (planes Pp entries apart)
     float *bg_buf;         // staging of the background for host outputs
     float *u_buf;          // staging of subspaces crossing the ABI from/to host memory
     int32_t *h_word;       // pinned scratch for small device -> host reads
@@ -111,7 +114,8 @@ int check_params(const prost_params *prm, DevParams *dp, std::string *why)
     if (dp) {
         memset(dp, 0, sizeof(*dp));
         dp->P = P;
-        dp->Pp = (P + 63) / 64 * 64;
+        dp->npt = (int)((P + TILE_P - 1) / TILE_P);
+        dp->Pp = (int64_t)dp->npt * TILE_P;
         dp->C = p.channels;
         dp->k = p.k;
         dp->n_cg = p.n_cg;
@@ -133,7 +137,7 @@ int check_params(const prost_params *prm, DevParams *dp, std::string *why)
 
 size_t frame_elem_bytes(const prost_params &p) { return p.frame_dtype == PROST_U8 ? 1 : 4; }
 
-// partial rows of the widest kernel: pass with M has k + k(k+1)/2 + 3 floats
+// partial rows of the widest reduction: a CG pass has k + k(k+1)/2 + 3 floats
 size_t partial_row(int k) { return (size_t)k + (size_t)k * (k + 1) / 2 + 3; }
 
 int grid_of(int occ, int sms, int64_t items)
@@ -151,6 +155,7 @@ void free_state(prost_handle *h)
     if (h->ks) cudaFree(h->ks);
     if (h->partials) cudaFree(h->partials);
     if (h->counter) cudaFree(h->counter);
+    if (h->bar) cudaFree(h->bar);
     if (h->frame_buf) cudaFree(h->frame_buf);
     if (h->bg_buf) cudaFree(h->bg_buf);
     if (h->u_buf) cudaFree(h->u_buf);
@@ -160,7 +165,7 @@ void free_state(prost_handle *h)
     for (int i = 0; i < CGMAX + 3; ++i) h->ev[i] = nullptr;
     h->U = nullptr; h->labels = nullptr; h->ks = nullptr; h->partials = nullptr;
     h->counter = nullptr; h->frame_buf = nullptr; h->bg_buf = nullptr; h->u_buf = nullptr;
-    h->h_word = nullptr;
+    h->h_word = nullptr; h->bar = nullptr;
 }
 
 int run_gram(prost_handle *h)
@@ -183,12 +188,16 @@ int read_status(prost_handle *h, int *status)
     return PROST_OK;
 }
 
+constexpr uint32_t REBASE_EVERY = 1024;
+
 struct StateHeader {
     char magic[8];
     uint32_t version;
     uint32_t header_bytes;
     prost_params prm;
     uint64_t u_bytes, ks_bytes, label_bytes;
+    uint32_t steps_since_rebase;
+    uint32_t pad;
 };
 
 } // namespace
@@ -222,8 +231,9 @@ int prost_state_bytes(const prost_params *prm, size_t *bytes)
     if (!bytes) return PROST_EINVAL;
     const int64_t m = m_of(*prm);
     size_t b = (size_t)prm->k * dp.C * dp.Pp * sizeof(float) + (size_t)dp.Pp + sizeof(KState) +
-               sizeof(unsigned int) + (size_t)4096 * partial_row(prm->k) * sizeof(float) +
-               (size_t)m * frame_elem_bytes(*prm);
+               sizeof(unsigned int) + sizeof(GridBar) + (size_t)4096 * partial_row(prm->k) * sizeof(float) +
+               (size_t)dp.C * dp.Pp * frame_elem_bytes(*prm);
+    (void)m;
     *bytes = b;
     return PROST_OK;
 }
@@ -248,7 +258,8 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     h->stream = (cudaStream_t)stream;
     h->U = nullptr; h->labels = nullptr; h->ks = nullptr; h->partials = nullptr;
     h->counter = nullptr; h->frame_buf = nullptr; h->bg_buf = nullptr; h->u_buf = nullptr;
-    h->h_word = nullptr;
+    h->h_word = nullptr; h->bar = nullptr; h->bar_base = 0;
+    h->steps_since_rebase = 0;
     h->timing = 0;
     h->timed_frames = 0;
     for (int i = 0; i < CGMAX + 3; ++i) h->ev[i] = nullptr;
@@ -271,31 +282,31 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     CKI(cudaGetDevice(&h->device));
     CKI(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
     const int fdt = prm->frame_dtype;
-    const int64_t groups = dp.Pp / ops->vw;
-    h->grid_pass_m = grid_of(ops->occupancy(0, fdt), h->num_sms, (int64_t)dp.C * groups);
-    h->grid_pass = grid_of(ops->occupancy(1, fdt), h->num_sms, (int64_t)dp.C * groups);
-    h->grid_ustep = grid_of(ops->occupancy(2, fdt), h->num_sms, dp.Pp / ops->vwu);
-    h->grid_gram = grid_of(ops->occupancy(3, fdt), h->num_sms, (int64_t)dp.C * groups);
-    int gmax = h->grid_pass_m;
-    if (h->grid_pass > gmax) gmax = h->grid_pass;
-    if (h->grid_ustep > gmax) gmax = h->grid_ustep;
+    const int occ = ops->frame_prepare(fdt);
+    if (occ < 1) { h->err = "the frame kernel does not fit on this device"; return bail(PROST_ECUDA); }
+    if (ops->tile != TILE_P) { h->err = "tile size mismatch"; return bail(PROST_ECUDA); }
+    int64_t gf = (int64_t)occ * h->num_sms;
+    if (gf > dp.npt) gf = dp.npt;  // every CTA gets at least one pixel tile
+    h->grid_frame = (int)(gf > 0 ? gf : 1);
+    h->grid_gram = grid_of(ops->gram_occupancy(), h->num_sms, (int64_t)dp.C * dp.npt * (TILE_P / ops->vw));
+    int gmax = 2 * h->grid_frame;
     if (h->grid_gram > gmax) gmax = h->grid_gram;
     h->partial_floats = (size_t)gmax * partial_row(prm->k);
 
-    const int64_t m = m_of(*prm);
     CKI(cudaMalloc(&h->U, (size_t)prm->k * dp.C * dp.Pp * sizeof(float)));
     CKI(cudaMalloc(&h->labels, (size_t)dp.Pp));
     CKI(cudaMalloc(&h->ks, sizeof(KState)));
     CKI(cudaMalloc(&h->partials, h->partial_floats * sizeof(float)));
     CKI(cudaMalloc(&h->counter, sizeof(unsigned int)));
-    CKI(cudaMalloc(&h->frame_buf, (size_t)m * frame_elem_bytes(*prm)));
+    CKI(cudaMalloc(&h->bar, sizeof(GridBar)));
+    CKI(cudaMalloc(&h->frame_buf, (size_t)dp.C * dp.Pp * frame_elem_bytes(*prm)));
     CKI(cudaMallocHost(&h->h_word, 64));
-    // the frame planes allow vector loads when every plane starts on a VW boundary
-    h->dp.vec = (dp.P % ops->vw) == 0 && (dp.P % ops->vwu) == 0 ? 1 : 0;
 
     CKI(cudaMemsetAsync(h->labels, 0, (size_t)dp.Pp, h->stream));
     CKI(cudaMemsetAsync(h->ks, 0, sizeof(KState), h->stream));
     CKI(cudaMemsetAsync(h->counter, 0, sizeof(unsigned int), h->stream));
+    CKI(cudaMemsetAsync(h->bar, 0, sizeof(GridBar), h->stream));
+    CKI(cudaMemsetAsync(h->frame_buf, 0, (size_t)dp.C * dp.Pp * frame_elem_bytes(*prm), h->stream));
     CKI(launch_init_gauss(h->U, h->dp, prm->seed, h->stream));
     rc = run_gram(h);
     if (rc) return bail(rc);
@@ -314,33 +325,22 @@ int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_
     if (!h) return PROST_EINVAL;
     if (!frame) return fail(h, PROST_EINVAL, "frame is NULL");
     DeviceGuard dg(h->device);
+    const DevParams &dp = h->dp;
     const int64_t m = m_of(h->prm);
     const int fdt = h->prm.frame_dtype;
-    const void *fptr = frame;
-    if (!on_device) {
-        CK(h, cudaMemcpyAsync(h->frame_buf, frame, (size_t)m * frame_elem_bytes(h->prm),
-                              cudaMemcpyHostToDevice, h->stream));
-        fptr = h->frame_buf;
-    }
-    // vector frame loads need planes on VW boundaries and an aligned base pointer
-    const uintptr_t fa = (uintptr_t)fptr;
     const size_t eb = frame_elem_bytes(h->prm);
-    PassArgs pa;
-    pa.U = h->U;
-    pa.frame = fptr;
-    pa.labels = h->labels;
-    pa.ks = h->ks;
-    pa.partials = h->partials;
-    pa.counter = h->counter;
-    pa.pad = 0;
-    pa.prm = h->dp;
-    pa.prm.vec = h->dp.vec && fa % (eb * (size_t)h->ops->vw) == 0;
-    if (h->timing) CK(h, cudaEventRecord(h->ev[0], h->stream));
-    for (int j = 0; j <= h->prm.n_cg; ++j) {
-        pa.pass = j;
-        const bool wm = j < h->prm.n_cg;
-        CK(h, h->ops->pass(pa, wm, fdt, wm ? h->grid_pass_m : h->grid_pass, h->stream));
-        if (h->timing) CK(h, cudaEventRecord(h->ev[j + 1], h->stream));
+    // The frame kernel copies frame planes with 16-byte bulk copies: a device
+    // frame whose planes start on 16-byte boundaries is read in place, any
+    // other frame is first staged into a buffer with a padded plane pitch.
+    const void *fptr = frame;
+    int64_t pitch = dp.P;
+    const bool direct = on_device && ((uintptr_t)frame % 16) == 0 && ((size_t)dp.P * eb) % 16 == 0;
+    if (!direct) {
+        CK(h, cudaMemcpy2DAsync(h->frame_buf, (size_t)dp.Pp * eb, frame, (size_t)dp.P * eb,
+                                (size_t)dp.P * eb, (size_t)dp.C,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+        fptr = h->frame_buf;
+        pitch = dp.Pp;
     }
     float *bg_dev = nullptr;
     if (background_out) {
@@ -351,25 +351,38 @@ int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_
             bg_dev = h->bg_buf;
         }
     }
-    UstepArgs ua;
-    ua.U = h->U;
-    ua.frame = fptr;
-    ua.labels = h->labels;
-    ua.mask_out = on_device ? mask_out : nullptr;
-    ua.bg_out = bg_dev;
-    ua.ks = h->ks;
-    ua.partials = h->partials;
-    ua.counter = h->counter;
-    ua.prm = h->dp;
-    ua.prm.vec = h->dp.vec && fa % (eb * (size_t)h->ops->vwu) == 0;
-    CK(h, h->ops->ustep(ua, fdt, h->grid_ustep, h->stream));
+    FrameArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.U = h->U;
+    fa.frame = fptr;
+    fa.labels = h->labels;
+    fa.mask_out = on_device ? mask_out : nullptr;
+    fa.bg_out = bg_dev;
+    fa.ks = h->ks;
+    fa.partials = h->partials;
+    fa.bar = h->bar;
+    fa.bar_base = h->bar_base;
+    fa.frame_pitch = pitch;
+    fa.row_stride = (int)partial_row(h->prm.k);
+    fa.prm = dp;
+    if (h->timing) CK(h, cudaEventRecord(h->ev[0], h->stream));
+    CK(h, h->ops->frame(fa, fdt, h->grid_frame, h->stream));
     if (h->timing) {
-        CK(h, cudaEventRecord(h->ev[h->prm.n_cg + 2], h->stream));
+        CK(h, cudaEventRecord(h->ev[1], h->stream));
         h->timed_frames += 1;
+    }
+    // arrivals per frame: one per CTA at each residual pass and at the end
+    h->bar_base += (unsigned long long)h->grid_frame * (unsigned long long)(h->prm.n_cg + 2);
+    // The frame kernel updates the stored rows in the stored basis (U = U_st T);
+    // every REBASE_EVERY frames the stored rows are moved onto the orthonormal
+    // representative so that the conditioning of U_st cannot drift.
+    if (++h->steps_since_rebase >= REBASE_EVERY) {
+        CK(h, h->ops->rebase(h->U, h->ks, dp, h->stream));
+        h->steps_since_rebase = 0;
     }
     if (on_device) return PROST_OK;
     if (mask_out)
-        CK(h, cudaMemcpyAsync(mask_out, h->labels, (size_t)h->dp.P, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaMemcpyAsync(mask_out, h->labels, (size_t)dp.P, cudaMemcpyDeviceToHost, h->stream));
     if (background_out)
         CK(h, cudaMemcpyAsync(background_out, h->bg_buf, (size_t)m * sizeof(float),
                               cudaMemcpyDeviceToHost, h->stream));
@@ -387,7 +400,13 @@ int prost_sync(prost_handle *h)
     CK(h, cudaMemsetAsync(&h->ks->err_flags, 0, sizeof(uint32_t), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     const uint32_t f = (uint32_t)h->h_word[0];
-    if (f & ERR_TIMEOUT) return PROST_ETIMEOUT;
+    if (f & ERR_TIMEOUT) {
+        // an aborted frame leaves the grid barrier count unknown: start it afresh
+        CK(h, cudaMemsetAsync(h->bar, 0, sizeof(GridBar), h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        h->bar_base = 0;
+        return PROST_ETIMEOUT;
+    }
     if (f & ERR_NOTSPD) return PROST_ENOTSPD;
     if (f & ERR_BADFRAME) return PROST_EBADFRAME;
     return PROST_OK;
@@ -430,6 +449,7 @@ int prost_set_subspace(prost_handle *h, const float *U, const double *y, int on_
         src = h->u_buf;
     }
     CK(h, launch_import_u(src, h->U, h->dp, h->stream));
+    h->steps_since_rebase = 0;
     if (y)
         CK(h, cudaMemcpyAsync(h->ks->y, y, (size_t)k * sizeof(double),
                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
@@ -506,8 +526,7 @@ int prost_get_state(prost_handle *h, void *buf, size_t *len)
     if (!h || !len) return PROST_EINVAL;
     DeviceGuard dg(h->device);
     const DevParams &dp = h->dp;
-    const size_t plane = (size_t)dp.P * sizeof(float);
-    const size_t u_bytes = plane * dp.C * dp.k;
+    const size_t u_bytes = (size_t)dp.k * dp.C * dp.Pp * sizeof(float); // the stored layout as is
     const size_t need = sizeof(StateHeader) + u_bytes + sizeof(KState) + (size_t)dp.P;
     if (!buf) { *len = need; return PROST_OK; }
     if (*len < need) return fail(h, PROST_EINVAL, "buffer too small");
@@ -520,13 +539,12 @@ int prost_get_state(prost_handle *h, void *buf, size_t *len)
     hd.u_bytes = u_bytes;
     hd.ks_bytes = sizeof(KState);
     hd.label_bytes = (uint64_t)dp.P;
+    hd.steps_since_rebase = h->steps_since_rebase;
     char *b = (char *)buf;
     memcpy(b, &hd, sizeof(hd));
     char *pu = b + sizeof(hd);
     CK(h, cudaStreamSynchronize(h->stream));
-    // planes of the stored subspace without their padding
-    CK(h, cudaMemcpy2D(pu, plane, h->U, (size_t)dp.Pp * sizeof(float), plane, (size_t)dp.C * dp.k,
-                       cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(pu, h->U, u_bytes, cudaMemcpyDeviceToHost));
     CK(h, cudaMemcpy(pu + u_bytes, h->ks, sizeof(KState), cudaMemcpyDeviceToHost));
     CK(h, cudaMemcpy(pu + u_bytes + sizeof(KState), h->labels, (size_t)dp.P, cudaMemcpyDeviceToHost));
     *len = need;
@@ -538,8 +556,7 @@ int prost_set_state(prost_handle *h, const void *buf, size_t len)
     if (!h || !buf) return PROST_EINVAL;
     DeviceGuard dg(h->device);
     const DevParams &dp = h->dp;
-    const size_t plane = (size_t)dp.P * sizeof(float);
-    const size_t u_bytes = plane * dp.C * dp.k;
+    const size_t u_bytes = (size_t)dp.k * dp.C * dp.Pp * sizeof(float);
     const size_t need = sizeof(StateHeader) + u_bytes + sizeof(KState) + (size_t)dp.P;
     if (len < sizeof(StateHeader)) return fail(h, PROST_EINVAL, "state buffer too short");
     StateHeader hd;
@@ -554,12 +571,11 @@ int prost_set_state(prost_handle *h, const void *buf, size_t len)
         return fail(h, PROST_EINVAL, "state buffer sizes do not match");
     const char *pu = (const char *)buf + sizeof(hd);
     CK(h, cudaStreamSynchronize(h->stream));
-    CK(h, cudaMemset(h->U, 0, (size_t)dp.k * dp.C * dp.Pp * sizeof(float)));
-    CK(h, cudaMemcpy2D(h->U, (size_t)dp.Pp * sizeof(float), pu, plane, plane, (size_t)dp.C * dp.k,
-                       cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(h->U, pu, u_bytes, cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(h->ks, pu + u_bytes, sizeof(KState), cudaMemcpyHostToDevice));
     CK(h, cudaMemset(h->labels, 0, (size_t)dp.Pp));
     CK(h, cudaMemcpy(h->labels, pu + u_bytes + sizeof(KState), (size_t)dp.P, cudaMemcpyHostToDevice));
+    h->steps_since_rebase = hd.steps_since_rebase;
     return PROST_OK;
 }
 
@@ -580,8 +596,10 @@ int prost_get_timing(prost_handle *h, float *ms, int *n)
     if (!h->timing || h->timed_frames == 0) return fail(h, PROST_EINVAL, "no traced frame");
     DeviceGuard dg(h->device);
     const int nl = h->prm.n_cg + 2;
-    CK(h, cudaEventSynchronize(h->ev[nl]));
-    for (int j = 0; j < nl; ++j) CK(h, cudaEventElapsedTime(&ms[j], h->ev[j], h->ev[j + 1]));
+    CK(h, cudaEventSynchronize(h->ev[1]));
+    uint64_t ts[CGMAX + 3];
+    CK(h, cudaMemcpy(ts, h->ks->phase_ts, sizeof(uint64_t) * (size_t)(nl + 1), cudaMemcpyDeviceToHost));
+    for (int j = 0; j < nl; ++j) ms[j] = (float)((double)(ts[j + 1] - ts[j]) * 1e-6);
     *n = nl;
     return PROST_OK;
 }

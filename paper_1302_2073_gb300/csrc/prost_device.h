@@ -9,7 +9,8 @@ namespace prost {
 
 constexpr int KMAX = 16;     // largest subspace dimension with a compiled kernel set
 constexpr int CGMAX = 32;    // largest number of CG iterations per frame
-constexpr int THREADS = 256; // threads per CTA of every per-pixel kernel
+constexpr int THREADS = 256; // threads per CTA of the Gram and layout kernels
+constexpr int TILE_P = 224;  // pixels per tile of the stored subspace (16-byte multiple for uint8)
 
 // Device-resident k-space state of one stream.  The stored subspace U_st is
 // kept in float32; its orthonormal representative is U = U_st T with
@@ -43,48 +44,42 @@ struct KState {
     double pi_norm, y_norm, sigma, t, theta, orth_err;
     int32_t updated, pad0;
     int64_t n_fg;
+    // %globaltimer (ns): start of the frame, end of each residual pass, end of the frame
+    uint64_t phase_ts[CGMAX + 3];
+    // %globaltimer (ns), CTA 0: CG pass 1 tiles done, partial row written, grid
+    // barrier passed, all rows reduced, CG step done; update-pass rows done,
+    // partial row written, arrived; last CTA: rows reduced
+    uint64_t sub_ts[9];
 };
 
 constexpr uint32_t ERR_BADFRAME = 1u, ERR_NOTSPD = 2u, ERR_TIMEOUT = 4u;
 
 // Parameters as the kernels use them.
+// Stored subspace layout (tile-blocked): each channel plane is cut into npt
+// tiles of TILE_P pixels; tile (c, pt) is one contiguous block of k columns of
+// TILE_P floats, so entry (e = c*P + q, j) sits at
+//   ((c*npt + q/TILE_P)*k + j)*TILE_P + q%TILE_P.
+// Pixels q in [P, Pp) with Pp = npt*TILE_P are padding rows holding zeros.
 struct DevParams {
     int64_t P;        // pixels per channel plane
-    int64_t Pp;       // padded plane stride of the stored subspace (multiple of 64)
+    int64_t Pp;       // padded plane length npt*TILE_P (also the pitch of staged frames)
     int C;            // channels
     int k;            // subspace dimension
     int n_cg;         // CG iterations per frame
     int mask_pre;     // labels from the subspace before Step 2
-    int vec;          // frame planes allow vector loads
+    int npt;          // tiles per channel plane
     int pad;
     float p, mu, delta, omega, in_scale, in_offset, e; // e = p/2 - 1
     float pad2;
     double pd, t_init, t_min, tau;
 };
 
-struct PassArgs {
-    const float *U;          // stored subspace, column j of channel c at U + (j*C + c)*Pp
-    const void *frame;       // C x P entries (uint8 or float)
-    const uint8_t *labels;   // previous labels, Pp bytes
-    KState *ks;
-    float *partials;         // gridDim.x rows of per-CTA sums
-    unsigned int *counter;   // arrival counter of the last-CTA reduction (0 between launches)
-    int pass;                // CG iterate index 0..n_cg
-    int pad;
-    DevParams prm;
-};
-
-struct UstepArgs {
-    float *U;
-    const void *frame;
-    uint8_t *labels;         // in: previous labels (weights); out: this frame's labels
-    uint8_t *mask_out;       // optional copy of the labels (device, P bytes)
-    float *bg_out;           // optional background U y + in_offset (device, m floats)
-    KState *ks;
-    float *partials;
-    unsigned int *counter;
-    DevParams prm;
-};
+// offset of entry (channel c, pixel q, column j) of the stored subspace
+__host__ __device__ __forceinline__ int64_t u_off(const DevParams &prm, int c, int64_t q, int j)
+{
+    const int64_t pt = q / TILE_P;
+    return (((int64_t)c * prm.npt + pt) * prm.k + j) * TILE_P + (q - pt * TILE_P);
+}
 
 struct GramArgs {
     const float *U;
@@ -94,17 +89,41 @@ struct GramArgs {
     DevParams prm;
 };
 
+// Grid barrier of the frame kernel: the arrival count only grows.
+struct GridBar {
+    unsigned long long count; // arrivals since the handle was created
+    int abort;                // set by a CTA whose wait gave up
+    int pad;
+};
+
+struct FrameArgs {
+    float *U;                 // stored subspace (tile-blocked, see DevParams)
+    const void *frame;        // channel planes frame_pitch entries apart (uint8 or float)
+    uint8_t *labels;          // in: previous labels (weights); out: this frame's labels
+    uint8_t *mask_out;        // optional copy of the labels (device, P bytes)
+    float *bg_out;            // optional background U y + in_offset (device, m floats)
+    KState *ks;
+    float *partials;          // 2 x gridDim.x rows of row_stride floats
+    GridBar *bar;
+    unsigned long long bar_base; // bar->count at launch
+    int64_t frame_pitch;
+    int row_stride;
+    int pad;
+    DevParams prm;
+};
+
 // Host-side entry points of one compiled kernel set (one per k).
 struct KernelOps {
-    cudaError_t (*pass)(const PassArgs &, bool with_m, int frame_dtype, int grid, cudaStream_t);
-    cudaError_t (*ustep)(const UstepArgs &, int frame_dtype, int grid, cudaStream_t);
+    cudaError_t (*frame)(const FrameArgs &, int frame_dtype, int grid, cudaStream_t);
+    int (*frame_prepare)(int frame_dtype); // resident frame-kernel CTAs per SM (0: cannot run)
     cudaError_t (*gram)(const GramArgs &, int grid, cudaStream_t);
     cudaError_t (*export_u)(const float *U, const KState *ks, float *out, DevParams prm,
                             cudaStream_t);
-    // resident CTAs per SM of kernel kind (0 pass+M, 1 pass, 2 ustep, 3 gram)
-    int (*occupancy)(int kind, int frame_dtype);
-    int vw;  // pixels per thread of the residual passes and the Gram kernel
-    int vwu; // pixels per thread of the update pass
+    int (*gram_occupancy)();
+    cudaError_t (*rebase)(float *U, KState *ks, DevParams prm, cudaStream_t);
+    int vw;        // pixels per thread of the Gram kernel
+    int tile;      // pixels per tile of the frame kernel
+    int frame_threads;
 };
 
 // kernels without a k template
@@ -112,6 +131,8 @@ cudaError_t launch_init_gauss(float *U, DevParams prm, uint64_t seed, cudaStream
 cudaError_t launch_import_u(const float *Urow, float *U, DevParams prm, cudaStream_t s);
 cudaError_t launch_import_labels(const uint8_t *src, uint8_t *labels, DevParams prm,
                                  cudaStream_t s);
+// after a rebase: R = T = I and the stored-row coefficients equal y
+cudaError_t launch_reset_fold(KState *ks, DevParams prm, cudaStream_t s);
 
 // per-k kernel sets, filled by the instantiation units
 void register_ops_k01_04(const KernelOps **table);

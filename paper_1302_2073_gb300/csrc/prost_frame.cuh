@@ -1,0 +1,741 @@
+// One persistent, cooperative launch per frame of pROST's update
+// (arXiv:1302.2073, Section 3.3) for sm_103a.
+//
+// Every CTA (one per SM, 16 warps) owns a fixed range of the stored
+// subspace's tiles for the residual passes and a fixed range of pixel tiles
+// for the update pass.  Each warp streams its rows with coalesced 8-byte loads
+// straight into registers: the subspace (36.9 MB at 640x480x3, k = 10) stays
+// resident in the 126 MB L2 across the n_cg + 2 passes of a frame, and from
+// L2 many threads with loads in flight deliver about twice the rate of a
+// single-thread bulk-copy ring.
+//
+// Phases:
+//   residual pass j = 0..n_cg: per row r = x - U y_j, the cost, U^T eta and
+//     (j < n_cg) U^T diag(c) U; CTA partial row -> grid barrier -> every CTA
+//     sums all partial rows in the same fixed order and runs the same k-space
+//     step (PR+ CG step, or for j = n_cg the rank-one SVD and the geodesic
+//     angle of Step 2), so all CTAs hold identical k-space state without a
+//     second barrier.
+//   update pass: geodesic update of every row (written back), labels and
+//     weights of Step 3 (max over channels), optional background, Gram of the
+//     new subspace; the last CTA to arrive runs the FP64 Cholesky-QR that is
+//     folded into the next frame and writes the k-space state back.
+//
+// Every wait is bounded (about one second of SM clock): a grid barrier that
+// does not complete sets a global abort flag and PROST_ETIMEOUT in the state
+// and the CTAs return.  The grid barrier counter only grows; the host passes
+// the value it must hold at launch, and a launch that finds another value (a
+// previous launch aborted) does nothing but raise the error.
+#pragma once
+
+#include "prost_kernels.cuh"
+
+namespace prost {
+
+template <int K> struct FCfg {
+    // 16 warps: at most 4 per SM sub-partition, so each thread may hold 128
+    // registers; one CTA per SM.
+    static constexpr int THREADS = 512;
+    static constexpr int NW = THREADS / 32;
+    static constexpr int TP = TILE_P;            // pixels per tile
+    static constexpr int RW = 2;                 // rows per thread per item (8-byte loads)
+    static constexpr int IPT = TP / RW;          // items per tile
+    static constexpr int NM = K * (K + 1) / 2;
+    static constexpr int NVR = K + NM + 3;       // CG pass partial row
+    static constexpr int NVF = K + 3;            // final pass partial row
+    static constexpr int NVU = NM + 1;           // update pass partial row
+    static constexpr int NPR = (NVR + 31) / 32 * 32;
+    static constexpr int NPF = (NVF + 31) / 32 * 32;
+    static constexpr int NPU = (NVU + 31) / 32 * 32;
+    static constexpr int NPMAX = NPR > NPU ? NPR : NPU;
+};
+static_assert(TILE_P % 2 == 0, "rows are read in pairs");
+
+constexpr long long WAIT_LIMIT = 2000000000ll; // SM clock cycles (about 1 s)
+
+template <int N> __device__ __forceinline__ void cons_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// two consecutive entries (RW = 2) of a frame plane or label row
+__device__ __forceinline__ void ld2(const uint8_t *p, bool pair, int nvalid, float (&o)[2])
+{
+    if (pair) {
+        const uchar2 v = __ldg(reinterpret_cast<const uchar2 *>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+    } else {
+        o[0] = nvalid > 0 ? (float)__ldg(p) : 0.f;
+        o[1] = nvalid > 1 ? (float)__ldg(p + 1) : 0.f;
+    }
+}
+__device__ __forceinline__ void ld2(const float *p, bool pair, int nvalid, float (&o)[2])
+{
+    if (pair) {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        o[0] = v.x;
+        o[1] = v.y;
+    } else {
+        o[0] = nvalid > 0 ? __ldg(p) : 0.f;
+        o[1] = nvalid > 1 ? __ldg(p + 1) : 0.f;
+    }
+}
+
+// ---- shared k-space state (identical copy in every CTA) -----------------------
+
+template <int K> struct SKState {
+    double y[K];       // coefficients in the orthonormal basis U = U_st T (FP64 storage)
+    float gprev[K], d[K];
+    float yf[K];       // T y: coefficients of the stored rows
+    float tv[K], tg[K];// T v and T g: dots of stored rows with v and g (Step 2)
+    float w[K];        // R^T v: the update direction in the stored basis
+    float Tf[K * K];   // T = R^{-1}, row-major upper triangular
+    float Rf[K * K];   // R, row-major upper triangular
+    float cm1, snp, yn;
+    int skip;          // frame rejected (non-finite entry)
+    int err;           // a grid barrier gave up
+    int last;          // this CTA arrived last at the end of the frame
+    int pad;
+    int64_t frame_index;
+};
+
+// Sum of all CTAs' partial rows in a fixed order (Kahan-compensated FP32),
+// by the consumer threads; identical in every CTA.
+template <int NV, int NCONS>
+__device__ __forceinline__ void reduce_rows(const float *rows, int nrows, int stride, float *tot, float *scr)
+{
+    constexpr int NG = NCONS / NV;
+    constexpr int MAXR = 48; // rows per thread held in flight at once
+    const int t = threadIdx.x, comp = t % NV, grp = t / NV;
+    if (grp < NG) {
+        float s = 0.f, c = 0.f;
+        for (int b0 = grp; b0 < nrows; b0 += MAXR * NG) {
+            float v[MAXR];
+#pragma unroll
+            for (int q = 0; q < MAXR; ++q) {
+                const int b = b0 + q * NG;
+                v[q] = b < nrows ? __ldcg(rows + (size_t)b * stride + comp) : 0.f;
+            }
+#pragma unroll
+            for (int q = 0; q < MAXR; ++q) {
+                const float yk = v[q] - c, tk = s + yk;
+                c = (tk - s) - yk;
+                s = tk;
+            }
+        }
+        scr[grp * NV + comp] = s;
+    }
+    cons_sync<NCONS>();
+    if (t < NV) {
+        float s = 0.f, c = 0.f;
+        for (int g2 = 0; g2 < NG; ++g2) {
+            const float yk = scr[g2 * NV + t] - c, tk = s + yk;
+            c = (tk - s) - yk;
+            s = tk;
+        }
+        tot[t] = s;
+    }
+    cons_sync<NCONS>();
+}
+
+// CTA sum of N per-thread values (all threads), first nv written to out
+template <int N, int NCW>
+__device__ __forceinline__ void cons_partials(float (&v)[N], int nv, float *out, float *sred)
+{
+    warp_split_reduce<N>(v);
+    constexpr int PER = N / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int s = 0; s < PER; ++s) sred[w * N + lane * PER + s] = v[s];
+    cons_sync<NCW * 32>();
+    for (int i = threadIdx.x; i < nv; i += NCW * 32) {
+        float a = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < NCW; ++ww) a += sred[ww * N + i];
+        out[i] = a;
+    }
+    __threadfence();
+}
+
+// Grid barrier: arrive, wait (bounded) until all CTAs arrived.
+template <int NCONS>
+__device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target, int *s_err, KState *ks)
+{
+    cons_sync<NCONS>();
+    if (threadIdx.x == 0) {
+        int ok = *s_err == 0;
+        if (ok) {
+            atomicAdd(&gb->count, 1ull);
+            const long long t0 = clock64();
+            unsigned it = 0;
+            while (ld_acquire_u64(&gb->count) < target) {
+                if ((++it & 15u) == 0) {
+                    if (*(volatile int *)&gb->abort || clock64() - t0 > WAIT_LIMIT) {
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        if (!ok) {
+            atomicExch(&gb->abort, 1);
+            atomicOr(&ks->err_flags, ERR_TIMEOUT);
+            *s_err = 1;
+        }
+        __threadfence();
+    }
+    cons_sync<NCONS>();
+    return *(volatile int *)s_err == 0;
+}
+
+// ---- k-space steps on the shared copy (one warp) ---------------------------------
+
+__device__ __forceinline__ float wsumf(float v)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+    return v;
+}
+
+// CG bookkeeping at iterate `pass` from the reduced sums tot:
+//   WM:  tot = [g_st (K) | M_st packed (K(K+1)/2) | f | |eta|^2 | #non-finite]
+//   !WM: tot = [g_st (K) | f | |eta|^2 | #non-finite]
+// g_st = U_st^T eta and M_st = U_st^T diag(c) U_st refer to the stored rows;
+// with U = U_st T the gradient is g = T^T g_st and d^T M d = (T d)^T M_st (T d).
+// The k-vector algebra is FP32 (k <= 16 terms per dot product); y is kept in
+// FP64 and the step size t (an exponential of the frame counter) is FP64.
+// GB300's FP64 pipe is narrow and long-latency, so FP64 stays off the chains.
+// CTA 0 also records the statistics in the global state.
+template <int K, bool WM>
+__device__ void kspace_cg(SKState<K> &sk, const DevParams &prm, const float *tot, int pass, KState *gks,
+                          bool stats)
+{
+    constexpr int NM = WM ? K * (K + 1) / 2 : 0;
+    const int l = threadIdx.x;
+    const bool act = l < K;
+    const float f = tot[K + NM], ee = tot[K + NM + 1], nbad = tot[K + NM + 2];
+    if (pass == 0 && nbad > 0.f) {
+        if (l == 0) sk.skip = 1;
+        __syncwarp();
+    }
+    float gl = 0.f;
+    if (act)
+        for (int i = 0; i <= l; ++i) gl = fmaf(sk.Tf[i * K + l], tot[i], gl);
+    const float gsq = wsumf(act ? gl * gl : 0.f);
+    float beta = 0.f, dl;
+    if (pass == 0) {
+        dl = act ? -gl : 0.f;
+    } else {
+        const float gp = act ? sk.gprev[l] : 0.f;
+        const float ggp = wsumf(gp * gp);
+        const float num = wsumf(act ? gl * (gl - gp) : 0.f);
+        beta = ggp > 0.f ? fmaxf(0.f, num / ggp) : 0.f;
+        dl = act ? fmaf(beta, sk.d[l], -gl) : 0.f;
+    }
+    if (stats && l == 0) {
+        gks->cost[pass] = f;
+        gks->gnorm[pass] = sqrtf(gsq);
+        gks->beta[pass] = beta;
+    }
+    if (sk.skip) return;
+    if (pass < prm.n_cg) {
+        float dst = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const float di = __shfl_sync(FULL, dl, i);
+            if (act && i >= l) dst = fmaf(sk.Tf[l * K + i], di, dst);
+        }
+        float md = 0.f;
+        if constexpr (WM) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const float si = __shfl_sync(FULL, dst, i);
+                if (act) md = fmaf(tot[K + (l <= i ? tri<K>(l, i) : tri<K>(i, l))], si, md);
+            }
+        }
+        const float den = prm.p * wsumf(act ? dst * md : 0.f);
+        const float dg = wsumf(act ? dl * gl : 0.f);
+        const float alpha = den > 0.f ? -dg / den : 0.f;
+        const double yl = act ? sk.y[l] + (double)alpha * (double)dl : 0.0;
+        const float ylf = (float)yl;
+        float ys = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const float yi = __shfl_sync(FULL, ylf, i);
+            if (act && i >= l) ys = fmaf(sk.Tf[l * K + i], yi, ys);
+        }
+        if (act) {
+            sk.y[l] = yl;
+            sk.d[l] = dl;
+            sk.gprev[l] = gl;
+            sk.yf[l] = ys;
+        }
+        if (stats && l == 0) gks->alpha[pass] = alpha;
+    } else {
+        const float yl = act ? (float)sk.y[l] : 0.f;
+        const float yn = sqrtf(wsumf(yl * yl));
+        const float pin2 = ee - gsq;
+        const float pin = pin2 > 0.f ? sqrtf(pin2) : 0.f;
+        const bool upd = yn > 0.f && pin > 0.f;
+        double t = 0.0;
+        if (l == 0) t = fmax(exp(-prm.tau * (double)sk.frame_index) * prm.t_init, prm.t_min);
+        t = __shfl_sync(FULL, t, 0);
+        const float sigma = pin * yn;
+        const float theta = sigma * (float)t;
+        const float sh = sinf(0.5f * theta);
+        // the update pass works on the stored rows u_st (u = T^T u_st): it needs
+        // T v and T g for the dots and w = R^T v, since u_st + gamma R^T v is
+        // the stored row of u + gamma v
+        const float vl = (act && upd) ? yl / yn : 0.f;
+        float tv = 0.f, tg = 0.f, wl = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            const float vi = __shfl_sync(FULL, vl, i);
+            const float gi = __shfl_sync(FULL, gl, i);
+            if (act && i >= l) {
+                tv = fmaf(sk.Tf[l * K + i], vi, tv);
+                tg = fmaf(sk.Tf[l * K + i], gi, tg);
+            }
+            if (act && i <= l) wl = fmaf(sk.Rf[i * K + l], vi, wl);
+        }
+        if (act) {
+            sk.tv[l] = tv;
+            sk.tg[l] = tg;
+            sk.w[l] = wl;
+        }
+        if (l == 0) {
+            sk.cm1 = upd ? -2.f * sh * sh : 0.f;
+            sk.snp = upd ? sinf(theta) / pin : 0.f;
+            sk.yn = yn;
+            if (stats) {
+                gks->pi_norm = pin;
+                gks->y_norm = yn;
+                gks->sigma = sigma;
+                gks->t = t;
+                gks->theta = upd ? theta : 0.f;
+                gks->updated = upd ? 1 : 0;
+                gks->n_cg_done = prm.n_cg;
+            }
+        }
+    }
+}
+
+// 1/sqrt(d) in FP64: a float seed refined by two Newton-Raphson steps for the
+// reciprocal square root, y <- y (3 - d y^2) / 2 (quadratic convergence from
+// float accuracy).  Replaces FP64 sqrt and division, which are long software
+// sequences on GB300's narrow FP64 pipe.
+__device__ __forceinline__ double rsqrt_nr(double d)
+{
+    double y = (double)rsqrtf((float)d);
+    y = y * fma(-0.5 * d * y, y, 1.5);
+    y = y * fma(-0.5 * d * y, y, 1.5);
+    return y;
+}
+
+// End of frame (last CTA, warp 0): Cholesky-QR of the new stored rows from
+// their Gram matrix G in FP64 (G = R'^T R', T' = R'^{-1}); the orthonormal
+// basis becomes U_st T', and y (coefficients of U_st T_old) becomes R' T_old y.
+// Right-looking over the k^2 entries, lane-parallel; sW is k x k scratch.
+template <int K>
+__device__ void finish_frame(const SKState<K> &sk, KState *ks, const float *G, float n_fg, double *sR,
+                             double *sT, double *sW)
+{
+    const int lane = threadIdx.x;
+    if (sk.skip) {
+        if (lane == 0) {
+            ks->err_flags |= ERR_BADFRAME;
+            ks->last_status = -4; // PROST_EBADFRAME
+            ks->bad_frames += 1;
+        }
+        return;
+    }
+    double oerr = 0.0;
+    for (int q = lane; q < K * K; q += 32) {
+        const int i = q / K, l = q - i * K;
+        const double gv = (double)(i <= l ? G[tri<K>(i, l)] : G[tri<K>(l, i)]);
+        sW[q] = gv;
+        sR[q] = 0.0;
+        oerr = fmax(oerr, fabs(gv - (i == l ? 1.0 : 0.0)));
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) oerr = fmax(oerr, __shfl_xor_sync(FULL, oerr, off));
+    __syncwarp();
+    double inv[K];
+    bool ok = true;
+    for (int a = 0; a < K; ++a) {
+        const double d = sW[a * K + a];
+        if (!(d > 0.0)) {
+            ok = false;
+            break;
+        }
+        const double ri = rsqrt_nr(d);
+        inv[a] = ri;
+        for (int l = lane; l < K; l += 32)
+            if (l >= a) sR[a * K + l] = l == a ? d * ri : sW[a * K + l] * ri;
+        __syncwarp();
+        for (int q = lane; q < K * K; q += 32) {
+            const int i = q / K, l = q - i * K;
+            if (i > a && l >= i) sW[q] = fma(-sR[a * K + i], sR[a * K + l], sW[q]);
+        }
+        __syncwarp();
+    }
+    if (!ok) {
+        for (int q = lane; q < K * K; q += 32) sR[q] = sT[q] = (q / K == q % K) ? 1.0 : 0.0;
+    } else {
+        for (int q = lane; q < K * K; q += 32) sW[q] = (q / K == q % K) ? 1.0 : 0.0;
+        __syncwarp();
+        for (int r = K - 1; r >= 0; --r) {
+            for (int l = lane; l < K; l += 32) sT[r * K + l] = sW[r * K + l] * inv[r];
+            __syncwarp();
+            for (int q = lane; q < K * K; q += 32) {
+                const int i = q / K, l = q - i * K;
+                if (i < r) sW[q] = fma(-sR[i * K + r], sT[r * K + l], sW[q]);
+            }
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+    // y' = R' (T_old y): T_old y in FP64 from the state of the finished frame
+    const bool act = lane < K;
+    double ty = 0.0;
+    if (act)
+        for (int q = lane; q < K; ++q) ty = fma(ks->T[lane * KMAX + q], sk.y[q], ty);
+    double ynew = 0.0;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const double tq = __shfl_sync(FULL, ty, q);
+        if (act && q >= lane) ynew = fma(sR[lane * K + q], tq, ynew);
+    }
+    __syncwarp();
+    for (int q = lane; q < K * K; q += 32) {
+        const int i = q / K, l = q - i * K;
+        ks->R[i * KMAX + l] = sR[q];
+        ks->T[i * KMAX + l] = sT[q];
+        ks->Tf[q] = (float)sT[q];
+    }
+    if (act) {
+        ks->y[lane] = ynew;
+        ks->yf[lane] = (float)ty;
+    }
+    if (lane == 0) {
+        ks->orth_err = oerr;
+        if (!ok) ks->err_flags |= ERR_NOTSPD;
+        ks->n_fg = (int64_t)n_fg;
+        ks->frame_index = sk.frame_index + 1;
+        ks->last_status = ok ? 0 : -6; // PROST_ENOTSPD
+        ks->skip = 0;
+    }
+}
+
+// ---- the frame kernel --------------------------------------------------------
+
+struct FrameTiles {
+    int nres, r0, nupt, u0;
+    __device__ FrameTiles(const DevParams &prm, int G, int b)
+    {
+        const long long NT = (long long)prm.C * prm.npt;
+        r0 = (int)(NT * b / G);
+        nres = (int)(NT * (b + 1) / G) - r0;
+        u0 = (int)((long long)prm.npt * b / G);
+        nupt = (int)((long long)prm.npt * (b + 1) / G) - u0;
+    }
+};
+
+// One residual pass over this CTA's tiles: per-thread sums of the cost, U^T eta,
+// |eta|^2, the non-finite count and (WM) U^T diag(c) U.
+template <int K, typename FT, bool WM>
+__device__ __forceinline__ void residual_pass(const FrameArgs &a, const FrameTiles &tl, const SKState<K> &sk,
+                                              float (&acc)[WM ? FCfg<K>::NPR : FCfg<K>::NPF])
+{
+    using F = FCfg<K>;
+    constexpr int TP = F::TP, RW = F::RW, IPT = F::IPT;
+    constexpr int NM = WM ? F::NM : 0;
+    const DevParams &prm = a.prm;
+    float y[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) y[j] = sk.yf[j];
+    const float mu = prm.mu, e = prm.e, pw = prm.p, om = prm.omega;
+    const float sc = prm.in_scale, of = prm.in_offset;
+    const FT *frame = static_cast<const FT *>(a.frame);
+    const int nitems = tl.nres * IPT;
+    for (int it = threadIdx.x; it < nitems; it += F::THREADS) {
+        const int ti = tl.r0 + it / IPT;
+        const int rp = it - (it / IPT) * IPT;
+        const int c = ti / prm.npt;
+        const int64_t p = (int64_t)(ti - c * prm.npt) * TP + rp * RW;
+        const int nvalid = prm.P - p < RW ? (int)(prm.P - p) : RW;
+        const float *ub = a.U + (int64_t)ti * K * TP + rp * RW;
+        float u[K][RW];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const float2 v = __ldcg(reinterpret_cast<const float2 *>(ub + j * TP));
+            u[j][0] = v.x;
+            u[j][1] = v.y;
+        }
+        float xv[RW], lb[RW];
+        ld2(frame + (int64_t)c * a.frame_pitch + p, nvalid == RW, nvalid, xv);
+        ld2(a.labels + p, true, RW, lb);
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const bool valid = r < nvalid;
+            float uy = 0.f;
+#pragma unroll
+            for (int j = 0; j < K; ++j) uy = fmaf(u[j][r], y[j], uy);
+            if constexpr (sizeof(FT) == 4) {
+                if (valid && !isfinite(xv[r])) acc[K + NM + 2] += 1.f;
+            }
+            const float res = valid ? fmaf(xv[r], sc, -of) - uy : 0.f;
+            const float z = fmaf(res, res, mu);
+            const float tz = __powf(z, e);
+            const float wv = valid ? (lb[r] != 0.f ? om : 1.f) : 0.f;
+            const float cw = wv * tz;
+            acc[K + NM] = fmaf(cw, z, acc[K + NM]);
+            const float eta = -pw * cw * res;
+            acc[K + NM + 1] = fmaf(eta, eta, acc[K + NM + 1]);
+#pragma unroll
+            for (int j = 0; j < K; ++j) acc[j] = fmaf(eta, u[j][r], acc[j]);
+            if constexpr (WM) {
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const float cu = cw * u[j][r];
+#pragma unroll
+                    for (int l2 = j; l2 < K; ++l2) acc[K + tri<K>(j, l2)] = fmaf(cu, u[l2][r], acc[K + tri<K>(j, l2)]);
+                }
+            }
+        }
+    }
+}
+
+template <int K, typename FT>
+__global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a)
+{
+    using F = FCfg<K>;
+    constexpr int TP = F::TP, RW = F::RW, IPT = F::IPT, NT = F::THREADS, NW = F::NW;
+    constexpr int NM = F::NM;
+    __shared__ float sred[NW * F::NPMAX];
+    __shared__ float tot[F::NVR > F::NVU ? F::NVR : F::NVU];
+    __shared__ float rscr[NT];
+    __shared__ double sR[K * K], sT[K * K], sW[K * K];
+    __shared__ SKState<K> sk;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const DevParams &prm = a.prm;
+    const int G = gridDim.x, b = blockIdx.x;
+    const FrameTiles tl(prm, G, b);
+
+    if (tid == 0) {
+        const unsigned long long c0 = ld_acquire_u64(&a.bar->count);
+        sk.err = (c0 < a.bar_base || c0 >= a.bar_base + (unsigned long long)G) ? 1 : 0;
+        sk.skip = 0;
+        sk.last = 0;
+        sk.frame_index = a.ks->frame_index;
+    }
+    for (int i = tid; i < K * K; i += NT) {
+        sk.Tf[i] = a.ks->Tf[i];
+        sk.Rf[i] = (float)a.ks->R[(i / K) * KMAX + (i % K)];
+    }
+    if (tid < K) {
+        sk.y[tid] = a.ks->y[tid];
+        sk.yf[tid] = a.ks->yf[tid];
+    }
+    __syncthreads();
+    if (sk.err) {
+        if (tid == 0 && b == 0) atomicOr(&a.ks->err_flags, ERR_TIMEOUT);
+        return;
+    }
+
+    const bool stats = b == 0;
+    int buf = 0;
+    unsigned long long target = a.bar_base;
+    if (stats && tid == 0) a.ks->phase_ts[0] = global_ns();
+
+    for (int pass = 0; pass <= prm.n_cg; ++pass) {
+        float *row = a.partials + ((size_t)buf * G + b) * a.row_stride;
+        const float *rows = a.partials + (size_t)buf * G * a.row_stride;
+        target += (unsigned long long)G;
+        if (pass < prm.n_cg) {
+            float acc[F::NPR];
+#pragma unroll
+            for (int i = 0; i < F::NPR; ++i) acc[i] = 0.f;
+            const bool trace = stats && tid == 0 && pass == 1;
+            residual_pass<K, FT, true>(a, tl, sk, acc);
+            if (trace) a.ks->sub_ts[0] = global_ns();
+            cons_partials<F::NPR, NW>(acc, F::NVR, row, sred);
+            if (trace) a.ks->sub_ts[1] = global_ns();
+            if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
+            if (trace) a.ks->sub_ts[2] = global_ns();
+            reduce_rows<F::NVR, NT>(rows, G, a.row_stride, tot, rscr);
+            if (trace) a.ks->sub_ts[3] = global_ns();
+            if (warp == 0) kspace_cg<K, true>(sk, prm, tot, pass, a.ks, stats);
+            if (trace) a.ks->sub_ts[4] = global_ns();
+        } else {
+            float acc[F::NPF];
+#pragma unroll
+            for (int i = 0; i < F::NPF; ++i) acc[i] = 0.f;
+            residual_pass<K, FT, false>(a, tl, sk, acc);
+            cons_partials<F::NPF, NW>(acc, F::NVF, row, sred);
+            if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
+            reduce_rows<F::NVF, NT>(rows, G, a.row_stride, tot, rscr);
+            if (warp == 0) kspace_cg<K, false>(sk, prm, tot, pass, a.ks, stats);
+        }
+        cons_sync<NT>();
+        if (stats && tid == 0) a.ks->phase_ts[pass + 1] = global_ns();
+        buf ^= 1;
+    }
+
+    // ---- update pass: Step 2 on every row, Step 3 labels, Gram of the new rows ----
+    float acc[F::NPU];
+#pragma unroll
+    for (int i = 0; i < F::NPU; ++i) acc[i] = 0.f;
+    {
+        const float cm1 = sk.cm1, snp = sk.snp, yn = sk.yn;
+        const float mu = prm.mu, e = prm.e, pw = prm.p, om = prm.omega, dl = prm.delta;
+        const float sc = prm.in_scale, of = prm.in_offset;
+        const bool pre = prm.mask_pre != 0;
+        const bool write = !sk.skip;
+        // read the k-space vectors from shared memory at each use (broadcast
+        // loads) rather than holding 4k of them in registers
+        const volatile float *vy = sk.yf;
+        const volatile float *vv = sk.tv;
+        const volatile float *vg = sk.tg;
+        const volatile float *vw = sk.w;
+        const FT *frame = static_cast<const FT *>(a.frame);
+        const int nitems = tl.nupt * IPT;
+        for (int it = tid; it < nitems; it += NT) {
+            const int pt = tl.u0 + it / IPT;
+            const int rp = it - (it / IPT) * IPT;
+            const int64_t p = (int64_t)pt * TP + rp * RW;
+            const int nvalid = prm.P - p < RW ? (int)(prm.P - p) : RW;
+            float lb[RW], mx[RW];
+            ld2(a.labels + p, true, RW, lb);
+#pragma unroll
+            for (int r = 0; r < RW; ++r) mx[r] = 0.f;
+            for (int c = 0; c < prm.C; ++c) {
+                float *ub = a.U + ((int64_t)c * prm.npt + pt) * K * TP + rp * RW;
+                float u[K][RW];
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const float2 v = __ldcg(reinterpret_cast<const float2 *>(ub + j * TP));
+                    u[j][0] = v.x;
+                    u[j][1] = v.y;
+                }
+                float xv[RW];
+                ld2(frame + (int64_t)c * a.frame_pitch + p, nvalid == RW, nvalid, xv);
+#pragma unroll
+                for (int r = 0; r < RW; ++r) {
+                    const bool valid = r < nvalid;
+                    // dots of the orthonormal row u = T^T u_st through T y, T v, T g
+                    float uy = 0.f, ug = 0.f, uv = 0.f;
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        uy = fmaf(u[j][r], vy[j], uy);
+                        ug = fmaf(u[j][r], vg[j], ug);
+                        uv = fmaf(u[j][r], vv[j], uv);
+                    }
+                    const float x = fmaf(xv[r], sc, -of);
+                    const float res = valid ? x - uy : 0.f;
+                    const float z = fmaf(res, res, mu);
+                    const float tz = __powf(z, e);
+                    const float wv = valid ? (lb[r] != 0.f ? om : 1.f) : 0.f;
+                    const float eta = -pw * wv * tz * res;
+                    // u <- u + ((cos(theta) - 1) u^T v - sin(theta) pi(eta)_e / |pi(eta)|) v
+                    const float gam = valid ? fmaf(cm1, uv, -snp * (eta - ug)) : 0.f;
+                    const float rn = pre ? res : fmaf(-gam, yn, res);
+                    if (valid) {
+                        mx[r] = fmaxf(mx[r], fabsf(rn));
+                        if (write && a.bg_out) a.bg_out[(int64_t)c * prm.P + p + r] = x - rn + of;
+                    }
+                    // stored row of u + gamma v: u_st + gamma R^T v
+#pragma unroll
+                    for (int j = 0; j < K; ++j) u[j][r] = fmaf(gam, vw[j], u[j][r]);
+#pragma unroll
+                    for (int j = 0; j < K; ++j)
+#pragma unroll
+                        for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[j][r], u[l2][r], acc[tri<K>(j, l2)]);
+                }
+                if (write) {
+#pragma unroll
+                    for (int j = 0; j < K; ++j)
+                        *reinterpret_cast<float2 *>(ub + j * TP) = make_float2(u[j][0], u[j][1]);
+                }
+            }
+            uint8_t nl[RW];
+#pragma unroll
+            for (int r = 0; r < RW; ++r) {
+                nl[r] = (r < nvalid && mx[r] >= dl) ? 1 : 0;
+                acc[NM] += (float)nl[r];
+            }
+            if (write) {
+                *reinterpret_cast<uchar2 *>(a.labels + p) = make_uchar2(nl[0], nl[1]);
+                if (a.mask_out) {
+#pragma unroll
+                    for (int r = 0; r < RW; ++r)
+                        if (r < nvalid) a.mask_out[p + r] = nl[r];
+                }
+            }
+        }
+    }
+    if (tid == 0 && stats) a.ks->sub_ts[5] = global_ns();
+    float *row = a.partials + ((size_t)buf * G + b) * a.row_stride;
+    cons_partials<F::NPU, NW>(acc, F::NVU, row, sred);
+    cons_sync<NT>();
+    if (tid == 0 && stats) a.ks->sub_ts[6] = global_ns();
+    if (tid == 0) {
+        const unsigned long long old = atomicAdd(&a.bar->count, 1ull);
+        sk.last = old == target + (unsigned long long)G - 1ull;
+        __threadfence();
+    }
+    cons_sync<NT>();
+    if (tid == 0 && stats) a.ks->sub_ts[7] = global_ns();
+    if (!sk.last) return;
+    reduce_rows<F::NVU, NT>(a.partials + (size_t)buf * G * a.row_stride, G, a.row_stride, tot, rscr);
+    if (tid == 0) a.ks->sub_ts[8] = global_ns();
+    if (warp == 0) finish_frame<K>(sk, a.ks, tot, tot[NM], sR, sT, sW);
+    if (tid == 0) a.ks->phase_ts[prm.n_cg + 2] = global_ns();
+}
+
+template <int K> struct FrameOps {
+    template <typename FT> static cudaError_t launch_t(const FrameArgs &a, int grid, cudaStream_t s)
+    {
+        void *args[] = {const_cast<FrameArgs *>(&a)};
+        return cudaLaunchCooperativeKernel((void *)k_frame<K, FT>, dim3(grid), dim3(FCfg<K>::THREADS), args, 0, s);
+    }
+    static cudaError_t launch(const FrameArgs &a, int fdt, int grid, cudaStream_t s)
+    {
+        return fdt == 0 ? launch_t<uint8_t>(a, grid, s) : launch_t<float>(a, grid, s);
+    }
+    template <typename FT> static int prepare_t()
+    {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_frame<K, FT>, FCfg<K>::THREADS, 0) != cudaSuccess)
+            return 0;
+        return n;
+    }
+    // resident CTAs per SM (0: the kernel cannot run)
+    static int prepare(int fdt) { return fdt == 0 ? prepare_t<uint8_t>() : prepare_t<float>(); }
+};
+
+template <int K> const KernelOps *kernel_table()
+{
+    static const KernelOps ops = {&FrameOps<K>::launch, &FrameOps<K>::prepare, &Ops<K>::gram,
+                                  &Ops<K>::export_u, &Ops<K>::gram_occupancy, &Ops<K>::rebase,
+                                  Cfg<K>::VW, FCfg<K>::TP, FCfg<K>::THREADS};
+    return &ops;
+}
+
+} // namespace prost

@@ -1,15 +1,15 @@
 // Kernel sets for subspace dimensions k = 13 .. 16 (one translation unit per
 // range so that the build compiles them in parallel).
-#include "prost_kernels.cuh"
+#include "prost_frame.cuh"
 
 namespace prost {
 
 void register_ops_k13_16(const KernelOps **table)
 {
-    table[13] = Ops<13>::table();
-    table[14] = Ops<14>::table();
-    table[15] = Ops<15>::table();
-    table[16] = Ops<16>::table();
+    table[13] = kernel_table<13>();
+    table[14] = kernel_table<14>();
+    table[15] = kernel_table<15>();
+    table[16] = kernel_table<16>();
 }
 
 } // namespace prost

@@ -1,20 +1,9 @@
-// Per-pixel kernels of pROST's per-frame update (arXiv:1302.2073, Section 3.3)
-// for sm_103a, templated on the subspace dimension K.
-//
-// One frame runs n_cg + 2 launches, each a single streaming pass over the
-// stored subspace (no residual vector is ever written):
-//   k_pass<WM=true>   at CG iterate j < n_cg : r = x - U y_j, cost, gradient
-//                     g = U^T eta, the weighted Gram M = U^T diag(c) U and the
-//                     non-finite-entry count; the last CTA runs the CG step.
-//   k_pass<WM=false>  at the final iterate  : cost, g, |eta|^2; the last CTA
-//                     forms the rank-one SVD and the geodesic angle of Step 2.
-//   k_ustep           geodesic update of every row, labels and weights of
-//                     Step 3, optional background, Gram of the new subspace;
-//                     the last CTA runs the FP64 Cholesky-QR that is folded
-//                     into the next frame.
-// Reductions are deterministic: per-thread FP32 sums, a split warp reduction,
-// per-CTA partials in a fixed slot, and a fixed-order (Kahan) sum over CTAs in
-// the last CTA to arrive.
+// Building blocks of the CUDA path (arXiv:1302.2073, Section 3.3) for sm_103a:
+// vector loads, deterministic reductions (per-thread FP32 sums, a split warp
+// reduction, per-CTA partial rows in fixed slots, a fixed-order Kahan sum over
+// CTAs), the FP64 Cholesky-QR of a Gram matrix, and the kernels that compute
+// the Gram of a stored subspace (after initialisation or import) and export its
+// orthonormal representative.  The per-frame kernel is in prost_frame.cuh.
 #pragma once
 
 #include <math.h>
@@ -24,10 +13,9 @@
 
 namespace prost {
 
-// rows (pixels) per thread of the per-pixel kernels
+// rows (pixels) per thread of the Gram kernel
 template <int K> struct Cfg {
-    static constexpr int VW = K <= 6 ? 4 : (K <= 12 ? 2 : 1);  // residual passes
-    static constexpr int VWU = K <= 4 ? 4 : (K <= 8 ? 2 : 1);  // update pass (more live values per row)
+    static constexpr int VW = K <= 6 ? 4 : (K <= 12 ? 2 : 1);
 };
 
 // index of (j, l), j <= l, in a packed upper-triangular K x K matrix
@@ -226,117 +214,7 @@ __device__ __forceinline__ double wsum(double v)
     return v;
 }
 
-// ---- k-space steps (one warp of the last CTA, FP64) ------------------------
-
-// CG bookkeeping at iterate `pass` from the reduced sums tot:
-//   WM:  tot = [g_st (K) | M_st packed (K(K+1)/2) | f | |eta|^2 | #non-finite]
-//   !WM: tot = [g_st (K) | f | |eta|^2 | #non-finite]
-// g_st = U_st^T eta and M_st = U_st^T diag(c) U_st refer to the stored rows;
-// with U = U_st T the gradient is g = T^T g_st and d^T M d = (T d)^T M_st (T d).
-template <int K, bool WM>
-__device__ void kspace_pass(KState *ks, const DevParams &prm, const double *tot, int pass)
-{
-    constexpr int NM = WM ? K * (K + 1) / 2 : 0;
-    const int l = threadIdx.x;
-    const bool act = l < K;
-    const double f = tot[K + NM], ee = tot[K + NM + 1], nbad = tot[K + NM + 2];
-    if (pass == 0) {
-        if (nbad > 0.0) {
-            if (l == 0) {
-                ks->skip = 1;
-                ks->err_flags |= ERR_BADFRAME;
-                ks->last_status = -4; // PROST_EBADFRAME
-                ks->bad_frames += 1;
-            }
-            return;
-        }
-        if (l == 0) ks->skip = 0;
-    }
-    double gl = 0.0;
-    if (act)
-        for (int i = 0; i <= l; ++i) gl += ks->T[i * KMAX + l] * tot[i];
-    const double gsq = wsum(act ? gl * gl : 0.0);
-    double beta = 0.0, dl;
-    if (pass == 0) {
-        dl = act ? -gl : 0.0;
-    } else {
-        const double gp = act ? ks->gprev[l] : 0.0;
-        const double ggp = wsum(gp * gp);
-        const double num = wsum(act ? gl * (gl - gp) : 0.0);
-        beta = ggp > 0.0 ? fmax(0.0, num / ggp) : 0.0;
-        dl = act ? -gl + beta * ks->d[l] : 0.0;
-    }
-    if (l == 0) {
-        ks->cost[pass] = f;
-        ks->gnorm[pass] = sqrt(gsq);
-        ks->beta[pass] = beta;
-    }
-    if (pass < prm.n_cg) {
-        // majorise-minimise line step: alpha = -d^T g / (p d^T M d)
-        double dst = 0.0;
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-            const double di = __shfl_sync(FULL, dl, i);
-            if (act && i >= l) dst += ks->T[l * KMAX + i] * di;
-        }
-        double md = 0.0;
-        if constexpr (WM) {
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const double si = __shfl_sync(FULL, dst, i);
-                if (act) md += tot[K + (l <= i ? tri<K>(l, i) : tri<K>(i, l))] * si;
-            }
-        }
-        const double den = prm.pd * wsum(act ? dst * md : 0.0);
-        const double dg = wsum(act ? dl * gl : 0.0);
-        const double alpha = den > 0.0 ? -dg / den : 0.0;
-        const double yl = act ? ks->y[l] + alpha * dl : 0.0;
-        double ys = 0.0;
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-            const double yi = __shfl_sync(FULL, yl, i);
-            if (act && i >= l) ys += ks->T[l * KMAX + i] * yi;
-        }
-        if (act) {
-            ks->y[l] = yl;
-            ks->d[l] = dl;
-            ks->gprev[l] = gl;
-            ks->yf[l] = (float)ys;
-        }
-        if (l == 0) ks->alpha[pass] = alpha;
-    } else {
-        // Step 2 quantities: |pi(eta)|^2 = |eta|^2 - |U^T eta|^2 (U orthonormal),
-        // sigma_1 = |pi(eta)| |y|, v = y/|y| (Eq. svd), theta = sigma_1 t.
-        const double yl = act ? ks->y[l] : 0.0;
-        const double yn = sqrt(wsum(yl * yl));
-        const double pin2 = ee - gsq;
-        const double pin = pin2 > 0.0 ? sqrt(pin2) : 0.0;
-        const double t = fmax(exp(-prm.tau * (double)ks->frame_index) * prm.t_init, prm.t_min);
-        const double sigma = pin * yn;
-        const double theta = sigma * t;
-        const bool upd = yn > 0.0 && pin > 0.0;
-        const double sh = sin(0.5 * theta);
-        if (act) {
-            ks->ye[l] = (float)yl;
-            ks->gf[l] = (float)gl;
-            ks->vf[l] = upd ? (float)(yl / yn) : 0.f;
-            ks->g[l] = gl;
-        }
-        if (l == 0) {
-            ks->cm1 = upd ? (float)(-2.0 * sh * sh) : 0.f;
-            ks->sn_pin = upd ? (float)(sin(theta) / pin) : 0.f;
-            ks->ynorm = (float)yn;
-            ks->do_update = upd ? 1 : 0;
-            ks->pi_norm = pin;
-            ks->y_norm = yn;
-            ks->sigma = sigma;
-            ks->t = t;
-            ks->theta = upd ? theta : 0.0;
-            ks->updated = upd ? 1 : 0;
-            ks->n_cg_done = prm.n_cg;
-        }
-    }
-}
+// ---- k-space (one warp, FP64) -----------------------------------------------
 
 // Cholesky-QR of the stored subspace from its Gram matrix G (packed upper):
 // G = R^T R, T = R^{-1}; y (coefficients w.r.t. the stored rows) becomes
@@ -419,192 +297,6 @@ __device__ void finish_reorth(KState *ks, const double *G, double *sR, double *s
 
 // ---- per-pixel kernels -------------------------------------------------------
 
-template <int K, typename FT, bool WM>
-__global__ void __launch_bounds__(THREADS) k_pass(const PassArgs a)
-{
-    constexpr int VW = Cfg<K>::VW;
-    constexpr int NM = WM ? K * (K + 1) / 2 : 0;
-    constexpr int NV = K + NM + 3;
-    constexpr int NP = (NV + 31) / 32 * 32;
-    __shared__ float sred[(THREADS / 32) * NP];
-    __shared__ double tot[NV];
-
-    if (a.pass > 0 && a.ks->skip) return; // frame rejected by pass 0 (uniform)
-    const DevParams &prm = a.prm;
-    float y[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) y[j] = a.ks->yf[j];
-    const float mu = prm.mu, e = prm.e, pw = prm.p, om = prm.omega;
-    const float sc = prm.in_scale, of = prm.in_offset;
-
-    float acc[NP];
-#pragma unroll
-    for (int i = 0; i < NP; ++i) acc[i] = 0.f;
-
-    const int ngroups = (int)(prm.Pp / VW);
-    const int nitems = prm.C * ngroups;
-    const FT *frame = static_cast<const FT *>(a.frame);
-    for (int it = blockIdx.x * THREADS + threadIdx.x; it < nitems; it += gridDim.x * THREADS) {
-        const int c = it / ngroups;
-        const int64_t p0 = (int64_t)(it - c * ngroups) * VW;
-        const int nvalid = prm.P - p0 < (int64_t)VW ? (int)(prm.P - p0) : VW;
-        if (nvalid <= 0) continue;
-        float u[K][VW];
-#pragma unroll
-        for (int j = 0; j < K; ++j) VL<VW>::ldu(a.U + ((int64_t)j * prm.C + c) * prm.Pp + p0, u[j]);
-        float xv[VW];
-        load_x<VW, FT>(frame + (int64_t)c * prm.P + p0, nvalid, prm.vec, xv);
-        uint8_t lab[VW];
-        VL<VW>::ldlab(a.labels + p0, lab);
-#pragma unroll
-        for (int r = 0; r < VW; ++r) {
-            const bool valid = r < nvalid;
-            float uy = 0.f;
-#pragma unroll
-            for (int j = 0; j < K; ++j) uy = fmaf(u[j][r], y[j], uy);
-            const float x = fmaf(xv[r], sc, -of);
-            if constexpr (sizeof(FT) == 4) {
-                if (valid && !isfinite(xv[r])) acc[K + NM + 2] += 1.f;
-            }
-            const float res = x - uy;
-            const float z = fmaf(res, res, mu);
-            const float tz = __powf(z, e);               // (r^2 + mu)^(p/2 - 1)
-            const float wv = valid ? (lab[r] ? om : 1.f) : 0.f;
-            const float cw = wv * tz;                     // c_e
-            acc[K + NM] = fmaf(cw, z, acc[K + NM]);       // w (r^2 + mu)^(p/2)
-            const float eta = -pw * cw * res;
-            acc[K + NM + 1] = fmaf(eta, eta, acc[K + NM + 1]);
-#pragma unroll
-            for (int j = 0; j < K; ++j) acc[j] = fmaf(eta, u[j][r], acc[j]);
-            if constexpr (WM) {
-#pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    const float cu = cw * u[j][r];
-#pragma unroll
-                    for (int l2 = j; l2 < K; ++l2) acc[K + tri<K>(j, l2)] = fmaf(cu, u[l2][r], acc[K + tri<K>(j, l2)]);
-                }
-            }
-        }
-    }
-    block_partials<NP>(acc, NV, a.partials + (size_t)blockIdx.x * NV, sred);
-    if (!arrive_last(a.counter)) return;
-    reduce_partials<NV>(a.partials, gridDim.x, tot, sred);
-    if (threadIdx.x < 32) kspace_pass<K, WM>(a.ks, prm, tot, a.pass);
-    if (threadIdx.x == 0) *a.counter = 0u;
-}
-
-template <int K, typename FT>
-__global__ void __launch_bounds__(THREADS) k_ustep(const UstepArgs a)
-{
-    constexpr int VW = Cfg<K>::VWU;
-    constexpr int NM = K * (K + 1) / 2;
-    constexpr int NV = NM + 1;
-    constexpr int NP = (NV + 31) / 32 * 32;
-    __shared__ float sred[(THREADS / 32) * NP];
-    __shared__ double tot[NV];
-    __shared__ double sR[K * K], sT[K * K];
-    __shared__ float s_T[K * K], s_y[K], s_g[K], s_v[K];
-
-    if (a.ks->skip) return;
-    const DevParams &prm = a.prm;
-    for (int i = threadIdx.x; i < K * K; i += THREADS) s_T[i] = a.ks->Tf[i];
-    if (threadIdx.x < K) {
-        s_y[threadIdx.x] = a.ks->ye[threadIdx.x];
-        s_g[threadIdx.x] = a.ks->gf[threadIdx.x];
-        s_v[threadIdx.x] = a.ks->vf[threadIdx.x];
-    }
-    const float cm1 = a.ks->cm1, snp = a.ks->sn_pin, yn = a.ks->ynorm;
-    const float mu = prm.mu, e = prm.e, pw = prm.p, om = prm.omega, dl = prm.delta;
-    const float sc = prm.in_scale, of = prm.in_offset;
-    const bool pre = prm.mask_pre != 0;
-    __syncthreads();
-
-    float acc[NP];
-#pragma unroll
-    for (int i = 0; i < NP; ++i) acc[i] = 0.f;
-
-    const int ngroups = (int)(prm.Pp / VW);
-    const FT *frame = static_cast<const FT *>(a.frame);
-    for (int pg = blockIdx.x * THREADS + threadIdx.x; pg < ngroups; pg += gridDim.x * THREADS) {
-        const int64_t p0 = (int64_t)pg * VW;
-        const int nvalid = prm.P - p0 < (int64_t)VW ? (int)(prm.P - p0) : VW;
-        if (nvalid <= 0) continue;
-        uint8_t lab[VW];
-        VL<VW>::ldlab(a.labels + p0, lab);
-        float mx[VW];
-#pragma unroll
-        for (int r = 0; r < VW; ++r) mx[r] = 0.f;
-        for (int c = 0; c < prm.C; ++c) {
-            float u[K][VW];
-#pragma unroll
-            for (int j = 0; j < K; ++j) VL<VW>::ldu_rw(a.U + ((int64_t)j * prm.C + c) * prm.Pp + p0, u[j]);
-            float xv[VW];
-            load_x<VW, FT>(frame + (int64_t)c * prm.P + p0, nvalid, prm.vec, xv);
-#pragma unroll
-            for (int r = 0; r < VW; ++r) {
-                const bool valid = r < nvalid;
-                // row of the orthonormal representative: u = T^T u_st
-                float ue[K];
-#pragma unroll
-                for (int j = K - 1; j >= 0; --j) {
-                    float s = 0.f;
-#pragma unroll
-                    for (int i = 0; i <= j; ++i) s = fmaf(s_T[i * K + j], u[i][r], s);
-                    ue[j] = s;
-                }
-                float uy = 0.f, ug = 0.f, uv = 0.f;
-#pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    uy = fmaf(ue[j], s_y[j], uy);
-                    ug = fmaf(ue[j], s_g[j], ug);
-                    uv = fmaf(ue[j], s_v[j], uv);
-                }
-                const float x = fmaf(xv[r], sc, -of);
-                const float res = x - uy;
-                const float z = fmaf(res, res, mu);
-                const float tz = __powf(z, e);
-                const float wv = valid ? (lab[r] ? om : 1.f) : 0.f;
-                const float eta = -pw * wv * tz * res;
-                // u <- u + ((cos(theta) - 1) u^T v - sin(theta) pi(eta)_e / |pi(eta)|) v
-                const float gam = valid ? fmaf(cm1, uv, -snp * (eta - ug)) : 0.f;
-                const float rn = pre ? res : fmaf(-gam, yn, res);
-                if (valid) {
-                    mx[r] = fmaxf(mx[r], fabsf(rn));
-                    if (a.bg_out) a.bg_out[(int64_t)c * prm.P + p0 + r] = x - rn + of;
-                }
-#pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    ue[j] = fmaf(gam, s_v[j], ue[j]);
-                    u[j][r] = ue[j];
-                }
-#pragma unroll
-                for (int j = 0; j < K; ++j)
-#pragma unroll
-                    for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(ue[j], ue[l2], acc[tri<K>(j, l2)]);
-            }
-#pragma unroll
-            for (int j = 0; j < K; ++j) VL<VW>::stu(a.U + ((int64_t)j * prm.C + c) * prm.Pp + p0, u[j]);
-        }
-        uint8_t nl[VW];
-#pragma unroll
-        for (int r = 0; r < VW; ++r) {
-            nl[r] = (r < nvalid && mx[r] >= dl) ? 1 : 0;
-            acc[NM] += (float)nl[r];
-        }
-        VL<VW>::stlab(a.labels + p0, nl);
-        if (a.mask_out) {
-#pragma unroll
-            for (int r = 0; r < VW; ++r)
-                if (r < nvalid) a.mask_out[p0 + r] = nl[r];
-        }
-    }
-    block_partials<NP>(acc, NV, a.partials + (size_t)blockIdx.x * NV, sred);
-    if (!arrive_last(a.counter)) return;
-    reduce_partials<NV>(a.partials, gridDim.x, tot, sred);
-    if (threadIdx.x < 32) finish_reorth<K>(a.ks, tot, sR, sT, true, tot[NM]);
-    if (threadIdx.x == 0) *a.counter = 0u;
-}
-
 // Gram of the stored subspace and its Cholesky-QR (after init / import).
 template <int K>
 __global__ void __launch_bounds__(THREADS) k_gram(const GramArgs a)
@@ -619,14 +311,16 @@ __global__ void __launch_bounds__(THREADS) k_gram(const GramArgs a)
     float acc[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) acc[i] = 0.f;
-    const int ngroups = (int)(prm.Pp / VW);
-    const int nitems = prm.C * ngroups;
+    // VW consecutive rows of one tile block (TILE_P is a multiple of VW)
+    constexpr int GPB = TILE_P / VW;
+    const int nitems = prm.C * prm.npt * GPB;
     for (int it = blockIdx.x * THREADS + threadIdx.x; it < nitems; it += gridDim.x * THREADS) {
-        const int c = it / ngroups;
-        const int64_t p0 = (int64_t)(it - c * ngroups) * VW;
+        const int blk = it / GPB;
+        const int r0 = (it - blk * GPB) * VW;
+        const float *base = a.U + (int64_t)blk * K * TILE_P + r0;
         float u[K][VW];
 #pragma unroll
-        for (int j = 0; j < K; ++j) VL<VW>::ldu(a.U + ((int64_t)j * prm.C + c) * prm.Pp + p0, u[j]);
+        for (int j = 0; j < K; ++j) VL<VW>::ldu(base + j * TILE_P, u[j]);
 #pragma unroll
         for (int r = 0; r < VW; ++r)
 #pragma unroll
@@ -655,7 +349,7 @@ __global__ void __launch_bounds__(THREADS) k_export(const float *U, const KState
         const int64_t q = e - (int64_t)c * prm.P;
         float u[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) u[j] = U[((int64_t)j * prm.C + c) * prm.Pp + q];
+        for (int j = 0; j < K; ++j) u[j] = U[u_off(prm, c, q, j)];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             float s = 0.f;
@@ -666,25 +360,37 @@ __global__ void __launch_bounds__(THREADS) k_export(const float *U, const KState
     }
 }
 
+// Rebase of the stored rows onto the orthonormal representative: U_st <- U_st T
+// (each row u_st becomes T^T u_st), after which the fold is the identity.
+template <int K>
+__global__ void __launch_bounds__(THREADS) k_rebase(float *U, const KState *ks, DevParams prm)
+{
+    __shared__ float sT[K * K];
+    for (int i = threadIdx.x; i < K * K; i += THREADS) sT[i] = ks->Tf[i];
+    __syncthreads();
+    const int64_t rows = (int64_t)prm.C * prm.Pp;
+    for (int64_t e = (int64_t)blockIdx.x * THREADS + threadIdx.x; e < rows; e += (int64_t)gridDim.x * THREADS) {
+        const int c = (int)(e / prm.Pp);
+        const int64_t q = e - (int64_t)c * prm.Pp;
+        float *base = U + u_off(prm, c, q, 0);
+        float u[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) u[j] = base[(int64_t)j * TILE_P];
+#pragma unroll
+        for (int j = K - 1; j >= 0; --j) {
+            float s = 0.f;
+#pragma unroll
+            for (int i = 0; i <= j; ++i) s = fmaf(sT[i * K + j], u[i], s);
+            u[j] = s;
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) base[(int64_t)j * TILE_P] = u[j];
+    }
+}
+
 // ---- host launchers of one kernel set ----------------------------------------
 
 template <int K> struct Ops {
-    template <typename FT> static cudaError_t pass_t(const PassArgs &a, bool wm, int grid, cudaStream_t s)
-    {
-        if (wm) k_pass<K, FT, true><<<grid, THREADS, 0, s>>>(a);
-        else k_pass<K, FT, false><<<grid, THREADS, 0, s>>>(a);
-        return cudaGetLastError();
-    }
-    static cudaError_t pass(const PassArgs &a, bool wm, int fdt, int grid, cudaStream_t s)
-    {
-        return fdt == 0 ? pass_t<uint8_t>(a, wm, grid, s) : pass_t<float>(a, wm, grid, s);
-    }
-    static cudaError_t ustep(const UstepArgs &a, int fdt, int grid, cudaStream_t s)
-    {
-        if (fdt == 0) k_ustep<K, uint8_t><<<grid, THREADS, 0, s>>>(a);
-        else k_ustep<K, float><<<grid, THREADS, 0, s>>>(a);
-        return cudaGetLastError();
-    }
     static cudaError_t gram(const GramArgs &a, int grid, cudaStream_t s)
     {
         k_gram<K><<<grid, THREADS, 0, s>>>(a);
@@ -698,23 +404,19 @@ template <int K> struct Ops {
         k_export<K><<<grid, THREADS, 0, s>>>(U, ks, out, prm);
         return cudaGetLastError();
     }
-    static int occupancy(int kind, int fdt)
+    static cudaError_t rebase(float *U, KState *ks, DevParams prm, cudaStream_t s)
+    {
+        const int64_t nb = ((int64_t)prm.C * prm.Pp + THREADS - 1) / THREADS;
+        k_rebase<K><<<(int)(nb < 4096 ? nb : 4096), THREADS, 0, s>>>(U, ks, prm);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        return launch_reset_fold(ks, prm, s);
+    }
+    static int gram_occupancy()
     {
         int n = 0;
-        cudaError_t e = cudaSuccess;
-        if (kind == 0) e = fdt == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pass<K, uint8_t, true>, THREADS, 0)
-                                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pass<K, float, true>, THREADS, 0);
-        else if (kind == 1) e = fdt == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pass<K, uint8_t, false>, THREADS, 0)
-                                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pass<K, float, false>, THREADS, 0);
-        else if (kind == 2) e = fdt == 0 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ustep<K, uint8_t>, THREADS, 0)
-                                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_ustep<K, float>, THREADS, 0);
-        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gram<K>, THREADS, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gram<K>, THREADS, 0);
         return e == cudaSuccess && n > 0 ? n : 1;
-    }
-    static const KernelOps *table()
-    {
-        static const KernelOps ops = {&pass, &ustep, &gram, &export_u, &occupancy, Cfg<K>::VW, Cfg<K>::VWU};
-        return &ops;
     }
 };
 

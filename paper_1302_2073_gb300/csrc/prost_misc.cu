@@ -28,36 +28,42 @@ __device__ __forceinline__ float gauss(uint64_t seed, uint64_t ctr)
     return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
 }
 
-// U_st = N(0, 1)/sqrt(m) per entry (pad rows 0); its Cholesky-QR (run next)
-// gives the orthonormal factor of a random m x k matrix (Section 3.4).
+// (channel, pixel, column) of element i of the tile-blocked stored subspace
+__device__ __forceinline__ void u_coords(const DevParams &prm, int64_t i, int64_t &c, int64_t &q, int &j)
+{
+    const int64_t blk = i / ((int64_t)prm.k * TILE_P);
+    const int64_t rem = i - blk * prm.k * TILE_P;
+    j = (int)(rem / TILE_P);
+    c = blk / prm.npt;
+    q = (blk - c * prm.npt) * TILE_P + (rem - (int64_t)j * TILE_P);
+}
+
+// U_st = N(0, 1)/sqrt(m) per entry (padding rows 0); its Cholesky-QR (run
+// next) gives the orthonormal factor of a random m x k matrix (Section 3.4).
 __global__ void k_init_gauss(float *U, DevParams prm, uint64_t seed)
 {
-    const int64_t rows = (int64_t)prm.C * prm.Pp;
-    const int64_t n = rows * prm.k;
+    const int64_t n = (int64_t)prm.C * prm.Pp * prm.k;
     const float s = rsqrtf((float)((double)prm.C * (double)prm.P));
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = i / rows;
-        const int64_t rr = i - j * rows;
-        const int64_t c = rr / prm.Pp;
-        const int64_t q = rr - c * prm.Pp;
+        int64_t c, q;
+        int j;
+        u_coords(prm, i, c, q, j);
         float v = 0.f;
         if (q < prm.P) v = s * gauss(seed, (uint64_t)((c * prm.P + q) * prm.k + j));
         U[i] = v;
     }
 }
 
-// m x k row-major -> stored layout (column j, channel c at (j*C + c)*Pp).
+// m x k row-major -> tile-blocked stored layout
 __global__ void k_import_u(const float *Urow, float *U, DevParams prm)
 {
-    const int64_t rows = (int64_t)prm.C * prm.Pp;
-    const int64_t n = rows * prm.k;
+    const int64_t n = (int64_t)prm.C * prm.Pp * prm.k;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = i / rows;
-        const int64_t rr = i - j * rows;
-        const int64_t c = rr / prm.Pp;
-        const int64_t q = rr - c * prm.Pp;
+        int64_t c, q;
+        int j;
+        u_coords(prm, i, c, q, j);
         U[i] = q < prm.P ? Urow[(c * prm.P + q) * prm.k + j] : 0.f;
     }
 }
@@ -67,6 +73,16 @@ __global__ void k_import_labels(const uint8_t *src, uint8_t *labels, DevParams p
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < prm.Pp;
          q += (int64_t)gridDim.x * blockDim.x)
         labels[q] = (src && q < prm.P && src[q]) ? 1 : 0;
+}
+
+__global__ void k_reset_fold(KState *ks, int k)
+{
+    for (int q = threadIdx.x; q < KMAX * KMAX; q += blockDim.x) {
+        const int i = q / KMAX, j = q % KMAX;
+        ks->R[q] = ks->T[q] = (i == j) ? 1.0 : 0.0;
+        if (i < k && j < k) ks->Tf[i * k + j] = (i == j) ? 1.f : 0.f;
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) ks->yf[i] = (float)ks->y[i];
 }
 
 static int grid_for(int64_t n)
@@ -84,6 +100,12 @@ cudaError_t launch_init_gauss(float *U, DevParams prm, uint64_t seed, cudaStream
 cudaError_t launch_import_u(const float *Urow, float *U, DevParams prm, cudaStream_t s)
 {
     k_import_u<<<grid_for((int64_t)prm.C * prm.Pp * prm.k), THREADS, 0, s>>>(Urow, U, prm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_fold(KState *ks, DevParams prm, cudaStream_t s)
+{
+    k_reset_fold<<<1, 256, 0, s>>>(ks, prm.k);
     return cudaGetLastError();
 }
 
