@@ -233,6 +233,20 @@ int prost_cost_grad_static(const prost_params *prm, const float *U, const double
                            const void *frame, const uint8_t *labels, double *out,
                            int32_t *status_out, void *stream);
 
+/* Raw device-clock stamps (%globaltimer, ns) of the last frame, for tracing
+ * the inside of a phase.  ts receives PROST_TRACE_LEN values:
+ *   ts[0 .. n_cg+2]      start of the frame, end of each residual pass, end of
+ *                        the frame (as used by prost_get_timing);
+ *   ts[PROST_MAX_CG+3 .. PROST_MAX_CG+12]  inside CG pass 1 (first CTA): rows
+ *                        streamed, CTA partial row written, grid barrier passed,
+ *                        all partial rows reduced, CG step done; inside the
+ *                        update pass: rows streamed, partial row written,
+ *                        arrival; (last CTA) partial rows reduced, Cholesky-QR
+ *                        factors and state written.
+ * Stamps of phases that did not run are stale.  Synchronises the stream. */
+#define PROST_TRACE_LEN (PROST_MAX_CG + 13)
+int prost_get_trace(prost_handle *h, uint64_t *ts);
+
 /* Release the device state (synchronises the stream first).  NULL is a no-op. */
 void prost_destroy(prost_handle *h);
 

@@ -310,6 +310,8 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     CKI(launch_init_gauss(h->U, h->dp, prm->seed, h->stream));
     rc = run_gram(h);
     if (rc) return bail(rc);
+    // store the orthonormal factor itself, so that the stored rows start orthonormal
+    CKI(ops->rebase(h->U, h->ks, h->dp, h->stream));
     int st = 0;
     rc = read_status(h, &st);
     if (rc) return bail(rc);
@@ -461,6 +463,9 @@ int prost_set_subspace(prost_handle *h, const float *U, const double *y, int on_
     rc = read_status(h, &st);
     if (rc) return rc;
     if (st == PROST_ENOTSPD) return fail(h, PROST_ENOTSPD, "subspace columns are not linearly independent");
+    // store the orthonormal factor itself, so that the stored rows start orthonormal
+    CK(h, h->ops->rebase(h->U, h->ks, h->dp, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
     return PROST_OK;
 }
 
@@ -601,6 +606,16 @@ int prost_get_timing(prost_handle *h, float *ms, int *n)
     CK(h, cudaMemcpy(ts, h->ks->phase_ts, sizeof(uint64_t) * (size_t)(nl + 1), cudaMemcpyDeviceToHost));
     for (int j = 0; j < nl; ++j) ms[j] = (float)((double)(ts[j + 1] - ts[j]) * 1e-6);
     *n = nl;
+    return PROST_OK;
+}
+
+int prost_get_trace(prost_handle *h, uint64_t *ts)
+{
+    if (!h || !ts) return PROST_EINVAL;
+    DeviceGuard dg(h->device);
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(ts, h->ks->phase_ts, sizeof(uint64_t) * (CGMAX + 3), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(ts + CGMAX + 3, h->ks->sub_ts, sizeof(uint64_t) * 10, cudaMemcpyDeviceToHost));
     return PROST_OK;
 }
 

@@ -48,8 +48,8 @@ struct KState {
     uint64_t phase_ts[CGMAX + 3];
     // %globaltimer (ns), CTA 0: CG pass 1 tiles done, partial row written, grid
     // barrier passed, all rows reduced, CG step done; update-pass rows done,
-    // partial row written, arrived; last CTA: rows reduced
-    uint64_t sub_ts[9];
+    // partial row written, arrived; last CTA: rows reduced, factors done
+    uint64_t sub_ts[10];
 };
 
 constexpr uint32_t ERR_BADFRAME = 1u, ERR_NOTSPD = 2u, ERR_TIMEOUT = 4u;

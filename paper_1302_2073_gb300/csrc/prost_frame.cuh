@@ -335,62 +335,58 @@ __device__ void kspace_cg(SKState<K> &sk, const DevParams &prm, const float *tot
     }
 }
 
-// 1/sqrt(d) in FP64: a float seed refined by two Newton-Raphson steps for the
-// reciprocal square root, y <- y (3 - d y^2) / 2 (quadratic convergence from
-// float accuracy).  Replaces FP64 sqrt and division, which are long software
-// sequences on GB300's narrow FP64 pipe.
-__device__ __forceinline__ double rsqrt_nr(double d)
+// FP64 with explicit rounding, so that every kernel running the deferred
+// re-orthonormalisation below produces the same bits
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// 1/sqrt(d) in FP64 for d near 1 (the diagonal of the Gram of a nearly
+// orthonormal basis): Newton-Raphson for the reciprocal square root from
+// y = 1, y <- y (3 - d y^2) / 2, which converges quadratically and reaches
+// FP64 accuracy in 6 steps for |d - 1| <= 1/4.  Farther from 1 the library
+// square root and division are used.
+__device__ __forceinline__ double rsqrt_near1(double d)
 {
-    double y = (double)rsqrtf((float)d);
-    y = y * fma(-0.5 * d * y, y, 1.5);
-    y = y * fma(-0.5 * d * y, y, 1.5);
+    if (fabs(d - 1.0) > 0.25) return 1.0 / sqrt(d);
+    const double hd = dmul(-0.5, d);
+    double y = 1.0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) y = dmul(y, dfma(hd, dmul(y, y), 1.5));
     return y;
 }
 
-// End of frame (last CTA, warp 0): Cholesky-QR of the new stored rows from
-// their Gram matrix G in FP64 (G = R'^T R', T' = R'^{-1}); the orthonormal
-// basis becomes U_st T', and y (coefficients of U_st T_old) becomes R' T_old y.
-// Right-looking over the k^2 entries, lane-parallel; sW is k x k scratch.
+// Cholesky-QR factors of the stored rows from their Gram matrix G (packed
+// upper, FP32 sums), in FP64 by one warp: G = R^T R, T = R^{-1} (row-major
+// k x k in sR, sT), and the coefficients y_old of the previous basis
+// U_st T_old re-expressed in the orthonormal basis U_st T: y_new = R T_old y_old.
+// Right-looking over the k^2 entries, lane-parallel.  Returns false when G is
+// not positive definite (then R = T = I and y_new = T_old y_old).
+// Right-looking FP64 Cholesky G = R^T R (G in sW, overwritten) and T = R^{-1}
+// for Gram matrices away from the identity; one warp (lanes of the calling
+// warp).  Returns false when G is not positive definite.
 template <int K>
-__device__ void finish_frame(const SKState<K> &sk, KState *ks, const float *G, float n_fg, double *sR,
-                             double *sT, double *sW)
+__device__ bool cholesky_rl(double *sR, double *sT, double *sW)
 {
-    const int lane = threadIdx.x;
-    if (sk.skip) {
-        if (lane == 0) {
-            ks->err_flags |= ERR_BADFRAME;
-            ks->last_status = -4; // PROST_EBADFRAME
-            ks->bad_frames += 1;
-        }
-        return;
-    }
-    double oerr = 0.0;
-    for (int q = lane; q < K * K; q += 32) {
-        const int i = q / K, l = q - i * K;
-        const double gv = (double)(i <= l ? G[tri<K>(i, l)] : G[tri<K>(l, i)]);
-        sW[q] = gv;
-        sR[q] = 0.0;
-        oerr = fmax(oerr, fabs(gv - (i == l ? 1.0 : 0.0)));
-    }
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) oerr = fmax(oerr, __shfl_xor_sync(FULL, oerr, off));
+    const int lane = threadIdx.x & 31;
+    for (int q = lane; q < K * K; q += 32) sR[q] = 0.0;
     __syncwarp();
     double inv[K];
     bool ok = true;
+#pragma unroll
     for (int a = 0; a < K; ++a) {
         const double d = sW[a * K + a];
         if (!(d > 0.0)) {
             ok = false;
             break;
         }
-        const double ri = rsqrt_nr(d);
+        const double ri = rsqrt_near1(d);
         inv[a] = ri;
         for (int l = lane; l < K; l += 32)
-            if (l >= a) sR[a * K + l] = l == a ? d * ri : sW[a * K + l] * ri;
+            if (l >= a) sR[a * K + l] = l == a ? dmul(d, ri) : dmul(sW[a * K + l], ri);
         __syncwarp();
         for (int q = lane; q < K * K; q += 32) {
             const int i = q / K, l = q - i * K;
-            if (i > a && l >= i) sW[q] = fma(-sR[a * K + i], sR[a * K + l], sW[q]);
+            if (i > a && l >= i) sW[q] = dfma(-sR[a * K + i], sR[a * K + l], sW[q]);
         }
         __syncwarp();
     }
@@ -399,41 +395,131 @@ __device__ void finish_frame(const SKState<K> &sk, KState *ks, const float *G, f
     } else {
         for (int q = lane; q < K * K; q += 32) sW[q] = (q / K == q % K) ? 1.0 : 0.0;
         __syncwarp();
+#pragma unroll
         for (int r = K - 1; r >= 0; --r) {
-            for (int l = lane; l < K; l += 32) sT[r * K + l] = sW[r * K + l] * inv[r];
+            for (int l = lane; l < K; l += 32) sT[r * K + l] = dmul(sW[r * K + l], inv[r]);
             __syncwarp();
             for (int q = lane; q < K * K; q += 32) {
                 const int i = q / K, l = q - i * K;
-                if (i < r) sW[q] = fma(-sR[i * K + r], sT[r * K + l], sW[q]);
+                if (i < r) sW[q] = dfma(-sR[i * K + r], sT[r * K + l], sW[q]);
             }
             __syncwarp();
         }
     }
     __syncwarp();
-    // y' = R' (T_old y): T_old y in FP64 from the state of the finished frame
-    const bool act = lane < K;
-    double ty = 0.0;
-    if (act)
-        for (int q = lane; q < K; ++q) ty = fma(ks->T[lane * KMAX + q], sk.y[q], ty);
-    double ynew = 0.0;
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-        const double tq = __shfl_sync(FULL, ty, q);
-        if (act && q >= lane) ynew = fma(sR[lane * K + q], tq, ynew);
+    return ok;
+}
+
+// Scratch of the end-of-frame re-orthonormalisation (last CTA).
+template <int K> struct ReorthScratch {
+    double R[K * K], T[K * K], W[K * K], Told[K * K], ty[K];
+    float Xh[K * K], Xl[K * K], X2[K * K];
+    float emax;
+    int ok;
+};
+
+// End of frame, all NT threads of the last CTA: the Cholesky-QR factors of the
+// new stored rows from their Gram matrix G (packed upper, FP32 sums) to FP64
+// accuracy, G = R^T R and T = R^{-1}; the new state R, T, y' = R T_old y (the
+// background U y is kept) and the frame's results.
+//
+// For a near-identity Gram (|G - I| <= 1e-5, the usual case: the geodesic step
+// keeps U orthonormal up to rounding) write R = I + X with X upper triangular.
+// R^T R = G reads X + X^T = E - X^T X with E = G - I, so X is the fixed point of
+// X <- Phi(E - X^T X), Phi taking the upper triangle with the diagonal halved.
+// X is carried as an unevaluated float sum Xh + Xl: Xh = Phi(E) is exact in
+// FP32 (G - I is exact by Sterbenz's lemma, halving is exact), and the
+// correction Xl = -Phi(Xh^T Xh + Xh^T Xl + Xl^T Xh), of size |E|^2 <= 1e-10,
+// takes two FP32 sweeps; its rounding and the neglected terms (|E|^3 and the
+// Xl^T Xl product) stay below 1e-15 absolute.  T = R^{-1} is the Neumann
+// series I - X + X^2 - X^3 (the next term is below 1e-20).  The pieces are
+// summed into FP64, which gives R and T to FP64 accuracy without long FP64
+// dependency chains (GB300's FP64 pipe has a long latency).  Gram matrices
+// farther from I take the right-looking FP64 factorisation.
+template <int K, int NT>
+__device__ void end_frame(const SKState<K> &sk, KState *ks, const float *G, float n_fg, ReorthScratch<K> &rs)
+{
+    const int t = threadIdx.x;
+    const int i = t / K, l = t - (t / K) * K;
+    const bool el = t < K * K;
+    if (sk.skip) {
+        if (t == 0) {
+            ks->err_flags |= ERR_BADFRAME;
+            ks->last_status = -4; // PROST_EBADFRAME
+            ks->bad_frames += 1;
+        }
+        return;
     }
-    __syncwarp();
-    for (int q = lane; q < K * K; q += 32) {
-        const int i = q / K, l = q - i * K;
-        ks->R[i * KMAX + l] = sR[q];
-        ks->T[i * KMAX + l] = sT[q];
-        ks->Tf[q] = (float)sT[q];
+    float e = 0.f;
+    if (el) {
+        const float gv = i <= l ? G[tri<K>(i, l)] : G[tri<K>(l, i)];
+        e = gv - (i == l ? 1.f : 0.f); // exact
+        rs.W[t] = (double)gv;
+        rs.Xh[t] = l > i ? e : (l == i ? 0.5f * e : 0.f);
+        rs.Xl[t] = 0.f;
     }
-    if (act) {
-        ks->y[lane] = ynew;
-        ks->yf[lane] = (float)ty;
+    if (t == 0) rs.emax = 0.f;
+    cons_sync<NT>();
+    // the bit patterns of non-negative floats order like the floats
+    if (el && fabsf(e) > 0.f) atomicMax(reinterpret_cast<int *>(&rs.emax), __float_as_int(fabsf(e)));
+    cons_sync<NT>();
+    const float emax = rs.emax;
+    if (emax <= 1e-5f) {
+        for (int sweep = 0; sweep < 2; ++sweep) {
+            float pv = 0.f;
+            if (el && l >= i)
+                for (int r = 0; r <= i; ++r) {
+                    pv = fmaf(rs.Xh[r * K + i], rs.Xh[r * K + l], pv);
+                    pv = fmaf(rs.Xh[r * K + i], rs.Xl[r * K + l], pv);
+                    pv = fmaf(rs.Xl[r * K + i], rs.Xh[r * K + l], pv);
+                }
+            cons_sync<NT>();
+            if (el) rs.Xl[t] = l > i ? -pv : (l == i ? -0.5f * pv : 0.f);
+            cons_sync<NT>();
+        }
+        // X^2 and X^3 (sizes |E|^2 and |E|^3) from the rounded sum Xh + Xl
+        float x2 = 0.f;
+        if (el && l >= i)
+            for (int r = i; r <= l; ++r)
+                x2 = fmaf(rs.Xh[i * K + r] + rs.Xl[i * K + r], rs.Xh[r * K + l] + rs.Xl[r * K + l], x2);
+        if (el) rs.X2[t] = x2;
+        cons_sync<NT>();
+        float x3 = 0.f;
+        if (el && l >= i)
+            for (int r = i; r <= l; ++r) x3 = fmaf(rs.X2[i * K + r], rs.Xh[r * K + l], x3);
+        if (el) {
+            const double xh = (double)rs.Xh[t], xl = (double)rs.Xl[t];
+            const double id = i == l ? 1.0 : 0.0;
+            rs.R[t] = (id + xh) + xl;
+            rs.T[t] = ((id - xh) - xl) + ((double)x2 - (double)x3);
+        }
+        if (t == 0) rs.ok = 1;
+    } else if (t < 32) {
+        const bool ok = cholesky_rl<K>(rs.R, rs.T, rs.W);
+        if (t == 0) rs.ok = ok ? 1 : 0;
     }
-    if (lane == 0) {
-        ks->orth_err = oerr;
+    cons_sync<NT>();
+    const bool ok = rs.ok != 0;
+    // y' = R (T_old y), FP64
+    if (t < K) {
+        double ty = 0.0;
+        for (int q = t; q < K; ++q) ty = dfma(rs.Told[t * K + q], sk.y[q], ty);
+        rs.ty[t] = ty;
+    }
+    cons_sync<NT>();
+    if (t < K) {
+        double yn = 0.0;
+        for (int q = t; q < K; ++q) yn = dfma(rs.R[t * K + q], rs.ty[q], yn);
+        ks->y[t] = yn;
+        ks->yf[t] = (float)rs.ty[t];
+    }
+    if (el) {
+        ks->R[i * KMAX + l] = rs.R[t];
+        ks->T[i * KMAX + l] = rs.T[t];
+        ks->Tf[t] = (float)rs.T[t];
+    }
+    if (t == 0) {
+        ks->orth_err = emax;
         if (!ok) ks->err_flags |= ERR_NOTSPD;
         ks->n_fg = (int64_t)n_fg;
         ks->frame_index = sk.frame_index + 1;
@@ -460,7 +546,7 @@ struct FrameTiles {
 // |eta|^2, the non-finite count and (WM) U^T diag(c) U.
 template <int K, typename FT, bool WM>
 __device__ __forceinline__ void residual_pass(const FrameArgs &a, const FrameTiles &tl, const SKState<K> &sk,
-                                              float (&acc)[WM ? FCfg<K>::NPR : FCfg<K>::NPF])
+                                              float (&acc)[WM ? FCfg<K>::NPR : FCfg<K>::NPF], int t0)
 {
     using F = FCfg<K>;
     constexpr int TP = F::TP, RW = F::RW, IPT = F::IPT;
@@ -473,7 +559,8 @@ __device__ __forceinline__ void residual_pass(const FrameArgs &a, const FrameTil
     const float sc = prm.in_scale, of = prm.in_offset;
     const FT *frame = static_cast<const FT *>(a.frame);
     const int nitems = tl.nres * IPT;
-    for (int it = threadIdx.x; it < nitems; it += F::THREADS) {
+    if ((int)threadIdx.x < t0) return; // threads [0, t0) do other work this pass
+    for (int it = threadIdx.x - t0; it < nitems; it += F::THREADS - t0) {
         const int ti = tl.r0 + it / IPT;
         const int rp = it - (it / IPT) * IPT;
         const int c = ti / prm.npt;
@@ -530,7 +617,7 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
     __shared__ float sred[NW * F::NPMAX];
     __shared__ float tot[F::NVR > F::NVU ? F::NVR : F::NVU];
     __shared__ float rscr[NT];
-    __shared__ double sR[K * K], sT[K * K], sW[K * K];
+    __shared__ ReorthScratch<K> rs;
     __shared__ SKState<K> sk;
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -548,6 +635,7 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
     for (int i = tid; i < K * K; i += NT) {
         sk.Tf[i] = a.ks->Tf[i];
         sk.Rf[i] = (float)a.ks->R[(i / K) * KMAX + (i % K)];
+        rs.Told[i] = a.ks->T[(i / K) * KMAX + (i % K)];
     }
     if (tid < K) {
         sk.y[tid] = a.ks->y[tid];
@@ -568,12 +656,13 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
         float *row = a.partials + ((size_t)buf * G + b) * a.row_stride;
         const float *rows = a.partials + (size_t)buf * G * a.row_stride;
         target += (unsigned long long)G;
+        const int t0 = 0;
         if (pass < prm.n_cg) {
             float acc[F::NPR];
 #pragma unroll
             for (int i = 0; i < F::NPR; ++i) acc[i] = 0.f;
             const bool trace = stats && tid == 0 && pass == 1;
-            residual_pass<K, FT, true>(a, tl, sk, acc);
+            residual_pass<K, FT, true>(a, tl, sk, acc, t0);
             if (trace) a.ks->sub_ts[0] = global_ns();
             cons_partials<F::NPR, NW>(acc, F::NVR, row, sred);
             if (trace) a.ks->sub_ts[1] = global_ns();
@@ -587,7 +676,7 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
             float acc[F::NPF];
 #pragma unroll
             for (int i = 0; i < F::NPF; ++i) acc[i] = 0.f;
-            residual_pass<K, FT, false>(a, tl, sk, acc);
+            residual_pass<K, FT, false>(a, tl, sk, acc, t0);
             cons_partials<F::NPF, NW>(acc, F::NVF, row, sred);
             if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
             reduce_rows<F::NVF, NT>(rows, G, a.row_stride, tot, rscr);
@@ -615,78 +704,86 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
         const volatile float *vg = sk.tg;
         const volatile float *vw = sk.w;
         const FT *frame = static_cast<const FT *>(a.frame);
-        const int nitems = tl.nupt * IPT;
+        // one pixel per thread and item, all channels' rows loaded up front
+        // (the labels of Step 3 take the maximum over the channels)
+        constexpr int CM = 4;
+        const int nitems = tl.nupt * TP;
         for (int it = tid; it < nitems; it += NT) {
-            const int pt = tl.u0 + it / IPT;
-            const int rp = it - (it / IPT) * IPT;
-            const int64_t p = (int64_t)pt * TP + rp * RW;
-            const int nvalid = prm.P - p < RW ? (int)(prm.P - p) : RW;
-            float lb[RW], mx[RW];
-            ld2(a.labels + p, true, RW, lb);
+            const int pt = tl.u0 + it / TP;
+            const int r0 = it - (it / TP) * TP;
+            const int64_t p = (int64_t)pt * TP + r0;
+            const bool valid = p < prm.P;
+            float u[CM][K], xv[CM];
 #pragma unroll
-            for (int r = 0; r < RW; ++r) mx[r] = 0.f;
-            for (int c = 0; c < prm.C; ++c) {
-                float *ub = a.U + ((int64_t)c * prm.npt + pt) * K * TP + rp * RW;
-                float u[K][RW];
+            for (int c = 0; c < CM; ++c) {
+                if (c < prm.C) {
+                    const float *ub = a.U + ((int64_t)c * prm.npt + pt) * K * TP + r0;
 #pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    const float2 v = __ldcg(reinterpret_cast<const float2 *>(ub + j * TP));
-                    u[j][0] = v.x;
-                    u[j][1] = v.y;
+                    for (int j = 0; j < K; ++j) u[c][j] = __ldcg(ub + j * TP);
+                    xv[c] = valid ? (float)__ldg(frame + (int64_t)c * a.frame_pitch + p) : 0.f;
                 }
-                float xv[RW];
-                ld2(frame + (int64_t)c * a.frame_pitch + p, nvalid == RW, nvalid, xv);
+            }
+            const float wv = valid ? (a.labels[p] ? om : 1.f) : 0.f;
+            // dots of the orthonormal rows u = T^T u_st through T y, T g, T v;
+            // each k-space entry is read once per pixel for all channels
+            float uy[CM], ug[CM], uv[CM], gam[CM];
 #pragma unroll
-                for (int r = 0; r < RW; ++r) {
-                    const bool valid = r < nvalid;
-                    // dots of the orthonormal row u = T^T u_st through T y, T v, T g
-                    float uy = 0.f, ug = 0.f, uv = 0.f;
+            for (int c = 0; c < CM; ++c) uy[c] = ug[c] = uv[c] = 0.f;
 #pragma unroll
-                    for (int j = 0; j < K; ++j) {
-                        uy = fmaf(u[j][r], vy[j], uy);
-                        ug = fmaf(u[j][r], vg[j], ug);
-                        uv = fmaf(u[j][r], vv[j], uv);
-                    }
-                    const float x = fmaf(xv[r], sc, -of);
-                    const float res = valid ? x - uy : 0.f;
+            for (int j = 0; j < K; ++j) {
+                const float yj = vy[j], gj = vg[j], vj = vv[j];
+#pragma unroll
+                for (int c = 0; c < CM; ++c) {
+                    uy[c] = fmaf(u[c][j], yj, uy[c]);
+                    ug[c] = fmaf(u[c][j], gj, ug[c]);
+                    uv[c] = fmaf(u[c][j], vj, uv[c]);
+                }
+            }
+            float mx = 0.f;
+#pragma unroll
+            for (int c = 0; c < CM; ++c) {
+                gam[c] = 0.f;
+                if (c < prm.C) {
+                    const float x = fmaf(xv[c], sc, -of);
+                    const float res = valid ? x - uy[c] : 0.f;
                     const float z = fmaf(res, res, mu);
                     const float tz = __powf(z, e);
-                    const float wv = valid ? (lb[r] != 0.f ? om : 1.f) : 0.f;
                     const float eta = -pw * wv * tz * res;
                     // u <- u + ((cos(theta) - 1) u^T v - sin(theta) pi(eta)_e / |pi(eta)|) v
-                    const float gam = valid ? fmaf(cm1, uv, -snp * (eta - ug)) : 0.f;
-                    const float rn = pre ? res : fmaf(-gam, yn, res);
+                    gam[c] = valid ? fmaf(cm1, uv[c], -snp * (eta - ug[c])) : 0.f;
+                    const float rn = pre ? res : fmaf(-gam[c], yn, res);
                     if (valid) {
-                        mx[r] = fmaxf(mx[r], fabsf(rn));
-                        if (write && a.bg_out) a.bg_out[(int64_t)c * prm.P + p + r] = x - rn + of;
+                        mx = fmaxf(mx, fabsf(rn));
+                        if (write && a.bg_out) a.bg_out[(int64_t)c * prm.P + p] = x - rn + of;
                     }
-                    // stored row of u + gamma v: u_st + gamma R^T v
+                }
+            }
+            // stored rows of u + gamma v: u_st + gamma R^T v
 #pragma unroll
-                    for (int j = 0; j < K; ++j) u[j][r] = fmaf(gam, vw[j], u[j][r]);
+            for (int j = 0; j < K; ++j) {
+                const float wj = vw[j];
+#pragma unroll
+                for (int c = 0; c < CM; ++c) u[c][j] = fmaf(gam[c], wj, u[c][j]);
+            }
+#pragma unroll
+            for (int c = 0; c < CM; ++c) {
+                if (c < prm.C) {
 #pragma unroll
                     for (int j = 0; j < K; ++j)
 #pragma unroll
-                        for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[j][r], u[l2][r], acc[tri<K>(j, l2)]);
-                }
-                if (write) {
+                        for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[c][j], u[c][l2], acc[tri<K>(j, l2)]);
+                    if (write) {
+                        float *ub = a.U + ((int64_t)c * prm.npt + pt) * K * TP + r0;
 #pragma unroll
-                    for (int j = 0; j < K; ++j)
-                        *reinterpret_cast<float2 *>(ub + j * TP) = make_float2(u[j][0], u[j][1]);
+                        for (int j = 0; j < K; ++j) ub[j * TP] = u[c][j];
+                    }
                 }
             }
-            uint8_t nl[RW];
-#pragma unroll
-            for (int r = 0; r < RW; ++r) {
-                nl[r] = (r < nvalid && mx[r] >= dl) ? 1 : 0;
-                acc[NM] += (float)nl[r];
-            }
+            const uint8_t nl = (valid && mx >= dl) ? 1 : 0;
+            acc[NM] += (float)nl;
             if (write) {
-                *reinterpret_cast<uchar2 *>(a.labels + p) = make_uchar2(nl[0], nl[1]);
-                if (a.mask_out) {
-#pragma unroll
-                    for (int r = 0; r < RW; ++r)
-                        if (r < nvalid) a.mask_out[p + r] = nl[r];
-                }
+                a.labels[p] = nl;
+                if (a.mask_out && valid) a.mask_out[p] = nl;
             }
         }
     }
@@ -705,7 +802,8 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
     if (!sk.last) return;
     reduce_rows<F::NVU, NT>(a.partials + (size_t)buf * G * a.row_stride, G, a.row_stride, tot, rscr);
     if (tid == 0) a.ks->sub_ts[8] = global_ns();
-    if (warp == 0) finish_frame<K>(sk, a.ks, tot, tot[NM], sR, sT, sW);
+    end_frame<K, NT>(sk, a.ks, tot, tot[NM], rs);
+    if (tid == 0) a.ks->sub_ts[9] = global_ns();
     if (tid == 0) a.ks->phase_ts[prm.n_cg + 2] = global_ns();
 }
 

@@ -75,6 +75,7 @@ def lib():
         L.prost_set_state.argtypes = [vp, vp, sz]
         L.prost_set_timing.argtypes = [vp, C.c_int]
         L.prost_get_timing.argtypes = [vp, P(C.c_float), P(C.c_int)]
+        L.prost_get_trace.argtypes = [vp, P(C.c_uint64)]
         L.prost_cost_grad_static.argtypes = [P(prost_params), vp, P(C.c_double), vp, vp, vp,
                                              vp, vp]
         L.prost_destroy.argtypes = [vp]
@@ -240,6 +241,16 @@ def prost_get_timing(h):
     n = C.c_int(0)
     _check(lib().prost_get_timing(h, buf, C.byref(n)), h)
     return [buf[j] for j in range(n.value)]
+
+
+PROST_TRACE_LEN = PROST_MAX_CG + 13
+
+
+def prost_get_trace(h):
+    """Raw %globaltimer stamps (ns) of the last frame (see include/prost.h)."""
+    buf = (C.c_uint64 * PROST_TRACE_LEN)()
+    _check(lib().prost_get_trace(h, buf), h)
+    return [int(v) for v in buf]
 
 
 def prost_cost_grad_static(params, U, y, frame, labels, out, status_out=None, stream=None):
