@@ -106,3 +106,92 @@ def test_stats_report_the_step_size_rule():
             assert st.frames == i + 1
     finally:
         pg.prost_destroy(h)
+
+
+def test_full_size_640x480_rgb_k10_in_the_benchmark_configuration():
+    """The benchmarked workload (640x480 RGB, k = 10, uint8 frames in device
+    memory, one prost_step per frame): teacher-forced parity of every output,
+    element by element, at frames 0 and 1 of an oracle trajectory."""
+    vid, wp = synth.make_workload("rgb640x480_k10", n_frames=3)
+    errs = _run_case(wp, vid, [0, 1])
+    print(errs)
+
+
+def _principal_angle_max(A, B):
+    qa, _ = np.linalg.qr(A.astype(np.float64))
+    qb, _ = np.linalg.qr(B.astype(np.float64))
+    s = np.linalg.svd(qa.T @ qb, compute_uv=False)
+    return float(np.arccos(np.clip(s.min(), -1.0, 1.0)))
+
+
+def test_free_running_trajectory_tracks_the_oracle():
+    """GPU and oracle each run 100 frames on their own from the same start.
+    FP32 rounding differs from FP64 by about 1e-7 per frame, and the tracking
+    dynamics do not amplify it: the subspaces stay within 1e-4 rad of each
+    other, and the labels agree except at isolated near-threshold pixels."""
+    vid, wp = synth.make_workload("gray160x120_k5", n_frames=100)
+    prm_o = oracle_params(wp)
+    U32, U64, y64 = matched_start(synth.random_orthonormal(vid.m, vid.k, 5), np.zeros(vid.k))
+    st = oracle.OracleState(U64.copy(), y64.copy(), np.zeros(vid.P, np.uint8), 0)
+    h = pg.prost_init(gpu_params(wp))
+    try:
+        pg.prost_set_subspace(h, U32)
+        dis, costs = [], []
+        for t in range(100):
+            f, _ = vid.frame(t)
+            m = np.empty(vid.P, np.uint8)
+            assert pg.prost_step(h, f, m) == pg.PROST_OK
+            res = oracle.frame_step(prm_o, st, f, want_residual=False)
+            dis.append(float((m != res.labels).mean()))
+            costs.append(abs(pg.prost_get_stats(h).cost[0] - res.trace.cost[0]) / res.trace.cost[0])
+        Ug = np.empty((vid.m, vid.k), np.float32)
+        pg.prost_get_subspace(h, Ug, np.empty(vid.k))
+    finally:
+        pg.prost_destroy(h)
+    ang = _principal_angle_max(Ug, st.U)
+    print("max angle", ang, "mean label disagreement", np.mean(dis), "max cost rel", max(costs))
+    assert ang < 1e-4
+    assert np.mean(dis) < 1e-3 and max(dis) < 1e-2
+    assert max(costs) < 1e-4
+
+
+def test_long_run_crosses_the_stored_basis_rebase():
+    """1,100 frames (the stored rows are rebased every 1,024): the exported
+    subspace stays orthonormal, follows the oracle, and a checkpoint taken
+    before the rebase resumes bit-identically across it."""
+    vid = synth.SyntheticVideo(32, 24, 1, 3, n_frames=1100, fg_fraction=0.05, walk_sigma=0.2,
+                               seed=31, dtype="f32")
+    wp = synth.video._params(vid.m, vid.k, "f32")
+    wp.update(width=32, height=24, channels=1, frame_dtype="f32", t_init=0.02, t_min=2e-3, i_init=50)
+    prm_o = oracle_params(wp)
+    U32, U64, y64 = matched_start(synth.random_orthonormal(vid.m, vid.k, 6), np.zeros(vid.k))
+    st = oracle.OracleState(U64.copy(), y64.copy(), np.zeros(vid.P, np.uint8), 0)
+    frames = vid.frames(0, 1100)
+    a = pg.prost_init(gpu_params(wp))
+    b = pg.prost_init(gpu_params(wp))
+    try:
+        pg.prost_set_subspace(a, U32)
+        m = np.empty(vid.P, np.uint8)
+        ck = None
+        for t in range(1100):
+            assert pg.prost_step(a, frames[t], m) == pg.PROST_OK
+            oracle.frame_step(prm_o, st, frames[t], want_residual=False)
+            if t == 1000:
+                ck = pg.prost_get_state(a)
+        Ua = np.empty((vid.m, vid.k), np.float32)
+        ya = np.empty(vid.k)
+        pg.prost_get_subspace(a, Ua, ya)
+        pg.prost_set_state(b, ck)
+        for t in range(1001, 1100):
+            assert pg.prost_step(b, frames[t], m) == pg.PROST_OK
+        Ub = np.empty((vid.m, vid.k), np.float32)
+        yb = np.empty(vid.k)
+        pg.prost_get_subspace(b, Ub, yb)
+    finally:
+        pg.prost_destroy(a)
+        pg.prost_destroy(b)
+    assert np.array_equal(Ua, Ub) and np.array_equal(ya, yb)
+    np.testing.assert_allclose(Ua.T.astype(np.float64) @ Ua, np.eye(vid.k), atol=2e-6)
+    ang = _principal_angle_max(Ua, st.U)
+    print("max angle after 1100 frames", ang)
+    assert ang < 1e-3
