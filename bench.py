@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--k", type=int, default=None, help="subspace dimension (default: the workload's)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -232,7 +233,9 @@ def run_ours(args, dist):
     dev = torch.device("cuda", dist.local)
     stream = torch.cuda.Stream(device=dev)
 
-    vid, wp = synth.make_workload(args.workload, seed=synth.WORKLOADS[args.workload]["video"]["seed"] + dist.rank)
+    over = {"k": args.k} if args.k else {}
+    vid, wp = synth.make_workload(args.workload, seed=synth.WORKLOADS[args.workload]["video"]["seed"] + dist.rank,
+                                  **over)
     K, W = args.steps, args.warmup
     n_frames = min(K + W, vid.n_frames)
     host = vid.frames(0, n_frames)

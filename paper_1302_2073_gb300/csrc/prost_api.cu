@@ -120,6 +120,9 @@ int check_params(const prost_params *prm, DevParams *dp, std::string *why)
         dp->k = p.k;
         dp->n_cg = p.n_cg;
         dp->mask_pre = p.mask_from == PROST_MASK_PRE_UPDATE;
+        // a subspace that L2 cannot hold across the passes of a frame is read
+        // from HBM in every pass; prefetching its tiles ahead hides the latency
+        dp->pf = (double)dp->C * (double)dp->Pp * p.k * sizeof(float) > 64.0 * (1 << 20);
         dp->p = (float)p.p;
         dp->mu = (float)mu;
         dp->delta = (float)p.delta;

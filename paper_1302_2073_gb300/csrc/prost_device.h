@@ -68,7 +68,7 @@ struct DevParams {
     int n_cg;         // CG iterations per frame
     int mask_pre;     // labels from the subspace before Step 2
     int npt;          // tiles per channel plane
-    int pad;
+    int pf;           // stream the stored rows with L2 prefetches (subspace larger than half of L2)
     float p, mu, delta, omega, in_scale, in_offset, e; // e = p/2 - 1
     float pad2;
     double pd, t_init, t_min, tau;

@@ -29,13 +29,18 @@
 #pragma once
 
 #include "prost_kernels.cuh"
+#include "prost_stage.cuh"
 
 namespace prost {
 
 template <int K> struct FCfg {
-    // 16 warps: at most 4 per SM sub-partition, so each thread may hold 128
-    // registers; one CTA per SM.
-    static constexpr int THREADS = 512;
+    // k <= 10: 16 warps (at most 4 per SM sub-partition, so each thread may
+    // hold 128 registers), rows loaded straight into registers; the subspace
+    // of the 640x480 workload stays in L2 across the passes of a frame.
+    // k >= 11: the streaming form (prost_stage.cuh), 8 warps of up to 255
+    // registers, rows staged through shared memory.  One CTA per SM.
+    static constexpr bool STREAM = K >= 11;
+    static constexpr int THREADS = STREAM ? 256 : 512;
     static constexpr int NW = THREADS / 32;
     static constexpr int TP = TILE_P;            // pixels per tile
     static constexpr int RW = 2;                 // rows per thread per item (8-byte loads)
@@ -162,6 +167,31 @@ __device__ __forceinline__ void cons_partials(float (&v)[N], int nv, float *out,
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int s = 0; s < PER; ++s) sred[w * N + lane * PER + s] = v[s];
+    cons_sync<NCW * 32>();
+    for (int i = threadIdx.x; i < nv; i += NCW * 32) {
+        float a = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < NCW; ++ww) a += sred[ww * N + i];
+        out[i] = a;
+    }
+    __threadfence();
+}
+
+// As cons_partials, with a plain shuffle tree per value (static indices
+// only): for the streaming form's long per-lane vectors, where the lane-
+// dependent selects of the split reduction would put the vector in local memory.
+template <int N, int NCW, int NA>
+__device__ __forceinline__ void cons_partials_tree(float (&v)[NA], int nv, float *out, float *sred)
+{
+    static_assert(N <= NA, "values beyond the array");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        float x = v[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
+        if (lane == (i & 31)) sred[w * N + i] = x;
+    }
     cons_sync<NCW * 32>();
     for (int i = threadIdx.x; i < nv; i += NCW * 32) {
         float a = 0.f;
@@ -619,6 +649,7 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
     __shared__ float rscr[NT];
     __shared__ ReorthScratch<K> rs;
     __shared__ SKState<K> sk;
+    extern __shared__ __align__(128) float stage_smem[]; // streaming form only
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const DevParams &prm = a.prm;
@@ -648,6 +679,7 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
     }
 
     const bool stats = b == 0;
+    float *wstage = stage_smem + (size_t)warp * STG_D * StageCfg<K, FT>::STAGE_F;
     int buf = 0;
     unsigned long long target = a.bar_base;
     if (stats && tid == 0) a.ks->phase_ts[0] = global_ns();
@@ -658,13 +690,19 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
         target += (unsigned long long)G;
         const int t0 = 0;
         if (pass < prm.n_cg) {
+            const bool trace = stats && tid == 0 && pass == 1;
             float acc[F::NPR];
 #pragma unroll
             for (int i = 0; i < F::NPR; ++i) acc[i] = 0.f;
-            const bool trace = stats && tid == 0 && pass == 1;
-            residual_pass<K, FT, true>(a, tl, sk, acc, t0);
+            if constexpr (F::STREAM)
+                stream_residual<K, FT, true, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
+            else
+                residual_pass<K, FT, true>(a, tl, sk, acc, t0);
             if (trace) a.ks->sub_ts[0] = global_ns();
-            cons_partials<F::NPR, NW>(acc, F::NVR, row, sred);
+            if constexpr (F::STREAM)
+                cons_partials_tree<F::NVR, NW>(acc, F::NVR, row, sred);
+            else
+                cons_partials<F::NPR, NW>(acc, F::NVR, row, sred);
             if (trace) a.ks->sub_ts[1] = global_ns();
             if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
             if (trace) a.ks->sub_ts[2] = global_ns();
@@ -676,8 +714,14 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
             float acc[F::NPF];
 #pragma unroll
             for (int i = 0; i < F::NPF; ++i) acc[i] = 0.f;
-            residual_pass<K, FT, false>(a, tl, sk, acc, t0);
-            cons_partials<F::NPF, NW>(acc, F::NVF, row, sred);
+            if constexpr (F::STREAM)
+                stream_residual<K, FT, false, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
+            else
+                residual_pass<K, FT, false>(a, tl, sk, acc, t0);
+            if constexpr (F::STREAM)
+                cons_partials_tree<F::NVF, NW>(acc, F::NVF, row, sred);
+            else
+                cons_partials<F::NPF, NW>(acc, F::NVF, row, sred);
             if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
             reduce_rows<F::NVF, NT>(rows, G, a.row_stride, tot, rscr);
             if (warp == 0) kspace_cg<K, false>(sk, prm, tot, pass, a.ks, stats);
@@ -688,6 +732,23 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
     }
 
     // ---- update pass: Step 2 on every row, Step 3 labels, Gram of the new rows ----
+    float *row = a.partials + ((size_t)buf * G + b) * a.row_stride;
+    if constexpr (F::STREAM) {
+        float acc[F::NPU];
+#pragma unroll
+        for (int i = 0; i < F::NPU; ++i) acc[i] = 0.f;
+        UpdVecs<K> kv;
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            kv.ty[j] = sk.yf[j];
+            kv.tg[j] = sk.tg[j];
+            kv.tv[j] = sk.tv[j];
+            kv.w[j] = sk.w[j];
+        }
+        stream_update<K, FT, NW>(a, tl.u0, tl.nupt, kv, sk.cm1, sk.snp, sk.yn, !sk.skip, wstage, acc);
+        if (tid == 0 && stats) a.ks->sub_ts[5] = global_ns();
+        cons_partials_tree<F::NVU, NW>(acc, F::NVU, row, sred);
+    } else {
     float acc[F::NPU];
 #pragma unroll
     for (int i = 0; i < F::NPU; ++i) acc[i] = 0.f;
@@ -788,8 +849,8 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
         }
     }
     if (tid == 0 && stats) a.ks->sub_ts[5] = global_ns();
-    float *row = a.partials + ((size_t)buf * G + b) * a.row_stride;
     cons_partials<F::NPU, NW>(acc, F::NVU, row, sred);
+    }
     cons_sync<NT>();
     if (tid == 0 && stats) a.ks->sub_ts[6] = global_ns();
     if (tid == 0) {
@@ -808,10 +869,16 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
 }
 
 template <int K> struct FrameOps {
+    // dynamic shared memory: the per-warp stages of the streaming form
+    template <typename FT> static constexpr int dyn_smem()
+    {
+        return FCfg<K>::STREAM ? FCfg<K>::NW * STG_D * StageCfg<K, FT>::STAGE_F * 4 : 0;
+    }
     template <typename FT> static cudaError_t launch_t(const FrameArgs &a, int grid, cudaStream_t s)
     {
         void *args[] = {const_cast<FrameArgs *>(&a)};
-        return cudaLaunchCooperativeKernel((void *)k_frame<K, FT>, dim3(grid), dim3(FCfg<K>::THREADS), args, 0, s);
+        return cudaLaunchCooperativeKernel((void *)k_frame<K, FT>, dim3(grid), dim3(FCfg<K>::THREADS), args,
+                                           dyn_smem<FT>(), s);
     }
     static cudaError_t launch(const FrameArgs &a, int fdt, int grid, cudaStream_t s)
     {
@@ -820,7 +887,12 @@ template <int K> struct FrameOps {
     template <typename FT> static int prepare_t()
     {
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_frame<K, FT>, FCfg<K>::THREADS, 0) != cudaSuccess)
+        if (dyn_smem<FT>() > 0 &&
+            cudaFuncSetAttribute(k_frame<K, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem<FT>()) !=
+                cudaSuccess)
+            return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_frame<K, FT>, FCfg<K>::THREADS, dyn_smem<FT>()) !=
+            cudaSuccess)
             return 0;
         return n;
     }

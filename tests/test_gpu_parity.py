@@ -66,13 +66,25 @@ def test_rgb_ragged_unaligned_planes_uint8():
     _run_case(wp, vid, [0, 1, 5])
 
 
+def test_rgb_ragged_two_lanes_per_row_forms():
+    # k = 15 (odd: a zero column in the rotated halves) and k = 9 (update pass
+    # split only) on 3 channels with ragged, unaligned planes
+    for k in (9, 15):
+        vid = synth.SyntheticVideo(37, 29, 3, k, n_frames=4, fg_fraction=0.1, shape="ellipse",
+                                   jitter=1, seed=300 + k, dtype="u8")
+        wp = synth.video._params(vid.m, vid.k, "u8")
+        wp.update(width=37, height=29, channels=3, frame_dtype="u8")
+        _run_case(wp, vid, [0, 2])
+        _run_case(wp, vid, [1], mask_from=pg.PROST_MASK_PRE_UPDATE)
+
+
 def test_rgb_64x48_k10_host_buffers_and_pre_update_labels():
     vid, wp = synth.make_workload("rgb640x480_k10", width=64, height=48, n_frames=6)
     _run_case(wp, vid, [0, 3], device=False)
     _run_case(wp, vid, [0, 3], mask_from=pg.PROST_MASK_PRE_UPDATE)
 
 
-@pytest.mark.parametrize("k", [1, 2, 7, 12, 16])
+@pytest.mark.parametrize("k", [1, 2, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16])
 def test_subspace_dimensions(k):
     vid = synth.SyntheticVideo(50, 40, 1, k, n_frames=4, fg_fraction=0.05, seed=100 + k, dtype="f32")
     wp = synth.video._params(vid.m, k, "f32")
