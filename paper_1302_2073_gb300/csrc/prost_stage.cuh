@@ -24,7 +24,7 @@
 
 namespace prost {
 
-constexpr int STG_D = 5;      // steps in flight per warp
+constexpr int STG_D = 8;      // steps in flight per warp
 constexpr int STG_ROWS = 32;  // rows per step (one per lane)
 static_assert(TILE_P % STG_ROWS == 0, "whole steps per tile");
 
@@ -187,9 +187,11 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
             cnval = (int)min((int64_t)TILE_P, prm.P - (int64_t)ctp * TILE_P);
         }
         const float xv = valid ? (float)xraw : 0.f;
-        float uy = 0.f;
+        // u . y in four independent partial sums (shorter dependency chain)
+        float uq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < K; ++j) uy = fmaf(u[j], y[j], uy);
+        for (int j = 0; j < K; ++j) uq[j & 3] = fmaf(u[j], y[j], uq[j & 3]);
+        const float uy = (uq[0] + uq[1]) + (uq[2] + uq[3]);
         if constexpr (sizeof(FT) == 4) {
             if (valid && !isfinite(xv)) acc[K + NM + 2] += 1.f;
         }
@@ -287,13 +289,14 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
             mx = 0.f;
         }
         const float x = valid ? fmaf((float)xraw, sc, -of) : 0.f;
-        float uy = 0.f, ug = 0.f, uv = 0.f;
+        float dy[2] = {0.f, 0.f}, dg[2] = {0.f, 0.f}, dv[2] = {0.f, 0.f};
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            uy = fmaf(u[j], kv.ty[j], uy);
-            ug = fmaf(u[j], kv.tg[j], ug);
-            uv = fmaf(u[j], kv.tv[j], uv);
+            dy[j & 1] = fmaf(u[j], kv.ty[j], dy[j & 1]);
+            dg[j & 1] = fmaf(u[j], kv.tg[j], dg[j & 1]);
+            dv[j & 1] = fmaf(u[j], kv.tv[j], dv[j & 1]);
         }
+        const float uy = dy[0] + dy[1], ug = dg[0] + dg[1], uv = dv[0] + dv[1];
         const float res = valid ? x - uy : 0.f;
         const float z = fmaf(res, res, mu);
         const float tz = __powf(z, e);
