@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--k", type=int, default=None, help="subspace dimension (default: the workload's)")
+    ap.add_argument("--u-dtype", default="f32", choices=["f32", "bf16"], help="subspace storage")
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -255,6 +256,7 @@ def run_ours(args, dist):
     n_cg = wp["n_cg"]
     launches_per_step = 1
 
+    wp["u_dtype"] = args.u_dtype
     h = pg.prost_init(pg.make_params(**wp, seed=dist.rank + 1), stream=stream)
     try:
         pg.prost_set_timing(h, True)

@@ -67,6 +67,14 @@ extern "C" {
 
 #define PROST_U8 0   /* frame entries uint8 */
 #define PROST_F32 1  /* frame entries float32; subspace storage float32 */
+#define PROST_BF16 2 /* subspace storage bfloat16 (u_dtype only): not in the paper.
+                      * The stored rows are rounded stochastically at every
+                      * update (unbiased, so that updates below half an ulp are
+                      * not lost), all arithmetic stays FP32 with the k x k
+                      * Cholesky-QR at FP64 accuracy, and the subspace streams
+                      * at half the bytes.  The results differ from the FP32
+                      * storage by the rounding; the error against the FP64
+                      * reference is a measured quantity, not a bound. */
 
 #define PROST_MASK_POST_UPDATE 0 /* Step 3 uses the subspace after Step 2 (default) */
 #define PROST_MASK_PRE_UPDATE 1  /* Step 3 uses the subspace before Step 2 */
@@ -88,7 +96,7 @@ typedef struct prost_params {
     int32_t n_cg;                    /* CG iterations per frame, 0 <= n_cg <= PROST_MAX_CG (paper: 5) */
     double in_scale, in_offset;      /* x = in_scale * frame - in_offset */
     int32_t frame_dtype;             /* PROST_U8 or PROST_F32 */
-    int32_t u_dtype;                 /* PROST_F32 */
+    int32_t u_dtype;                 /* PROST_F32 or PROST_BF16 (subspace storage) */
     int32_t mask_from;               /* PROST_MASK_POST_UPDATE or PROST_MASK_PRE_UPDATE */
     int32_t reserved;                /* must be 0 */
     uint64_t seed;                   /* seed of the random initial subspace (Section 3.4) */

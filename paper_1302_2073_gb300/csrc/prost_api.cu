@@ -20,7 +20,7 @@ struct prost_handle {
     int device;
     int num_sms;
     int grid_frame, grid_gram;
-    float *U;              // stored subspace (C x npt tile blocks of k x TILE_P floats)
+    void *U;               // stored subspace (C x npt tile blocks of k x TILE_P float32 or bfloat16)
     uint8_t *labels;       // previous labels (Pp bytes)
     KState *ks;
     float *partials;
@@ -42,19 +42,26 @@ struct prost_handle {
 namespace {
 
 std::string g_init_err;
-const KernelOps *g_ops[KMAX + 1];
+const KernelOps *g_ops[2][KMAX + 1]; // [float32, bfloat16 subspace][k]
 std::once_flag g_ops_once;
 
 void load_ops()
 {
     std::call_once(g_ops_once, [] {
-        for (int i = 0; i <= KMAX; ++i) g_ops[i] = nullptr;
-        register_ops_k01_04(g_ops);
-        register_ops_k05_08(g_ops);
-        register_ops_k09_12(g_ops);
-        register_ops_k13_16(g_ops);
+        for (int i = 0; i <= KMAX; ++i) g_ops[0][i] = g_ops[1][i] = nullptr;
+        register_ops_k01_02(g_ops[0], g_ops[1]);
+        register_ops_k03_04(g_ops[0], g_ops[1]);
+        register_ops_k05_06(g_ops[0], g_ops[1]);
+        register_ops_k07_08(g_ops[0], g_ops[1]);
+        register_ops_k09_10(g_ops[0], g_ops[1]);
+        register_ops_k11_12(g_ops[0], g_ops[1]);
+        register_ops_k13_14(g_ops[0], g_ops[1]);
+        register_ops_k15_16(g_ops[0], g_ops[1]);
     });
 }
+
+// bytes of one stored subspace entry
+size_t u_elem_bytes(const DevParams &dp) { return dp.ubf16 ? 2 : 4; }
 
 // restores the caller's current device on scope exit
 struct DeviceGuard {
@@ -108,7 +115,7 @@ int check_params(const prost_params *prm, DevParams *dp, std::string *why)
     if (p.n_cg < 0 || p.n_cg > CGMAX) { *why = "n_cg must be in 0..32"; return PROST_EINVAL; }
     if (!isfinite(p.in_scale) || !isfinite(p.in_offset)) { *why = "in_scale and in_offset must be finite"; return PROST_EINVAL; }
     if (p.frame_dtype != PROST_U8 && p.frame_dtype != PROST_F32) { *why = "frame_dtype must be PROST_U8 or PROST_F32"; return PROST_EINVAL; }
-    if (p.u_dtype != PROST_F32) { *why = "u_dtype must be PROST_F32"; return PROST_EINVAL; }
+    if (p.u_dtype != PROST_F32 && p.u_dtype != PROST_BF16) { *why = "u_dtype must be PROST_F32 or PROST_BF16"; return PROST_EINVAL; }
     if (p.mask_from != PROST_MASK_POST_UPDATE && p.mask_from != PROST_MASK_PRE_UPDATE) { *why = "mask_from must be 0 or 1"; return PROST_EINVAL; }
     if (p.reserved != 0) { *why = "reserved must be 0"; return PROST_EINVAL; }
     if (dp) {
@@ -120,9 +127,8 @@ int check_params(const prost_params *prm, DevParams *dp, std::string *why)
         dp->k = p.k;
         dp->n_cg = p.n_cg;
         dp->mask_pre = p.mask_from == PROST_MASK_PRE_UPDATE;
-        // a subspace that L2 cannot hold across the passes of a frame is read
-        // from HBM in every pass; prefetching its tiles ahead hides the latency
-        dp->pf = (double)dp->C * (double)dp->Pp * p.k * sizeof(float) > 64.0 * (1 << 20);
+        dp->ubf16 = p.u_dtype == PROST_BF16;
+        dp->sr_seed = (uint32_t)(p.seed ^ (p.seed >> 32)) ^ 0x5bd1e995u;
         dp->p = (float)p.p;
         dp->mu = (float)mu;
         dp->delta = (float)p.delta;
@@ -183,6 +189,16 @@ int run_gram(prost_handle *h)
     return PROST_OK;
 }
 
+// Move the stored rows onto the orthonormal representative (U_st <- U_st T,
+// T <- I).  A bfloat16 subspace is rounded in the move, so its Gram and
+// Cholesky-QR are taken again of the stored values.
+int rebase(prost_handle *h)
+{
+    CK(h, h->ops->rebase(h->U, h->ks, h->dp, h->stream));
+    if (h->dp.ubf16) return run_gram(h);
+    return PROST_OK;
+}
+
 int read_status(prost_handle *h, int *status)
 {
     CK(h, cudaMemcpyAsync(h->h_word, &h->ks->last_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
@@ -233,7 +249,7 @@ int prost_state_bytes(const prost_params *prm, size_t *bytes)
     if (rc) return rc;
     if (!bytes) return PROST_EINVAL;
     const int64_t m = m_of(*prm);
-    size_t b = (size_t)prm->k * dp.C * dp.Pp * sizeof(float) + (size_t)dp.Pp + sizeof(KState) +
+    size_t b = (size_t)prm->k * dp.C * dp.Pp * u_elem_bytes(dp) + (size_t)dp.Pp + sizeof(KState) +
                sizeof(unsigned int) + sizeof(GridBar) + (size_t)4096 * partial_row(prm->k) * sizeof(float) +
                (size_t)dp.C * dp.Pp * frame_elem_bytes(*prm);
     (void)m;
@@ -250,7 +266,7 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     int rc = check_params(prm, &dp, &why);
     if (rc) { g_init_err = why; return rc; }
     load_ops();
-    const KernelOps *ops = g_ops[prm->k];
+    const KernelOps *ops = g_ops[prm->u_dtype == PROST_BF16 ? 1 : 0][prm->k];
     if (!ops) { g_init_err = "no kernel set for this k"; return PROST_EINVAL; }
 
     prost_handle *h = new (std::nothrow) prost_handle();
@@ -296,7 +312,7 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     if (h->grid_gram > gmax) gmax = h->grid_gram;
     h->partial_floats = (size_t)gmax * partial_row(prm->k);
 
-    CKI(cudaMalloc(&h->U, (size_t)prm->k * dp.C * dp.Pp * sizeof(float)));
+    CKI(cudaMalloc(&h->U, (size_t)prm->k * dp.C * dp.Pp * u_elem_bytes(dp)));
     CKI(cudaMalloc(&h->labels, (size_t)dp.Pp));
     CKI(cudaMalloc(&h->ks, sizeof(KState)));
     CKI(cudaMalloc(&h->partials, h->partial_floats * sizeof(float)));
@@ -314,7 +330,8 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     rc = run_gram(h);
     if (rc) return bail(rc);
     // store the orthonormal factor itself, so that the stored rows start orthonormal
-    CKI(ops->rebase(h->U, h->ks, h->dp, h->stream));
+    rc = rebase(h);
+    if (rc) return bail(rc);
     int st = 0;
     rc = read_status(h, &st);
     if (rc) return bail(rc);
@@ -382,7 +399,8 @@ int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_
     // every REBASE_EVERY frames the stored rows are moved onto the orthonormal
     // representative so that the conditioning of U_st cannot drift.
     if (++h->steps_since_rebase >= REBASE_EVERY) {
-        CK(h, h->ops->rebase(h->U, h->ks, dp, h->stream));
+        const int rc = rebase(h);
+        if (rc) return rc;
         h->steps_since_rebase = 0;
     }
     if (on_device) return PROST_OK;
@@ -467,7 +485,8 @@ int prost_set_subspace(prost_handle *h, const float *U, const double *y, int on_
     if (rc) return rc;
     if (st == PROST_ENOTSPD) return fail(h, PROST_ENOTSPD, "subspace columns are not linearly independent");
     // store the orthonormal factor itself, so that the stored rows start orthonormal
-    CK(h, h->ops->rebase(h->U, h->ks, h->dp, h->stream));
+    rc = rebase(h);
+    if (rc) return rc;
     CK(h, cudaStreamSynchronize(h->stream));
     return PROST_OK;
 }
@@ -534,7 +553,7 @@ int prost_get_state(prost_handle *h, void *buf, size_t *len)
     if (!h || !len) return PROST_EINVAL;
     DeviceGuard dg(h->device);
     const DevParams &dp = h->dp;
-    const size_t u_bytes = (size_t)dp.k * dp.C * dp.Pp * sizeof(float); // the stored layout as is
+    const size_t u_bytes = (size_t)dp.k * dp.C * dp.Pp * u_elem_bytes(dp); // the stored layout as is
     const size_t need = sizeof(StateHeader) + u_bytes + sizeof(KState) + (size_t)dp.P;
     if (!buf) { *len = need; return PROST_OK; }
     if (*len < need) return fail(h, PROST_EINVAL, "buffer too small");
@@ -564,7 +583,7 @@ int prost_set_state(prost_handle *h, const void *buf, size_t len)
     if (!h || !buf) return PROST_EINVAL;
     DeviceGuard dg(h->device);
     const DevParams &dp = h->dp;
-    const size_t u_bytes = (size_t)dp.k * dp.C * dp.Pp * sizeof(float);
+    const size_t u_bytes = (size_t)dp.k * dp.C * dp.Pp * u_elem_bytes(dp);
     const size_t need = sizeof(StateHeader) + u_bytes + sizeof(KState) + (size_t)dp.P;
     if (len < sizeof(StateHeader)) return fail(h, PROST_EINVAL, "state buffer too short");
     StateHeader hd;

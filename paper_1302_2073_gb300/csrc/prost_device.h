@@ -68,9 +68,9 @@ struct DevParams {
     int n_cg;         // CG iterations per frame
     int mask_pre;     // labels from the subspace before Step 2
     int npt;          // tiles per channel plane
-    int pf;           // stream the stored rows with L2 prefetches (subspace larger than half of L2)
+    int ubf16;        // stored subspace in bfloat16 (else float32)
     float p, mu, delta, omega, in_scale, in_offset, e; // e = p/2 - 1
-    float pad2;
+    uint32_t sr_seed; // stochastic rounding of bfloat16 stores (from the handle's seed)
     double pd, t_init, t_min, tau;
 };
 
@@ -82,7 +82,7 @@ __host__ __device__ __forceinline__ int64_t u_off(const DevParams &prm, int c, i
 }
 
 struct GramArgs {
-    const float *U;
+    const void *U;    // stored subspace (float32 or bfloat16)
     KState *ks;
     float *partials;
     unsigned int *counter;
@@ -97,7 +97,7 @@ struct GridBar {
 };
 
 struct FrameArgs {
-    float *U;                 // stored subspace (tile-blocked, see DevParams)
+    void *U;                  // stored subspace (tile-blocked, see DevParams; float32 or bfloat16)
     const void *frame;        // channel planes frame_pitch entries apart (uint8 or float)
     uint8_t *labels;          // in: previous labels (weights); out: this frame's labels
     uint8_t *mask_out;        // optional copy of the labels (device, P bytes)
@@ -117,27 +117,31 @@ struct KernelOps {
     cudaError_t (*frame)(const FrameArgs &, int frame_dtype, int grid, cudaStream_t);
     int (*frame_prepare)(int frame_dtype); // resident frame-kernel CTAs per SM (0: cannot run)
     cudaError_t (*gram)(const GramArgs &, int grid, cudaStream_t);
-    cudaError_t (*export_u)(const float *U, const KState *ks, float *out, DevParams prm,
+    cudaError_t (*export_u)(const void *U, const KState *ks, float *out, DevParams prm,
                             cudaStream_t);
     int (*gram_occupancy)();
-    cudaError_t (*rebase)(float *U, KState *ks, DevParams prm, cudaStream_t);
+    cudaError_t (*rebase)(void *U, KState *ks, DevParams prm, cudaStream_t);
     int vw;        // pixels per thread of the Gram kernel
     int tile;      // pixels per tile of the frame kernel
     int frame_threads;
 };
 
 // kernels without a k template
-cudaError_t launch_init_gauss(float *U, DevParams prm, uint64_t seed, cudaStream_t s);
-cudaError_t launch_import_u(const float *Urow, float *U, DevParams prm, cudaStream_t s);
+cudaError_t launch_init_gauss(void *U, DevParams prm, uint64_t seed, cudaStream_t s);
+cudaError_t launch_import_u(const float *Urow, void *U, DevParams prm, cudaStream_t s);
 cudaError_t launch_import_labels(const uint8_t *src, uint8_t *labels, DevParams prm,
                                  cudaStream_t s);
 // after a rebase: R = T = I and the stored-row coefficients equal y
 cudaError_t launch_reset_fold(KState *ks, DevParams prm, cudaStream_t s);
 
 // per-k kernel sets, filled by the instantiation units
-void register_ops_k01_04(const KernelOps **table);
-void register_ops_k05_08(const KernelOps **table);
-void register_ops_k09_12(const KernelOps **table);
-void register_ops_k13_16(const KernelOps **table);
+void register_ops_k01_02(const KernelOps **f32, const KernelOps **bf16);
+void register_ops_k03_04(const KernelOps **f32, const KernelOps **bf16);
+void register_ops_k05_06(const KernelOps **f32, const KernelOps **bf16);
+void register_ops_k07_08(const KernelOps **f32, const KernelOps **bf16);
+void register_ops_k09_10(const KernelOps **f32, const KernelOps **bf16);
+void register_ops_k11_12(const KernelOps **f32, const KernelOps **bf16);
+void register_ops_k13_14(const KernelOps **f32, const KernelOps **bf16);
+void register_ops_k15_16(const KernelOps **f32, const KernelOps **bf16);
 
 } // namespace prost

@@ -33,13 +33,14 @@
 
 namespace prost {
 
-template <int K> struct FCfg {
+template <int K, typename UT = float> struct FCfg {
     // k <= 10: 16 warps (at most 4 per SM sub-partition, so each thread may
     // hold 128 registers), rows loaded straight into registers; the subspace
     // of the 640x480 workload stays in L2 across the passes of a frame.
-    // k >= 11: the streaming form (prost_stage.cuh), 8 warps of up to 255
-    // registers, rows staged through shared memory.  One CTA per SM.
-    static constexpr bool STREAM = K >= 11;
+    // k >= 11, and any k with a bfloat16 subspace: the streaming form
+    // (prost_stage.cuh), 8 warps of up to 255 registers, rows staged through
+    // shared memory.  One CTA per SM.
+    static constexpr bool STREAM = K >= 11 || sizeof(UT) == 2;
     static constexpr int THREADS = STREAM ? 256 : 512;
     static constexpr int NW = THREADS / 32;
     static constexpr int TP = TILE_P;            // pixels per tile
@@ -596,7 +597,7 @@ __device__ __forceinline__ void residual_pass(const FrameArgs &a, const FrameTil
         const int c = ti / prm.npt;
         const int64_t p = (int64_t)(ti - c * prm.npt) * TP + rp * RW;
         const int nvalid = prm.P - p < RW ? (int)(prm.P - p) : RW;
-        const float *ub = a.U + (int64_t)ti * K * TP + rp * RW;
+        const float *ub = static_cast<const float *>(a.U) + (int64_t)ti * K * TP + rp * RW;
         float u[K][RW];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
@@ -638,10 +639,10 @@ __device__ __forceinline__ void residual_pass(const FrameArgs &a, const FrameTil
     }
 }
 
-template <int K, typename FT>
-__global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a)
+template <int K, typename FT, typename UT>
+__global__ void __launch_bounds__(FCfg<K, UT>::THREADS, 1) k_frame(const FrameArgs a)
 {
-    using F = FCfg<K>;
+    using F = FCfg<K, UT>;
     constexpr int TP = F::TP, RW = F::RW, IPT = F::IPT, NT = F::THREADS, NW = F::NW;
     constexpr int NM = F::NM;
     __shared__ float sred[NW * F::NPMAX];
@@ -679,7 +680,8 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
     }
 
     const bool stats = b == 0;
-    float *wstage = stage_smem + (size_t)warp * STG_D * StageCfg<K, FT>::STAGE_F;
+    unsigned char *wstage =
+        reinterpret_cast<unsigned char *>(stage_smem) + (size_t)warp * STG_D * StageCfg<K, FT, UT>::STAGE_B;
     int buf = 0;
     unsigned long long target = a.bar_base;
     if (stats && tid == 0) a.ks->phase_ts[0] = global_ns();
@@ -695,7 +697,7 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
 #pragma unroll
             for (int i = 0; i < F::NPR; ++i) acc[i] = 0.f;
             if constexpr (F::STREAM)
-                stream_residual<K, FT, true, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
+                stream_residual<K, FT, UT, true, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
             else
                 residual_pass<K, FT, true>(a, tl, sk, acc, t0);
             if (trace) a.ks->sub_ts[0] = global_ns();
@@ -715,7 +717,7 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
 #pragma unroll
             for (int i = 0; i < F::NPF; ++i) acc[i] = 0.f;
             if constexpr (F::STREAM)
-                stream_residual<K, FT, false, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
+                stream_residual<K, FT, UT, false, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
             else
                 residual_pass<K, FT, false>(a, tl, sk, acc, t0);
             if constexpr (F::STREAM)
@@ -745,7 +747,8 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
             kv.tv[j] = sk.tv[j];
             kv.w[j] = sk.w[j];
         }
-        stream_update<K, FT, NW>(a, tl.u0, tl.nupt, kv, sk.cm1, sk.snp, sk.yn, !sk.skip, wstage, acc);
+        const uint32_t sr_key = pcg_hash(prm.sr_seed ^ pcg_hash((uint32_t)sk.frame_index));
+        stream_update<K, FT, UT, NW>(a, tl.u0, tl.nupt, kv, sk.cm1, sk.snp, sk.yn, !sk.skip, sr_key, wstage, acc);
         if (tid == 0 && stats) a.ks->sub_ts[5] = global_ns();
         cons_partials_tree<F::NVU, NW>(acc, F::NVU, row, sred);
     } else {
@@ -778,7 +781,7 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
 #pragma unroll
             for (int c = 0; c < CM; ++c) {
                 if (c < prm.C) {
-                    const float *ub = a.U + ((int64_t)c * prm.npt + pt) * K * TP + r0;
+                    const float *ub = static_cast<const float *>(a.U) + ((int64_t)c * prm.npt + pt) * K * TP + r0;
 #pragma unroll
                     for (int j = 0; j < K; ++j) u[c][j] = __ldcg(ub + j * TP);
                     xv[c] = valid ? (float)__ldg(frame + (int64_t)c * a.frame_pitch + p) : 0.f;
@@ -834,7 +837,7 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
 #pragma unroll
                         for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[c][j], u[c][l2], acc[tri<K>(j, l2)]);
                     if (write) {
-                        float *ub = a.U + ((int64_t)c * prm.npt + pt) * K * TP + r0;
+                        float *ub = static_cast<float *>(a.U) + ((int64_t)c * prm.npt + pt) * K * TP + r0;
 #pragma unroll
                         for (int j = 0; j < K; ++j) ub[j * TP] = u[c][j];
                     }
@@ -868,16 +871,17 @@ __global__ void __launch_bounds__(FCfg<K>::THREADS, 1) k_frame(const FrameArgs a
     if (tid == 0) a.ks->phase_ts[prm.n_cg + 2] = global_ns();
 }
 
-template <int K> struct FrameOps {
+template <int K, typename UT> struct FrameOps {
+    using F = FCfg<K, UT>;
     // dynamic shared memory: the per-warp stages of the streaming form
     template <typename FT> static constexpr int dyn_smem()
     {
-        return FCfg<K>::STREAM ? FCfg<K>::NW * STG_D * StageCfg<K, FT>::STAGE_F * 4 : 0;
+        return F::STREAM ? F::NW * STG_D * StageCfg<K, FT, UT>::STAGE_B : 0;
     }
     template <typename FT> static cudaError_t launch_t(const FrameArgs &a, int grid, cudaStream_t s)
     {
         void *args[] = {const_cast<FrameArgs *>(&a)};
-        return cudaLaunchCooperativeKernel((void *)k_frame<K, FT>, dim3(grid), dim3(FCfg<K>::THREADS), args,
+        return cudaLaunchCooperativeKernel((void *)k_frame<K, FT, UT>, dim3(grid), dim3(F::THREADS), args,
                                            dyn_smem<FT>(), s);
     }
     static cudaError_t launch(const FrameArgs &a, int fdt, int grid, cudaStream_t s)
@@ -888,10 +892,10 @@ template <int K> struct FrameOps {
     {
         int n = 0;
         if (dyn_smem<FT>() > 0 &&
-            cudaFuncSetAttribute(k_frame<K, FT>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem<FT>()) !=
-                cudaSuccess)
+            cudaFuncSetAttribute(k_frame<K, FT, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 dyn_smem<FT>()) != cudaSuccess)
             return 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_frame<K, FT>, FCfg<K>::THREADS, dyn_smem<FT>()) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_frame<K, FT, UT>, F::THREADS, dyn_smem<FT>()) !=
             cudaSuccess)
             return 0;
         return n;
@@ -900,11 +904,11 @@ template <int K> struct FrameOps {
     static int prepare(int fdt) { return fdt == 0 ? prepare_t<uint8_t>() : prepare_t<float>(); }
 };
 
-template <int K> const KernelOps *kernel_table()
+template <int K, typename UT> const KernelOps *kernel_table()
 {
-    static const KernelOps ops = {&FrameOps<K>::launch, &FrameOps<K>::prepare, &Ops<K>::gram,
-                                  &Ops<K>::export_u, &Ops<K>::gram_occupancy, &Ops<K>::rebase,
-                                  Cfg<K>::VW, FCfg<K>::TP, FCfg<K>::THREADS};
+    static const KernelOps ops = {&FrameOps<K, UT>::launch, &FrameOps<K, UT>::prepare, &Ops<K, UT>::gram,
+                                  &Ops<K, UT>::export_u, &Ops<K, UT>::gram_occupancy, &Ops<K, UT>::rebase,
+                                  Cfg<K>::VW, FCfg<K, UT>::TP, FCfg<K, UT>::THREADS};
     return &ops;
 }
 

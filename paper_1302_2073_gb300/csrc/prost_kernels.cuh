@@ -9,6 +9,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
 #include "prost_device.h"
 
 namespace prost {
@@ -25,6 +27,37 @@ template <int K> __host__ __device__ constexpr int tri(int j, int l)
 }
 
 constexpr unsigned FULL = 0xffffffffu;
+
+// ---- stored-subspace element types -----------------------------------------
+
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ float ld_u(const float *p) { return *p; }
+__device__ __forceinline__ float ld_u(const bf16 *p) { return __bfloat162float(*p); }
+__device__ __forceinline__ float ldg_u(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ldg_u(const bf16 *p) { return __bfloat162float(__ldg(p)); }
+// round to nearest (imports, rebase)
+__device__ __forceinline__ void st_u(float *p, float v) { *p = v; }
+__device__ __forceinline__ void st_u(bf16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
+// Counter-based 32-bit hash (the PCG output permutation applied to one LCG
+// step; Jarzynski and Olano, "Hash Functions for GPU Rendering", JCGT 2020).
+__device__ __forceinline__ uint32_t pcg_hash(uint32_t x)
+{
+    const uint32_t state = x * 747796405u + 2891336453u;
+    const uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+
+// v rounded to bfloat16 stochastically with the 16 random bits r: the bits
+// below the bfloat16 mantissa are a fraction of an ulp of |v|, and adding a
+// uniform 16-bit number before truncating rounds |v| up with exactly that
+// probability, so the rounding is unbiased (and zero stays zero).
+__device__ __forceinline__ float round_bf16_sr(float v, uint32_t r)
+{
+    const uint32_t b = (__float_as_uint(v) + (r & 0xffffu)) & 0xffff0000u;
+    return __uint_as_float(b);
+}
 
 // ---- vector loads and stores ------------------------------------------------
 
@@ -298,7 +331,7 @@ __device__ void finish_reorth(KState *ks, const double *G, double *sR, double *s
 // ---- per-pixel kernels -------------------------------------------------------
 
 // Gram of the stored subspace and its Cholesky-QR (after init / import).
-template <int K>
+template <int K, typename UT>
 __global__ void __launch_bounds__(THREADS) k_gram(const GramArgs a)
 {
     constexpr int VW = Cfg<K>::VW;
@@ -317,10 +350,17 @@ __global__ void __launch_bounds__(THREADS) k_gram(const GramArgs a)
     for (int it = blockIdx.x * THREADS + threadIdx.x; it < nitems; it += gridDim.x * THREADS) {
         const int blk = it / GPB;
         const int r0 = (it - blk * GPB) * VW;
-        const float *base = a.U + (int64_t)blk * K * TILE_P + r0;
+        const UT *base = static_cast<const UT *>(a.U) + (int64_t)blk * K * TILE_P + r0;
         float u[K][VW];
 #pragma unroll
-        for (int j = 0; j < K; ++j) VL<VW>::ldu(base + j * TILE_P, u[j]);
+        for (int j = 0; j < K; ++j) {
+            if constexpr (sizeof(UT) == 4) {
+                VL<VW>::ldu(reinterpret_cast<const float *>(base) + j * TILE_P, u[j]);
+            } else {
+#pragma unroll
+                for (int r = 0; r < VW; ++r) u[j][r] = ldg_u(base + j * TILE_P + r);
+            }
+        }
 #pragma unroll
         for (int r = 0; r < VW; ++r)
 #pragma unroll
@@ -336,8 +376,8 @@ __global__ void __launch_bounds__(THREADS) k_gram(const GramArgs a)
 }
 
 // Orthonormal representative U = U_st T, written m x k row-major.
-template <int K>
-__global__ void __launch_bounds__(THREADS) k_export(const float *U, const KState *ks, float *out,
+template <int K, typename UT>
+__global__ void __launch_bounds__(THREADS) k_export(const UT *U, const KState *ks, float *out,
                                                      DevParams prm)
 {
     __shared__ float sT[K * K];
@@ -349,7 +389,7 @@ __global__ void __launch_bounds__(THREADS) k_export(const float *U, const KState
         const int64_t q = e - (int64_t)c * prm.P;
         float u[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) u[j] = U[u_off(prm, c, q, j)];
+        for (int j = 0; j < K; ++j) u[j] = ld_u(U + u_off(prm, c, q, j));
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             float s = 0.f;
@@ -362,8 +402,8 @@ __global__ void __launch_bounds__(THREADS) k_export(const float *U, const KState
 
 // Rebase of the stored rows onto the orthonormal representative: U_st <- U_st T
 // (each row u_st becomes T^T u_st), after which the fold is the identity.
-template <int K>
-__global__ void __launch_bounds__(THREADS) k_rebase(float *U, const KState *ks, DevParams prm)
+template <int K, typename UT>
+__global__ void __launch_bounds__(THREADS) k_rebase(UT *U, const KState *ks, DevParams prm)
 {
     __shared__ float sT[K * K];
     for (int i = threadIdx.x; i < K * K; i += THREADS) sT[i] = ks->Tf[i];
@@ -372,10 +412,10 @@ __global__ void __launch_bounds__(THREADS) k_rebase(float *U, const KState *ks, 
     for (int64_t e = (int64_t)blockIdx.x * THREADS + threadIdx.x; e < rows; e += (int64_t)gridDim.x * THREADS) {
         const int c = (int)(e / prm.Pp);
         const int64_t q = e - (int64_t)c * prm.Pp;
-        float *base = U + u_off(prm, c, q, 0);
+        UT *base = U + u_off(prm, c, q, 0);
         float u[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) u[j] = base[(int64_t)j * TILE_P];
+        for (int j = 0; j < K; ++j) u[j] = ld_u(base + (int64_t)j * TILE_P);
 #pragma unroll
         for (int j = K - 1; j >= 0; --j) {
             float s = 0.f;
@@ -384,30 +424,30 @@ __global__ void __launch_bounds__(THREADS) k_rebase(float *U, const KState *ks, 
             u[j] = s;
         }
 #pragma unroll
-        for (int j = 0; j < K; ++j) base[(int64_t)j * TILE_P] = u[j];
+        for (int j = 0; j < K; ++j) st_u(base + (int64_t)j * TILE_P, u[j]);
     }
 }
 
 // ---- host launchers of one kernel set ----------------------------------------
 
-template <int K> struct Ops {
+template <int K, typename UT> struct Ops {
     static cudaError_t gram(const GramArgs &a, int grid, cudaStream_t s)
     {
-        k_gram<K><<<grid, THREADS, 0, s>>>(a);
+        k_gram<K, UT><<<grid, THREADS, 0, s>>>(a);
         return cudaGetLastError();
     }
-    static cudaError_t export_u(const float *U, const KState *ks, float *out, DevParams prm, cudaStream_t s)
+    static cudaError_t export_u(const void *U, const KState *ks, float *out, DevParams prm, cudaStream_t s)
     {
         const int64_t m = (int64_t)prm.C * prm.P;
         const int64_t nb = (m + THREADS - 1) / THREADS;
         const int grid = (int)(nb < 4096 ? nb : 4096);
-        k_export<K><<<grid, THREADS, 0, s>>>(U, ks, out, prm);
+        k_export<K, UT><<<grid, THREADS, 0, s>>>(static_cast<const UT *>(U), ks, out, prm);
         return cudaGetLastError();
     }
-    static cudaError_t rebase(float *U, KState *ks, DevParams prm, cudaStream_t s)
+    static cudaError_t rebase(void *U, KState *ks, DevParams prm, cudaStream_t s)
     {
         const int64_t nb = ((int64_t)prm.C * prm.Pp + THREADS - 1) / THREADS;
-        k_rebase<K><<<(int)(nb < 4096 ? nb : 4096), THREADS, 0, s>>>(U, ks, prm);
+        k_rebase<K, UT><<<(int)(nb < 4096 ? nb : 4096), THREADS, 0, s>>>(static_cast<UT *>(U), ks, prm);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         return launch_reset_fold(ks, prm, s);
@@ -415,7 +455,7 @@ template <int K> struct Ops {
     static int gram_occupancy()
     {
         int n = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gram<K>, THREADS, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_gram<K, UT>, THREADS, 0);
         return e == cudaSuccess && n > 0 ? n : 1;
     }
 };

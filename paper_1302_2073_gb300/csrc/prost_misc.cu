@@ -3,6 +3,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cuda_bf16.h>
+
 #include "prost_device.h"
 
 namespace prost {
@@ -40,7 +42,11 @@ __device__ __forceinline__ void u_coords(const DevParams &prm, int64_t i, int64_
 
 // U_st = N(0, 1)/sqrt(m) per entry (padding rows 0); its Cholesky-QR (run
 // next) gives the orthonormal factor of a random m x k matrix (Section 3.4).
-__global__ void k_init_gauss(float *U, DevParams prm, uint64_t seed)
+__device__ __forceinline__ void store(float *p, float v) { *p = v; }
+__device__ __forceinline__ void store(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+
+template <typename UT>
+__global__ void k_init_gauss(UT *U, DevParams prm, uint64_t seed)
 {
     const int64_t n = (int64_t)prm.C * prm.Pp * prm.k;
     const float s = rsqrtf((float)((double)prm.C * (double)prm.P));
@@ -51,12 +57,13 @@ __global__ void k_init_gauss(float *U, DevParams prm, uint64_t seed)
         u_coords(prm, i, c, q, j);
         float v = 0.f;
         if (q < prm.P) v = s * gauss(seed, (uint64_t)((c * prm.P + q) * prm.k + j));
-        U[i] = v;
+        store(U + i, v);
     }
 }
 
 // m x k row-major -> tile-blocked stored layout
-__global__ void k_import_u(const float *Urow, float *U, DevParams prm)
+template <typename UT>
+__global__ void k_import_u(const float *Urow, UT *U, DevParams prm)
 {
     const int64_t n = (int64_t)prm.C * prm.Pp * prm.k;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -64,7 +71,7 @@ __global__ void k_import_u(const float *Urow, float *U, DevParams prm)
         int64_t c, q;
         int j;
         u_coords(prm, i, c, q, j);
-        U[i] = q < prm.P ? Urow[(c * prm.P + q) * prm.k + j] : 0.f;
+        store(U + i, q < prm.P ? Urow[(c * prm.P + q) * prm.k + j] : 0.f);
     }
 }
 
@@ -91,15 +98,23 @@ static int grid_for(int64_t n)
     return (int)(b < 8192 ? (b > 0 ? b : 1) : 8192);
 }
 
-cudaError_t launch_init_gauss(float *U, DevParams prm, uint64_t seed, cudaStream_t s)
+cudaError_t launch_init_gauss(void *U, DevParams prm, uint64_t seed, cudaStream_t s)
 {
-    k_init_gauss<<<grid_for((int64_t)prm.C * prm.Pp * prm.k), THREADS, 0, s>>>(U, prm, seed);
+    const int g = grid_for((int64_t)prm.C * prm.Pp * prm.k);
+    if (prm.ubf16)
+        k_init_gauss<<<g, THREADS, 0, s>>>(static_cast<__nv_bfloat16 *>(U), prm, seed);
+    else
+        k_init_gauss<<<g, THREADS, 0, s>>>(static_cast<float *>(U), prm, seed);
     return cudaGetLastError();
 }
 
-cudaError_t launch_import_u(const float *Urow, float *U, DevParams prm, cudaStream_t s)
+cudaError_t launch_import_u(const float *Urow, void *U, DevParams prm, cudaStream_t s)
 {
-    k_import_u<<<grid_for((int64_t)prm.C * prm.Pp * prm.k), THREADS, 0, s>>>(Urow, U, prm);
+    const int g = grid_for((int64_t)prm.C * prm.Pp * prm.k);
+    if (prm.ubf16)
+        k_import_u<<<g, THREADS, 0, s>>>(Urow, static_cast<__nv_bfloat16 *>(U), prm);
+    else
+        k_import_u<<<g, THREADS, 0, s>>>(Urow, static_cast<float *>(U), prm);
     return cudaGetLastError();
 }
 

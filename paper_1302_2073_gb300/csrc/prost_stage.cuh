@@ -28,16 +28,16 @@ constexpr int STG_D = 8;      // steps in flight per warp
 constexpr int STG_ROWS = 32;  // rows per step (one per lane)
 static_assert(TILE_P % STG_ROWS == 0, "whole steps per tile");
 
-template <int K, typename FT> struct StageCfg {
-    static constexpr int F_OFF = STG_ROWS * K;                          // floats
-    static constexpr int F_F = STG_ROWS * (int)sizeof(FT) / 4;
-    static constexpr int L_OFF = F_OFF + F_F;
-    static constexpr int STAGE_F = (L_OFF + STG_ROWS / 4 + 7) / 8 * 8;  // 32-byte multiple
-    static constexpr int NCU = K * STG_ROWS * 4 / 16;                   // 16-byte chunks: subspace
-    static constexpr int NCF = STG_ROWS * (int)sizeof(FT) / 16;         // frame entries
-    static constexpr int NCL = STG_ROWS / 16;                           // labels
+template <int K, typename FT, typename UT> struct StageCfg {
+    static constexpr int UB = STG_ROWS * K * (int)sizeof(UT);            // bytes of the subspace block
+    static constexpr int F_OFF = UB;                                     // byte offsets
+    static constexpr int L_OFF = F_OFF + STG_ROWS * (int)sizeof(FT);
+    static constexpr int STAGE_B = (L_OFF + STG_ROWS + 31) / 32 * 32;
+    static constexpr int CPC = STG_ROWS * (int)sizeof(UT) / 16;          // chunks per column
+    static constexpr int NCU = K * CPC;                                  // 16-byte chunks: subspace
+    static constexpr int NCF = STG_ROWS * (int)sizeof(FT) / 16;          // frame entries
+    static constexpr int NCL = STG_ROWS / 16;                            // labels
     static constexpr int NCH = NCU + NCF + NCL;
-    static constexpr int CPL = (NCH + 31) / 32;                         // chunks per lane
     static constexpr int STEPS_PER_TILE = TILE_P / STG_ROWS;
 };
 
@@ -59,37 +59,45 @@ template <int N> __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// This lane's chunks of a step: chunk q is number lane + 32 q of the step.
-// kind 0: subspace column (element offset off from the tile's first row),
-// 1: frame entries (offset in rows), 2: labels (offset in rows), 3: none.
-template <int K, typename FT> struct Chunks {
-    using S = StageCfg<K, FT>;
-    int kind[S::CPL], off[S::CPL], soff[S::CPL];
+// This lane's chunks of a step.  Chunk number lane + 32 q of the step's
+// subspace block is column (lane / CPC) + q (32 / CPC) at row part
+// lane % CPC, so for the NQU whole rounds one base pointer per lane serves
+// and round q is a fixed offset away (immediate operands, no branches); the
+// last round mixes the remaining subspace chunks, the frame entries and the
+// labels.
+template <int K, typename FT, typename UT> struct Chunks {
+    using S = StageCfg<K, FT, UT>;
+    static constexpr int NQU = S::NCU / 32;                    // whole rounds of subspace chunks
+    static constexpr int TR = (S::NCH - 32 * NQU + 31) / 32;   // rounds after them (1 or 2)
+    static constexpr int QCOL = 32 / S::CPC;                   // columns per round
+    static constexpr int RPC = 16 / (int)sizeof(UT);           // rows per subspace chunk
+    int uoff;      // element offset of this lane's subspace chunk in round 0
+    int soff;      // byte offset in the stage
+    int tkind[TR]; // later rounds: 0 subspace, 1 frame, 2 labels, 3 none
+    int toff[TR];  // later rounds: row offset (frame, labels) of this lane's chunk
+    int tsoff[TR]; // later rounds: byte offset in the stage
 
     __device__ __forceinline__ explicit Chunks(int lane)
     {
+        uoff = (lane / S::CPC) * TILE_P + (lane % S::CPC) * RPC;
+        soff = (lane / S::CPC) * STG_ROWS * (int)sizeof(UT) + 16 * (lane % S::CPC);
 #pragma unroll
-        for (int q = 0; q < S::CPL; ++q) {
-            const int ch = lane + 32 * q;
+        for (int r = 0; r < TR; ++r) {
+            const int ch = 32 * (NQU + r) + lane;
+            tsoff[r] = 0;
+            toff[r] = 0;
             if (ch < S::NCU) {
-                const int col = ch / (STG_ROWS / 4), part = ch % (STG_ROWS / 4);
-                kind[q] = 0;
-                off[q] = col * TILE_P + 4 * part;
-                soff[q] = STG_ROWS * col + 4 * part;
+                tkind[r] = 0;
             } else if (ch < S::NCU + S::NCF) {
-                const int part = ch - S::NCU;
-                kind[q] = 1;
-                off[q] = part * (16 / (int)sizeof(FT));
-                soff[q] = S::F_OFF + 4 * part;
+                tkind[r] = 1;
+                toff[r] = (ch - S::NCU) * (16 / (int)sizeof(FT));
+                tsoff[r] = S::F_OFF + 16 * (ch - S::NCU);
             } else if (ch < S::NCH) {
-                const int part = ch - S::NCU - S::NCF;
-                kind[q] = 2;
-                off[q] = 16 * part;
-                soff[q] = S::L_OFF + 4 * part;
+                tkind[r] = 2;
+                toff[r] = 16 * (ch - S::NCU - S::NCF);
+                tsoff[r] = S::L_OFF + 16 * (ch - S::NCU - S::NCF);
             } else {
-                kind[q] = 3;
-                off[q] = 0;
-                soff[q] = 0;
+                tkind[r] = 3;
             }
         }
     }
@@ -97,18 +105,22 @@ template <int K, typename FT> struct Chunks {
     // rows rs .. rs + 31 of a tile: its subspace block ut, the frame entries
     // and labels of its first pixel (ft, lt), nval rows inside the plane;
     // with_labels false leaves the label slots unwritten
-    __device__ __forceinline__ void issue(float *st, const float *ut, const FT *ft, const uint8_t *lt, int rs,
+    __device__ __forceinline__ void issue(unsigned char *st, const UT *ut, const FT *ft, const uint8_t *lt, int rs,
                                           int nval, bool with_labels) const
     {
+        const UT *src = ut + uoff + rs;
+        unsigned char *dst = st + soff;
 #pragma unroll
-        for (int q = 0; q < S::CPL; ++q) {
-            if (kind[q] == 0) {
-                cp_async16(st + soff[q], ut + off[q] + rs, true);
-            } else if (kind[q] == 1) {
-                const bool v = rs + off[q] < nval;
-                cp_async16(st + soff[q], v ? (const void *)(ft + rs + off[q]) : (const void *)lt, v);
-            } else if (kind[q] == 2 && with_labels) {
-                cp_async16(st + soff[q], lt + rs + off[q], true);
+        for (int q = 0; q < NQU; ++q) cp_async16(dst + q * 512, src + q * QCOL * TILE_P, true);
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+            if (tkind[r] == 0) {
+                cp_async16(dst + (NQU + r) * 512, src + (NQU + r) * QCOL * TILE_P, true);
+            } else if (tkind[r] == 1) {
+                const bool v = rs + toff[r] < nval;
+                cp_async16(st + tsoff[r], v ? (const void *)(ft + rs + toff[r]) : (const void *)lt, v);
+            } else if (tkind[r] == 2 && with_labels) {
+                cp_async16(st + tsoff[r], lt + rs + toff[r], true);
             }
         }
     }
@@ -117,14 +129,18 @@ template <int K, typename FT> struct Chunks {
 // One residual pass of this warp (all lanes) over its tiles r0 + warp,
 // r0 + warp + NW, ... of the CTA's range: per-lane sums [g_st (K) | (WM)
 // U_st^T diag(c) U_st packed | f | |eta|^2 | #non-finite], the standard
-// partial-row layout.
-template <int K, typename FT, bool WM, int NW, int NP>
-__device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int nres, const float *yf, float *wbuf,
-                                                float (&acc)[NP])
+// partial-row layout.  A tile is SPT = 7 steps and STG_D = SPT + 1, so the
+// copies run exactly one tile ahead: step s of tile t + 1 is issued while
+// step s of tile t is consumed (one pointer update per tile, a constant wait
+// depth, the steps of a tile unrolled).
+template <int K, typename FT, typename UT, bool WM, int NW, int NP>
+__device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int nres, const float *yf,
+                                                unsigned char *wbuf, float (&acc)[NP])
 {
-    using S = StageCfg<K, FT>;
+    using S = StageCfg<K, FT, UT>;
     constexpr int NM = WM ? K * (K + 1) / 2 : 0;
     constexpr int SPT = S::STEPS_PER_TILE;
+    static_assert(STG_D == SPT + 1, "the copies run one tile ahead");
     const DevParams &prm = a.prm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float y[K];
@@ -133,84 +149,88 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
     const float mu = prm.mu, e = prm.e, pw = prm.p, om = prm.omega;
     const float sc = prm.in_scale, of = prm.in_offset;
     const int npt = prm.npt;
-    const Chunks<K, FT> ch(lane);
+    const Chunks<K, FT, UT> ch(lane);
+    const UT *U = static_cast<const UT *>(a.U);
     const int ntile = nres > warp ? (nres - warp + NW - 1) / NW : 0;
-    const int nstep = ntile * SPT;
 
-    // issue side: tile iti (plane ic, index in plane itp), step is
-    int is = 0, iti = r0 + warp, ic = iti / npt, itp = iti - ic * npt;
-    const float *iut = a.U + (int64_t)iti * K * TILE_P;
-    const FT *ift = static_cast<const FT *>(a.frame) + (int64_t)ic * a.frame_pitch + (int64_t)itp * TILE_P;
-    const uint8_t *ilt = a.labels + (int64_t)itp * TILE_P;
-    int inval = (int)min((int64_t)TILE_P, prm.P - (int64_t)itp * TILE_P);
-    auto issue_next = [&](int k) {
-        if (k < nstep) {
-            ch.issue(wbuf + (k % STG_D) * S::STAGE_F, iut, ift, ilt, STG_ROWS * is, inval, true);
-            if (++is == SPT && k + 1 < nstep) {
-                is = 0;
-                iti += NW;
-                itp += NW;
-                while (itp >= npt) {
-                    itp -= npt;
-                    ++ic;
-                }
-                iut = a.U + (int64_t)iti * K * TILE_P;
-                ift = static_cast<const FT *>(a.frame) + (int64_t)ic * a.frame_pitch + (int64_t)itp * TILE_P;
-                ilt = a.labels + (int64_t)itp * TILE_P;
-                inval = (int)min((int64_t)TILE_P, prm.P - (int64_t)itp * TILE_P);
-            }
-        }
-        cp_async_commit();
+    // a tile of this warp: subspace block, frame and label rows, rows in plane
+    struct Tile {
+        const UT *ut;
+        const FT *ft;
+        const uint8_t *lt;
+        int nval;
     };
-#pragma unroll
-    for (int k = 0; k < STG_D - 1; ++k) issue_next(k);
-
-    // consume side: step cs of the tile whose index in its plane is ctp
-    int cs = 0, ctp = (r0 + warp) % npt;
-    int cnval = (int)min((int64_t)TILE_P, prm.P - (int64_t)ctp * TILE_P);
-    for (int k = 0; k < nstep; ++k) {
-        issue_next(k + STG_D - 1);
-        cp_async_wait<STG_D - 1>();
-        __syncwarp();
-        const float *st = wbuf + (k % STG_D) * S::STAGE_F;
-        float u[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) u[j] = st[STG_ROWS * j + lane];
-        const FT xraw = reinterpret_cast<const FT *>(st + S::F_OFF)[lane];
-        const uint8_t lb = reinterpret_cast<const uint8_t *>(st + S::L_OFF)[lane];
-        __syncwarp(); // the stage is refilled by a later step's copies
-        const bool valid = STG_ROWS * cs + lane < cnval;
-        if (++cs == SPT) {
-            cs = 0;
-            ctp += NW;
-            while (ctp >= npt) ctp -= npt;
-            cnval = (int)min((int64_t)TILE_P, prm.P - (int64_t)ctp * TILE_P);
+    int ti = r0 + warp, tc = ti / npt, tp = ti - tc * npt; // next tile to issue
+    auto make_tile = [&]() {
+        Tile t;
+        t.ut = U + (int64_t)ti * K * TILE_P;
+        t.ft = static_cast<const FT *>(a.frame) + (int64_t)tc * a.frame_pitch + (int64_t)tp * TILE_P;
+        t.lt = a.labels + (int64_t)tp * TILE_P;
+        t.nval = (int)min((int64_t)TILE_P, prm.P - (int64_t)tp * TILE_P);
+        ti += NW;
+        tp += NW;
+        while (tp >= npt) {
+            tp -= npt;
+            ++tc;
         }
-        const float xv = valid ? (float)xraw : 0.f;
-        // u . y in four independent partial sums (shorter dependency chain)
-        float uq[4] = {0.f, 0.f, 0.f, 0.f};
+        return t;
+    };
+    Tile nxt = make_tile(), cur;
+    if (ntile > 0) {
 #pragma unroll
-        for (int j = 0; j < K; ++j) uq[j & 3] = fmaf(u[j], y[j], uq[j & 3]);
-        const float uy = (uq[0] + uq[1]) + (uq[2] + uq[3]);
-        if constexpr (sizeof(FT) == 4) {
-            if (valid && !isfinite(xv)) acc[K + NM + 2] += 1.f;
+        for (int s = 0; s < SPT; ++s) {
+            ch.issue(wbuf + s * S::STAGE_B, nxt.ut, nxt.ft, nxt.lt, STG_ROWS * s, nxt.nval, true);
+            cp_async_commit();
         }
-        const float res = valid ? fmaf(xv, sc, -of) - uy : 0.f;
-        const float z = fmaf(res, res, mu);
-        const float tz = __powf(z, e);
-        const float wv = valid ? (lb != 0 ? om : 1.f) : 0.f;
-        const float cw = wv * tz;
-        acc[K + NM] = fmaf(cw, z, acc[K + NM]);
-        const float eta = -pw * cw * res;
-        acc[K + NM + 1] = fmaf(eta, eta, acc[K + NM + 1]);
+    }
+    for (int t = 0; t < ntile; ++t) {
+        cur = nxt;
+        const bool more = t + 1 < ntile;
+        if (more) nxt = make_tile();
+        const int kbase = SPT * t;
 #pragma unroll
-        for (int j = 0; j < K; ++j) acc[j] = fmaf(eta, u[j], acc[j]);
-        if constexpr (WM) {
+        for (int s = 0; s < SPT; ++s) {
+            const int k = kbase + s;
+            if (more)
+                ch.issue(wbuf + ((k + SPT) & (STG_D - 1)) * S::STAGE_B, nxt.ut, nxt.ft, nxt.lt, STG_ROWS * s,
+                         nxt.nval, true);
+            cp_async_commit();
+            cp_async_wait<STG_D - 1>();
+            __syncwarp();
+            const unsigned char *st = wbuf + (k & (STG_D - 1)) * S::STAGE_B;
+            float u[K];
 #pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const float cu = cw * u[j];
+            for (int j = 0; j < K; ++j) u[j] = ld_u(reinterpret_cast<const UT *>(st) + STG_ROWS * j + lane);
+            const FT xraw = reinterpret_cast<const FT *>(st + S::F_OFF)[lane];
+            const uint8_t lb = st[S::L_OFF + lane];
+            __syncwarp(); // the stage is refilled by a later step's copies
+            const bool valid = STG_ROWS * s + lane < cur.nval;
+            const float xv = valid ? (float)xraw : 0.f;
+            // u . y in four independent partial sums (shorter dependency chain)
+            float uq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int l2 = j; l2 < K; ++l2) acc[K + tri<K>(j, l2)] = fmaf(cu, u[l2], acc[K + tri<K>(j, l2)]);
+            for (int j = 0; j < K; ++j) uq[j & 3] = fmaf(u[j], y[j], uq[j & 3]);
+            const float uy = (uq[0] + uq[1]) + (uq[2] + uq[3]);
+            if constexpr (sizeof(FT) == 4) {
+                if (valid && !isfinite(xv)) acc[K + NM + 2] += 1.f;
+            }
+            const float res = valid ? fmaf(xv, sc, -of) - uy : 0.f;
+            const float z = fmaf(res, res, mu);
+            const float tz = __powf(z, e);
+            const float wv = valid ? (lb != 0 ? om : 1.f) : 0.f;
+            const float cw = wv * tz;
+            acc[K + NM] = fmaf(cw, z, acc[K + NM]);
+            const float eta = -pw * cw * res;
+            acc[K + NM + 1] = fmaf(eta, eta, acc[K + NM + 1]);
+#pragma unroll
+            for (int j = 0; j < K; ++j) acc[j] = fmaf(eta, u[j], acc[j]);
+            if constexpr (WM) {
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const float cu = cw * u[j];
+#pragma unroll
+                    for (int l2 = j; l2 < K; ++l2) acc[K + tri<K>(j, l2)] = fmaf(cu, u[l2], acc[K + tri<K>(j, l2)]);
+                }
             }
         }
     }
@@ -226,11 +246,12 @@ template <int K> struct UpdVecs {
 // one step is 32 pixels of one channel; the channels of a pixel group follow
 // each other, and the label (max over channels) is written after the last.
 // Per-lane sums [Gram of the new stored rows packed | #foreground].
-template <int K, typename FT, int NW, int NP>
+template <int K, typename FT, typename UT, int NW, int NP>
 __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nupt, const UpdVecs<K> &kv, float cm1,
-                                             float snp, float yn, bool write, float *wbuf, float (&acc)[NP])
+                                             float snp, float yn, bool write, uint32_t sr_key, unsigned char *wbuf,
+                                             float (&acc)[NP])
 {
-    using S = StageCfg<K, FT>;
+    using S = StageCfg<K, FT, UT>;
     constexpr int NM = K * (K + 1) / 2;
     constexpr int SPT = S::STEPS_PER_TILE;
     const DevParams &prm = a.prm;
@@ -240,7 +261,8 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
     const bool pre = prm.mask_pre != 0;
     const int C = prm.C, npt = prm.npt;
     const int64_t cstride = (int64_t)npt * K * TILE_P; // one channel plane of the stored rows
-    const Chunks<K, FT> ch(lane);
+    const Chunks<K, FT, UT> ch(lane);
+    UT *U = static_cast<UT *>(a.U);
     const int ntile = nupt > warp ? (nupt - warp + NW - 1) / NW : 0;
     const int nstep = ntile * SPT * C;
 
@@ -249,10 +271,10 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
     int inval = (int)min((int64_t)TILE_P, prm.P - (int64_t)ipt * TILE_P);
     auto issue_next = [&](int k) {
         if (k < nstep) {
-            const float *ut = a.U + icc * cstride + (int64_t)ipt * K * TILE_P;
+            const UT *ut = U + icc * cstride + (int64_t)ipt * K * TILE_P;
             const FT *ft = static_cast<const FT *>(a.frame) + (int64_t)icc * a.frame_pitch + (int64_t)ipt * TILE_P;
             const uint8_t *lt = a.labels + (int64_t)ipt * TILE_P;
-            ch.issue(wbuf + (k % STG_D) * S::STAGE_F, ut, ft, lt, STG_ROWS * is, inval, icc == 0);
+            ch.issue(wbuf + (k % STG_D) * S::STAGE_B, ut, ft, lt, STG_ROWS * is, inval, icc == 0);
             if (++icc == C) {
                 icc = 0;
                 if (++is == SPT) {
@@ -274,12 +296,12 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
         issue_next(k + STG_D - 1);
         cp_async_wait<STG_D - 1>();
         __syncwarp();
-        const float *st = wbuf + (k % STG_D) * S::STAGE_F;
+        const unsigned char *st = wbuf + (k % STG_D) * S::STAGE_B;
         float u[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) u[j] = st[STG_ROWS * j + lane];
+        for (int j = 0; j < K; ++j) u[j] = ld_u(reinterpret_cast<const UT *>(st) + STG_ROWS * j + lane);
         const FT xraw = reinterpret_cast<const FT *>(st + S::F_OFF)[lane];
-        const uint8_t lb = reinterpret_cast<const uint8_t *>(st + S::L_OFF)[lane];
+        const uint8_t lb = st[S::L_OFF + lane];
         __syncwarp();
         const int row = STG_ROWS * cs + lane;
         const bool valid = row < cnval;
@@ -308,17 +330,31 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
             mx = fmaxf(mx, fabsf(rn));
             if (write && a.bg_out) a.bg_out[(int64_t)cc * prm.P + p] = x - rn + of;
         }
-        // stored row u_st + gamma R^T v, its Gram, written back
+        // stored row u_st + gamma R^T v, its Gram, written back; a bfloat16
+        // row is rounded stochastically first (round to nearest would drop
+        // the per-frame updates that are smaller than half an ulp) and its
+        // Gram taken of the stored values
 #pragma unroll
         for (int j = 0; j < K; ++j) u[j] = fmaf(gam, kv.w[j], u[j]);
+        if constexpr (sizeof(UT) == 2) {
+            // one hash per stored row, then the 32-bit linear congruential
+            // generator of Press et al. (Numerical Recipes, 1664525 x +
+            // 1013904223 mod 2^32) per entry, its high 16 bits as the noise
+            uint32_t rk = pcg_hash(sr_key ^ (uint32_t)(cc * prm.Pp + p));
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                rk = rk * 1664525u + 1013904223u;
+                u[j] = round_bf16_sr(u[j], rk >> 16);
+            }
+        }
 #pragma unroll
         for (int j = 0; j < K; ++j)
 #pragma unroll
             for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[j], u[l2], acc[tri<K>(j, l2)]);
         if (write) {
-            float *ub = a.U + cc * cstride + (int64_t)cpt * K * TILE_P + row;
+            UT *ub = U + cc * cstride + (int64_t)cpt * K * TILE_P + row;
 #pragma unroll
-            for (int j = 0; j < K; ++j) ub[j * TILE_P] = u[j];
+            for (int j = 0; j < K; ++j) st_u(ub + j * TILE_P, u[j]); // exact for a rounded bfloat16 value
         }
         if (++cc == C) { // the pixel group's last channel: its label
             cc = 0;

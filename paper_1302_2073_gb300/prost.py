@@ -19,7 +19,7 @@ from . import build as _build
 
 PROST_OK, PROST_EINVAL, PROST_ENOMEM, PROST_ECUDA = 0, -1, -2, -3
 PROST_EBADFRAME, PROST_ETIMEOUT, PROST_ENOTSPD = -4, -5, -6
-PROST_U8, PROST_F32 = 0, 1
+PROST_U8, PROST_F32, PROST_BF16 = 0, 1, 2
 PROST_MASK_POST_UPDATE, PROST_MASK_PRE_UPDATE = 0, 1
 PROST_MAX_K, PROST_MAX_CG = 16, 32
 
@@ -132,7 +132,8 @@ def _check(rc, h=None, allow=()):
     return rc
 
 
-_DTYPES = {"u8": PROST_U8, "uint8": PROST_U8, "f32": PROST_F32, "float32": PROST_F32}
+_DTYPES = {"u8": PROST_U8, "uint8": PROST_U8, "f32": PROST_F32, "float32": PROST_F32,
+           "bf16": PROST_BF16, "bfloat16": PROST_BF16}
 
 
 def make_params(width, height, channels=1, k=5, p=0.25, mu=0.0, delta=0.35, omega=5e-5,
