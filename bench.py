@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the bfloat16 against float32 storage study")
     return ap.parse_args()
 
 
@@ -212,10 +214,118 @@ def run_reference(args, dist):
     return 0
 
 
+def algorithmic_bytes(m, P, k, n_cg, sx, su):
+    """Bytes one frame must stream: the subspace once per gradient evaluation
+    (n_cg + 1 residual passes and the update pass) and once written, the frame
+    and the weight byte per pass, the mask written."""
+    return (n_cg + 2) * m * k * su + m * k * su + (n_cg + 2) * (m * sx + P) + P
+
+
+def _timed_fps(torch, pg, h, frames, masks, stream, warm, flush_l2):
+    """Frames/s of prost_step on device-resident frames, L2 flushed before
+    every timed frame, per-frame CUDA events on the library's stream."""
+    n = frames.shape[0]
+    with torch.cuda.stream(stream):
+        for t in range(warm):
+            pg.prost_step(h, frames[t % n], masks[t % 2])
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n - warm)]
+    with torch.cuda.stream(stream):
+        for i, (a, b) in enumerate(ev):
+            flush_l2(i)
+            a.record(stream)
+            pg.prost_step(h, frames[warm + i], masks[i % 2])
+            b.record(stream)
+    torch.cuda.synchronize()
+    assert pg.prost_sync(h) == pg.PROST_OK
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    return len(ev) / (ms / 1000.0)
+
+
+def _angle(A, B):
+    qa, _ = np.linalg.qr(np.asarray(A, np.float64))
+    qb, _ = np.linalg.qr(np.asarray(B, np.float64))
+    sv = np.linalg.svd(qa.T @ qb, compute_uv=False)
+    return float(np.arccos(np.clip(sv.min(), -1.0, 1.0)))
+
+
+def precision_study(torch, pg, dev, stream, flush_l2, frames_timed=40, warm=3):
+    """bfloat16 against float32 subspace storage: frames/s on the
+    1920x1080 RGB, k = 15 stream, and the bfloat16 error against the FP64
+    oracle (one teacher-forced 1080p frame; a 200-frame free run on the
+    160x120 gray stream, where the oracle is quick)."""
+    import oracle
+    import synth
+    out = {"workload": "rgb1920x1080_k15", "frames_timed": frames_timed}
+    vid, wp = synth.make_workload("rgb1920x1080_k15", n_frames=frames_timed + warm)
+    host = vid.frames(0, frames_timed + warm)
+    frames = torch.from_numpy(host).to(dev)
+    masks = torch.empty((2, vid.P), dtype=torch.uint8, device=dev)
+    fps = {}
+    for ud in ("f32", "bf16"):
+        h = pg.prost_init(pg.make_params(**dict(wp, u_dtype=ud), seed=1), stream=stream)
+        try:
+            fps[ud] = _timed_fps(torch, pg, h, frames, masks, stream, warm, flush_l2)
+        finally:
+            pg.prost_destroy(h)
+    out["fp32_fps"], out["bf16_fps"] = fps["f32"], fps["bf16"]
+    out["bf16_over_fp32"] = fps["bf16"] / fps["f32"]
+    out["bytes_per_frame"] = {ud: algorithmic_bytes(vid.m, vid.P, vid.k, wp["n_cg"], 1, su)
+                              for ud, su in (("f32", 4), ("bf16", 2))}
+    del frames
+    # one frame from a common seeded orthonormal start, against the oracle
+    prm_o = oracle.params(**wp)
+    U0 = synth.random_orthonormal(vid.m, vid.k, 7).astype(np.float32)
+    f0 = host[0]
+    h = pg.prost_init(pg.make_params(**dict(wp, u_dtype="bf16"), seed=1))
+    try:
+        pg.prost_set_subspace(h, U0)
+        mask = np.empty(vid.P, np.uint8)
+        bg = np.empty(vid.m, np.float32)
+        pg.prost_step(h, f0, mask, bg)
+        cost0 = pg.prost_get_stats(h).cost[0]
+        U64, y64 = oracle.reorthonormalize(U0.astype(np.float64), np.zeros(vid.k))
+    finally:
+        pg.prost_destroy(h)
+    st = oracle.OracleState(U64, y64, np.zeros(vid.P, np.uint8), 0)
+    ref = oracle.frame_step(prm_o, st, f0)
+    x = f0.reshape(-1).astype(np.float64) * wp["in_scale"] - wp["in_offset"]
+    r_gpu = x - (bg.astype(np.float64) - wp["in_offset"])
+    out["bf16_teacher_forced_1080p"] = {
+        "residual_rel": float(np.linalg.norm(r_gpu - ref.residual) / np.linalg.norm(ref.residual)),
+        "cost_rel": float(abs(cost0 - ref.trace.cost[0]) / ref.trace.cost[0]),
+        "mask_disagreement": float((mask != ref.labels).mean())}
+    # free run: principal angle to the oracle's subspace and mask disagreement
+    vs, ws = synth.make_workload("gray160x120_k5", n_frames=200)
+    prm_s = oracle.params(**ws)
+    Us = synth.random_orthonormal(vs.m, vs.k, 5).astype(np.float32)
+    Us64, ys64 = oracle.reorthonormalize(Us.astype(np.float64), np.zeros(vs.k))
+    orc = oracle.OracleState(Us64.copy(), ys64.copy(), np.zeros(vs.P, np.uint8), 0)
+    orc_masks = []
+    for t in range(200):
+        orc_masks.append(oracle.frame_step(prm_s, orc, vs.frame(t)[0], want_residual=False).labels)
+    for ud in ("f32", "bf16"):
+        h = pg.prost_init(pg.make_params(**dict(ws, u_dtype=ud), seed=1))
+        dis = []
+        try:
+            pg.prost_set_subspace(h, Us)
+            m_ = np.empty(vs.P, np.uint8)
+            for t in range(200):
+                pg.prost_step(h, vs.frame(t)[0], m_)
+                dis.append(float((m_ != orc_masks[t]).mean()))
+            Ug = np.empty((vs.m, vs.k), np.float32)
+            pg.prost_get_subspace(h, Ug, np.empty(vs.k))
+        finally:
+            pg.prost_destroy(h)
+        out[f"{ud}_free_run_gray160x120_k5_200"] = {"principal_angle_rad": _angle(Ug, orc.U),
+                                                    "mask_disagreement_mean": float(np.mean(dis))}
+    return out
+
+
 def _config(args, vid, wp, steps):
     return {"workload": args.workload, "width": vid.width, "height": vid.height,
             "channels": vid.channels, "k": vid.k, "n_cg": wp["n_cg"], "frame_dtype": vid.dtype,
-            "u_dtype": "f32", "frames_timed": steps,
+            "u_dtype": args.u_dtype, "frames_timed": steps,
             "l2": "flushed before every timed frame (256 MiB write, then 256 MiB read of another buffer); per-frame CUDA events",
             "replicas": args.gpus}
 
@@ -312,7 +422,7 @@ def run_ours(args, dist):
     kern = np.array(kern)  # K x (n_cg + 2) phase times from the device clock
     m, P, k = vid.m, vid.P, vid.k
     sx = 1 if vid.dtype == "u8" else 4
-    frame_bytes = (n_cg + 2) * m * k * 4 + m * k * 4 + (n_cg + 2) * (m * sx + P) + P
+    frame_bytes = algorithmic_bytes(m, P, k, n_cg, sx, 2 if args.u_dtype == "bf16" else 4)
     peak, peak_src = measured_peak_hbm()
     launch_ms = float(np.mean(step_ms))
     achieved = frame_bytes / (launch_ms * 1e-3) / 1e9
@@ -338,6 +448,8 @@ def run_ours(args, dist):
            "gpu_launches": K * launches_per_step,
            "clocks": clk}
 
+    if dist.rank == 0 and n == 1 and not args.no_precision:
+        out["bf16_vs_fp32"] = precision_study(torch, pg, dev, stream, flush_l2)
     if dist.rank == 0 and n == 1 and not args.no_cpu_baseline:
         fps, nf, secs = oracle_sample(args.workload, args.cpu_seconds)
         out["cpu_baseline"] = {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",
