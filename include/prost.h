@@ -258,6 +258,41 @@ int prost_get_trace(prost_handle *h, uint64_t *ts);
 /* Release the device state (synchronises the stream first).  NULL is a no-op. */
 void prost_destroy(prost_handle *h);
 
+/* ---- pre- and post-processing (Section 3.4) -------------------------------
+ *
+ * Pre-processing: each frame (channels planes of h_in x w_in, uint8 or
+ * float32 as frame_dtype, row-major) is resampled by area averaging to
+ * h_out x w_out (160 x 120 in the paper); during the initialisation phase
+ * (its first i_init frames) the running per-entry mean and the running sample
+ * standard deviation of all entries are updated with every frame (the current
+ * one included) and kept fixed afterwards; the output is (v - mean) / std,
+ * float32, channels planes of h_out x w_out: the frame a prost_handle made with
+ * frame_dtype = PROST_F32, in_scale = 1 and in_offset = 0 takes.
+ * The handle owns its device state and orders its work on the given stream.
+ * Errors: PROST_EINVAL for bad sizes (planes up to 2^30 pixels, 1..4
+ * channels) or NULL pointers, PROST_ENOMEM, PROST_ECUDA. */
+typedef struct prost_pre prost_pre;
+int prost_pre_init(int32_t w_in, int32_t h_in, int32_t channels, int32_t w_out, int32_t h_out,
+                   int32_t frame_dtype, int32_t i_init, void *stream, prost_pre **out);
+/* One frame: frame and out are device pointers of the current device
+ * (on_device = 1, only enqueued) or host pointers (on_device = 0, synchronous). */
+int prost_pre_apply(prost_pre *p, const void *frame, int on_device, float *out);
+/* The running statistics (synchronises): mean_out (host, channels*h_out*w_out
+ * floats, or NULL), the standard deviation, the frames counted so far. */
+int prost_pre_get_stats(prost_pre *p, float *mean_out, double *sigma_out, int32_t *frames_out);
+const char *prost_pre_last_error(const prost_pre *p);
+void prost_pre_destroy(prost_pre *p);
+
+/* Post-processing (Section 3.4): the 3 x 3 median of a binary mask (height x
+ * width bytes, row-major, nonzero = foreground) with border pixels replicated,
+ * which is 1 exactly where at least 5 of the 9 neighbours are.  The paper runs
+ * it on the CPU.  mask_in and mask_out are device pointers (on_device = 1,
+ * distinct buffers, enqueued on stream) or host pointers (on_device = 0,
+ * synchronous).  Errors: PROST_EINVAL (NULL, sizes, in-place on the device),
+ * PROST_ENOMEM, PROST_ECUDA. */
+int prost_median3x3(const uint8_t *mask_in, uint8_t *mask_out, int32_t width, int32_t height,
+                    int on_device, void *stream);
+
 /* Name of an error code (static string). */
 const char *prost_strerror(int code);
 

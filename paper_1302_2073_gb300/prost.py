@@ -85,6 +85,14 @@ def lib():
         L.prost_last_error.argtypes = [vp]
         L.prost_last_error.restype = C.c_char_p
         L.prost_version.argtypes = []
+        L.prost_pre_init.argtypes = [C.c_int32] * 7 + [vp, P(vp)]
+        L.prost_pre_apply.argtypes = [vp, vp, C.c_int, vp]
+        L.prost_pre_get_stats.argtypes = [vp, vp, P(C.c_double), P(C.c_int32)]
+        L.prost_pre_last_error.argtypes = [vp]
+        L.prost_pre_last_error.restype = C.c_char_p
+        L.prost_pre_destroy.argtypes = [vp]
+        L.prost_pre_destroy.restype = None
+        L.prost_median3x3.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int, vp]
         _lib = L
     return _lib
 
@@ -267,6 +275,54 @@ def prost_cost_grad_static(params, U, y, frame, labels, out, status_out=None, st
 def prost_destroy(h):
     if h:
         lib().prost_destroy(h)
+
+
+# ---- pre- and post-processing (Section 3.4) ---------------------------------
+
+def _check_pre(rc, p=None):
+    if rc < 0:
+        detail = lib().prost_pre_last_error(p).decode()
+        raise ProstError(rc, f"{prost_strerror(rc)}: {detail}" if detail else prost_strerror(rc))
+    return rc
+
+
+def prost_pre_init(w_in, h_in, channels, w_out, h_out, frame_dtype="u8", i_init=100, stream=None):
+    """Resampling to w_out x h_out and running mean/deviation normalisation
+    over the first i_init frames; returns the handle."""
+    fd = _DTYPES[frame_dtype] if isinstance(frame_dtype, str) else int(frame_dtype)
+    out = C.c_void_p()
+    _check_pre(lib().prost_pre_init(int(w_in), int(h_in), int(channels), int(w_out), int(h_out), fd,
+                                    int(i_init), _stream_ptr(stream), C.byref(out)))
+    return out.value
+
+
+def prost_pre_apply(p, frame, out):
+    """One frame into out (channels x h_out x w_out float32), both on the
+    device (enqueued) or both on the host (synchronous)."""
+    return _check_pre(lib().prost_pre_apply(p, _ptr(frame), _where(frame, out), _ptr(out)), p)
+
+
+def prost_pre_get_stats(p, mean_out=None):
+    """(deviation, frames counted); fills mean_out (host float32) if given."""
+    sd = C.c_double(0.0)
+    n = C.c_int32(0)
+    _check_pre(lib().prost_pre_get_stats(p, _ptr(mean_out), C.byref(sd), C.byref(n)), p)
+    return sd.value, n.value
+
+
+def prost_pre_last_error(p=None):
+    return lib().prost_pre_last_error(p).decode()
+
+
+def prost_pre_destroy(p):
+    if p:
+        lib().prost_pre_destroy(p)
+
+
+def prost_median3x3(mask_in, mask_out, width, height, stream=None):
+    """3 x 3 median of a binary mask (border replicated), device or host buffers."""
+    return _check(lib().prost_median3x3(_ptr(mask_in), _ptr(mask_out), int(width), int(height),
+                                        _where(mask_in, mask_out), _stream_ptr(stream)))
 
 
 __all__ = [n for n in dir() if n.startswith(("prost_", "PROST_"))] + [
