@@ -322,6 +322,106 @@ def precision_study(torch, pg, dev, stream, flush_l2, frames_timed=40, warm=3):
     return out
 
 
+def pipeline_study(torch, pg, dev, stream, flush_l2, frames_timed=200, warm=10):
+    """The paper's whole per-frame pipeline (Section 3.4) on the GPU: a
+    640x480 RGB uint8 frame resampled to 160x120 and normalised, one tracker
+    step at k = 15 (the paper's configuration), the 3 x 3 median of the mask.
+    Frames/s of the three together, and the time of each part (CUDA events)."""
+    import synth
+    vid, _ = synth.make_workload("rgb640x480_k10", n_frames=frames_timed + warm)
+    w, h = 160, 120
+    wp = synth.video._params(3 * w * h, 15, "f32")
+    wp.update(width=w, height=h, channels=3, frame_dtype="f32", in_scale=1.0, in_offset=0.0)
+    frames = torch.from_numpy(vid.frames(0, frames_timed + warm)).to(dev)
+    p = pg.prost_pre_init(640, 480, 3, w, h, "u8", 100, stream=stream)
+    hdl = pg.prost_init(pg.make_params(**wp, seed=3), stream=stream)
+    x = torch.empty((3, h, w), dtype=torch.float32, device=dev)
+    mask = torch.empty(w * h, dtype=torch.uint8, device=dev)
+    med = torch.empty_like(mask)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(frames_timed)]
+    try:
+        with torch.cuda.stream(stream):
+            for t in range(warm):
+                pg.prost_pre_apply(p, frames[t], x)
+                pg.prost_step(hdl, x, mask)
+                pg.prost_median3x3(mask, med, w, h, stream=stream)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            for i in range(frames_timed):
+                flush_l2(i)
+                e = ev[i]
+                e[0].record(stream)
+                pg.prost_pre_apply(p, frames[warm + i], x)
+                e[1].record(stream)
+                pg.prost_step(hdl, x, mask)
+                e[2].record(stream)
+                pg.prost_median3x3(mask, med, w, h, stream=stream)
+                e[3].record(stream)
+        torch.cuda.synchronize()
+        assert pg.prost_sync(hdl) == pg.PROST_OK
+    finally:
+        pg.prost_destroy(hdl)
+        pg.prost_pre_destroy(p)
+    t = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(3)] for e in ev])  # ms
+    total = t.sum(axis=1)
+    return {"input": "rgb640x480 uint8", "tracker": "160x120 RGB, k = 15, float frames",
+            "frames_timed": frames_timed, "frames_per_s": float(frames_timed / (total.sum() / 1e3)),
+            "pre_us": float(t[:, 0].mean() * 1e3), "step_us": float(t[:, 1].mean() * 1e3),
+            "median_us": float(t[:, 2].mean() * 1e3),
+            "note": "the first 100 frames are the initialisation phase (three pre-processing launches each)"}
+
+
+def batched_study(torch, pg, dev, stream, ticks=30, n_distinct=4):
+    """64 streams of uneven size and rank (16 grayscale streams at each of
+    160x120, 320x240, 640x480, 1280x720, k from {5, 10, 15}) advanced together,
+    one tick = one frame of every stream, float32 against bfloat16 storage, each
+    with its autotuned plan.  The subspaces total 0.85 GB (float32), so every
+    tick streams from HBM without an L2 flush.  Each stream cycles through
+    n_distinct seeded frames."""
+    import synth
+    streams = synth.batched_workload(n_frames=n_distinct)
+    frames = [[torch.from_numpy(v.frame(t)[0]).to(dev) for v, _ in streams] for t in range(n_distinct)]
+    n = len(streams)
+    out = {"streams": n, "ticks_timed": ticks, "sizes": [list(x) for x in synth.video.BATCH_SIZES],
+           "ranks": sorted({wp["k"] for _, wp in streams}),
+           "u_bytes_f32": int(sum(v.m * v.k * 4 for v, _ in streams))}
+    last = {}
+    for ud in ("f32", "bf16"):
+        b = pg.prost_batch_init([pg.make_params(**dict(wp, u_dtype=ud), seed=i + 1)
+                                 for i, (_, wp) in enumerate(streams)], stream=stream)
+        try:
+            masks = [torch.empty(v.P, dtype=torch.uint8, device=dev) for v, _ in streams]
+            tuned_ms = pg.prost_batch_tune(b, frames[0], ticks=3)
+            ctas, ngroups, alpha, graph = pg.prost_batch_plan(b, n)
+            res = {}
+            for use_graph in (graph, not graph):
+                pg.prost_batch_set_graph(b, use_graph)
+                for t in range(3):
+                    pg.prost_batch_step(b, frames[t % n_distinct], masks)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for t in range(ticks):
+                    pg.prost_batch_step(b, frames[t % n_distinct], masks)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / ticks
+                res["graph" if use_graph else "direct"] = {"ms_per_tick": ms, "frames_per_s": n / (ms / 1e3)}
+            pg.prost_batch_sync(b)
+            last[ud] = [m.cpu().numpy() for m in masks]
+            best = min(res.values(), key=lambda r: r["ms_per_tick"])
+            out[ud] = {"frames_per_s": best["frames_per_s"], "ms_per_tick": best["ms_per_tick"],
+                       "plan": {"alpha": alpha, "graph": bool(graph), "kernel_groups": ngroups,
+                                "tuner_ms_per_tick": tuned_ms},
+                       "launch": res}
+        finally:
+            pg.prost_batch_destroy(b)
+    out["bf16_over_f32"] = out["bf16"]["frames_per_s"] / out["f32"]["frames_per_s"]
+    dis = [float((a != c).mean()) for a, c in zip(last["f32"], last["bf16"])]
+    out["bf16_vs_f32_mask_disagreement_last_tick"] = {"mean": float(np.mean(dis)), "max": float(np.max(dis))}
+    return out
+
+
 def _config(args, vid, wp, steps):
     return {"workload": args.workload, "width": vid.width, "height": vid.height,
             "channels": vid.channels, "k": vid.k, "n_cg": wp["n_cg"], "frame_dtype": vid.dtype,
@@ -450,6 +550,8 @@ def run_ours(args, dist):
 
     if dist.rank == 0 and n == 1 and not args.no_precision:
         out["bf16_vs_fp32"] = precision_study(torch, pg, dev, stream, flush_l2)
+        out["pipeline_160x120_k15"] = pipeline_study(torch, pg, dev, stream, flush_l2)
+        out["batched_64_streams"] = batched_study(torch, pg, dev, stream)
     if dist.rank == 0 and n == 1 and not args.no_cpu_baseline:
         fps, nf, secs = oracle_sample(args.workload, args.cpu_seconds)
         out["cpu_baseline"] = {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",

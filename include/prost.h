@@ -258,6 +258,45 @@ int prost_get_trace(prost_handle *h, uint64_t *ts);
 /* Release the device state (synchronises the stream first).  NULL is a no-op. */
 void prost_destroy(prost_handle *h);
 
+/* ---- many streams per tick (not in the paper) --------------------------------
+ *
+ * A batch tracks n independent streams (each its own prost_params: sizes, k,
+ * storage and frame types may all differ) and advances all of them by one
+ * frame per prost_batch_step().  The streams are grouped by kernel family (k,
+ * storage type, frame type); each group is one cooperative launch in which the
+ * CTAs are split between its streams, and with the CUDA graph on (the
+ * default) a whole tick is one graph launch.  Each stream computes exactly what
+ * a prost_handle with its parameters computes (Steps 1-3 of Section 3.3), up to
+ * the summation order of its reductions.
+ * The batch owns its handles; prost_batch_stream() lends one (for
+ * prost_get_subspace, prost_get_stats, checkpoints...; frames must go through
+ * prost_batch_step while the batch lives).  Work is ordered on the given stream.
+ * Errors: PROST_EINVAL (bad parameters of a stream, NULL, unaligned frames),
+ * PROST_ENOMEM, PROST_ECUDA; prost_batch_last_error() gives the detail. */
+typedef struct prost_batch prost_batch;
+int prost_batch_init(const prost_params *prms, int32_t n, void *stream, prost_batch **out);
+/* One tick: frames[i] is stream i's frame, a device pointer whose channel
+ * planes start on 16-byte boundaries (P * bytes per entry a multiple of 16);
+ * masks[i] (device, P bytes) receives its labels, masks or masks[i] may be
+ * NULL.  Only enqueues. */
+int prost_batch_step(prost_batch *b, const void *const *frames, uint8_t *const *masks);
+/* Wait for the stream and report the first device-side error of any stream. */
+int prost_batch_sync(prost_batch *b);
+int prost_batch_stream(prost_batch *b, int32_t i, prost_handle **h);
+/* Capture ticks in a CUDA graph (1, the default) or launch them directly (0). */
+int prost_batch_set_graph(prost_batch *b, int enable);
+/* Autotuner: times `ticks` ticks of each candidate plan (the split of each
+ * group's CTAs between its streams in proportion to rows^alpha, alpha in
+ * {0.5, 0.75, 1}; graph on or off) on the given frames and keeps the fastest.
+ * The trackers' states are saved and restored around the trials.  best_ms:
+ * the chosen plan's time per tick. */
+int prost_batch_tune(prost_batch *b, const void *const *frames, int32_t ticks, float *best_ms);
+/* The plan in use: CTAs per stream (n values), kernel groups, alpha, graph. */
+int prost_batch_plan(prost_batch *b, int32_t *ctas_per_stream, int32_t *n_groups, float *alpha,
+                     int32_t *graph);
+const char *prost_batch_last_error(const prost_batch *b);
+void prost_batch_destroy(prost_batch *b);
+
 /* ---- pre- and post-processing (Section 3.4) -------------------------------
  *
  * Pre-processing: each frame (channels planes of h_in x w_in, uint8 or

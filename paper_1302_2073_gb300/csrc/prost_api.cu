@@ -4,7 +4,10 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
+#include <new>
+#include <vector>
 #include <string>
 
 #include "prost.h"
@@ -386,6 +389,7 @@ int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_
     fa.bar_base = h->bar_base;
     fa.frame_pitch = pitch;
     fa.row_stride = (int)partial_row(h->prm.k);
+    fa.grid = h->grid_frame;
     fa.prm = dp;
     if (h->timing) CK(h, cudaEventRecord(h->ev[0], h->stream));
     CK(h, h->ops->frame(fa, fdt, h->grid_frame, h->stream));
@@ -653,3 +657,457 @@ void prost_destroy(prost_handle *h)
 }
 
 } // extern "C"
+
+// ---- many streams per tick ------------------------------------------------------
+//
+// A batch owns one prost_handle per stream.  A tick advances every stream by
+// one frame: the streams are grouped by kernel family (k, storage type, frame
+// type) and each group is one cooperative launch of the multi-stream frame
+// kernel, its CTAs split between the group's streams (each stream keeps its
+// own grid barrier).  The launches read the per-stream arguments (frame and
+// mask pointers, barrier bases) from a device table that the tick's first
+// operation copies from one of two pinned host tables; with the CUDA graph on,
+// that copy and the launches are captured once per table and a tick is one
+// graph launch.  The rows of every stream are rebased together every
+// REBASE_EVERY ticks, outside the graph.
+
+namespace {
+
+struct BatchGroup {
+    const KernelOps *ops;
+    int fdt;
+    int first, count; // its streams are order[first .. first + count)
+    int ctas;         // CTAs of its launch
+    int2 *d_map;      // CTA -> (stream slot in the table, CTA within the stream)
+};
+
+int occupancy_ctas(prost_handle *h, const KernelOps *ops, int fdt)
+{
+    const int occ = ops->frame_prepare(fdt);
+    return occ < 1 ? 0 : occ * h->num_sms;
+}
+
+} // namespace
+
+struct prost_batch {
+    std::vector<prost_handle *> h;
+    std::vector<int> order;     // table slot -> stream index (grouped)
+    std::vector<int> grid;      // CTAs per stream
+    std::vector<BatchGroup> groups;
+    cudaStream_t stream;
+    int device;
+    FrameArgs *d_args;          // device argument table (one slot per stream)
+    FrameArgs *h_args[2];       // pinned host tables, alternating ticks
+    cudaEvent_t used[2];        // recorded after the tick that read h_args[i]
+    int buf;
+    int use_graph;
+    int graph_ok;               // the capture worked (cooperative kernel nodes)
+    cudaGraphExec_t gexec[2];
+    float alpha;                // CTAs of a stream proportional to (its rows)^alpha
+    uint32_t ticks_since_rebase;
+    void *save;                 // device scratch of the tuner (states saved around trial ticks)
+    size_t save_bytes;
+    std::string err;
+};
+
+namespace {
+
+int bfail(prost_batch *b, int code, const std::string &why)
+{
+    b->err = why;
+    return code;
+}
+
+#define BCK(call)                                                                             \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? PROST_ENOMEM : PROST_ECUDA,     \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+// Split each group's CTA budget between its streams: shares proportional to
+// rows^alpha, at least one CTA and at most one per pixel tile for a stream,
+// remainders to the largest fractional parts.
+int plan_ctas(prost_batch *b)
+{
+    for (BatchGroup &g : b->groups) {
+        prost_handle *h0 = b->h[b->order[g.first]];
+        const int budget = occupancy_ctas(h0, g.ops, g.fdt);
+        if (budget < g.count) return bfail(b, PROST_EINVAL, "more streams in a group than resident CTAs");
+        std::vector<double> w(g.count);
+        double wsum = 0.0;
+        for (int i = 0; i < g.count; ++i) {
+            prost_handle *h = b->h[b->order[g.first + i]];
+            w[i] = pow((double)h->dp.C * (double)h->dp.P, (double)b->alpha);
+            wsum += w[i];
+        }
+        std::vector<int> n(g.count);
+        std::vector<double> frac(g.count);
+        int used = 0;
+        for (int i = 0; i < g.count; ++i) {
+            prost_handle *h = b->h[b->order[g.first + i]];
+            const double share = budget * w[i] / wsum;
+            int c = (int)floor(share);
+            c = c < 1 ? 1 : c;
+            if (c > h->dp.npt) c = h->dp.npt;
+            n[i] = c;
+            frac[i] = share - floor(share);
+            used += c;
+        }
+        // hand out what is left, largest fractional part first, within the caps
+        while (used < budget) {
+            int best = -1;
+            for (int i = 0; i < g.count; ++i) {
+                prost_handle *h = b->h[b->order[g.first + i]];
+                if (n[i] < h->dp.npt && (best < 0 || frac[i] > frac[best])) best = i;
+            }
+            if (best < 0) break;
+            n[best] += 1;
+            frac[best] -= 1.0;
+            used += 1;
+        }
+        // over budget (the minimum of one CTA each): take from the largest
+        while (used > budget) {
+            int big = 0;
+            for (int i = 1; i < g.count; ++i)
+                if (n[i] > n[big]) big = i;
+            n[big] -= 1;
+            used -= 1;
+        }
+        std::vector<int2> map;
+        map.reserve(used);
+        for (int i = 0; i < g.count; ++i) {
+            const int slot = g.first + i;
+            b->grid[b->order[slot]] = n[i];
+            for (int c = 0; c < n[i]; ++c) map.push_back(make_int2(slot, c));
+        }
+        g.ctas = used;
+        if (g.d_map) cudaFree(g.d_map);
+        g.d_map = nullptr;
+        BCK(cudaMalloc(&g.d_map, map.size() * sizeof(int2)));
+        BCK(cudaMemcpy(g.d_map, map.data(), map.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    }
+    // partial-row space: every stream's handle holds rows for its own grid
+    for (size_t s = 0; s < b->h.size(); ++s)
+        if ((size_t)2 * b->grid[s] * partial_row(b->h[s]->prm.k) > b->h[s]->partial_floats)
+            return bfail(b, PROST_EINVAL, "partial rows");
+    return PROST_OK;
+}
+
+void drop_graphs(prost_batch *b)
+{
+    for (int i = 0; i < 2; ++i)
+        if (b->gexec[i]) {
+            cudaGraphExecDestroy(b->gexec[i]);
+            b->gexec[i] = nullptr;
+        }
+}
+
+// the tick's operations on the batch stream: table copy, one launch per group
+int enqueue_tick(prost_batch *b, int t)
+{
+    BCK(cudaMemcpyAsync(b->d_args, b->h_args[t], b->h.size() * sizeof(FrameArgs), cudaMemcpyHostToDevice,
+                        b->stream));
+    // the CTA maps hold table slots of the whole batch
+    for (const BatchGroup &g : b->groups)
+        BCK(g.ops->frame_multi(b->d_args, g.d_map, g.ctas, g.fdt, b->stream));
+    return PROST_OK;
+}
+
+int capture(prost_batch *b, int t)
+{
+    cudaGraph_t graph = nullptr;
+    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue_tick(b, t);
+    const cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return bfail(b, PROST_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(&b->gexec[t], graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return bfail(b, PROST_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    return PROST_OK;
+}
+
+} // namespace
+
+extern "C" int prost_batch_init(const prost_params *prms, int32_t n, void *stream, prost_batch **out)
+{
+    if (!out) { g_init_err = "out is NULL"; return PROST_EINVAL; }
+    *out = nullptr;
+    if (!prms || n < 1) { g_init_err = "no streams"; return PROST_EINVAL; }
+    prost_batch *b = new (std::nothrow) prost_batch();
+    if (!b) { g_init_err = "host allocation failed"; return PROST_ENOMEM; }
+    b->stream = (cudaStream_t)stream;
+    b->alpha = 1.f;
+    b->use_graph = 1;
+    b->graph_ok = 1;
+    auto bail = [&](int code) {
+        if (g_init_err.empty()) g_init_err = b->err;
+        prost_batch_destroy(b);
+        return code;
+    };
+    g_init_err.clear();
+    for (int i = 0; i < n; ++i) {
+        prost_handle *h = nullptr;
+        const int rc = prost_init(&prms[i], stream, &h);
+        if (rc) {
+            g_init_err = "stream " + std::to_string(i) + ": " + g_init_err;
+            return bail(rc);
+        }
+        b->h.push_back(h);
+    }
+    b->device = b->h[0]->device;
+    b->grid.assign(n, 1);
+    // group by kernel family, streams of a group in consecutive table slots
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        const prost_params &a = b->h[x]->prm, &c = b->h[y]->prm;
+        if (a.k != c.k) return a.k < c.k;
+        if (a.u_dtype != c.u_dtype) return a.u_dtype < c.u_dtype;
+        return a.frame_dtype < c.frame_dtype;
+    });
+    b->order = idx;
+    for (int i = 0; i < n;) {
+        int j = i;
+        const prost_params &a = b->h[idx[i]]->prm;
+        while (j < n && b->h[idx[j]]->prm.k == a.k && b->h[idx[j]]->prm.u_dtype == a.u_dtype &&
+               b->h[idx[j]]->prm.frame_dtype == a.frame_dtype)
+            ++j;
+        BatchGroup g;
+        g.ops = b->h[idx[i]]->ops;
+        g.fdt = a.frame_dtype;
+        g.first = i;
+        g.count = j - i;
+        g.ctas = 0;
+        g.d_map = nullptr;
+        b->groups.push_back(g);
+        i = j;
+    }
+    int rc = plan_ctas(b);
+    if (rc) return bail(rc);
+    if (cudaMalloc(&b->d_args, (size_t)n * sizeof(FrameArgs)) != cudaSuccess) return bail(PROST_ENOMEM);
+    for (int t = 0; t < 2; ++t) {
+        if (cudaMallocHost(&b->h_args[t], (size_t)n * sizeof(FrameArgs)) != cudaSuccess) return bail(PROST_ENOMEM);
+        if (cudaEventCreateWithFlags(&b->used[t], cudaEventDisableTiming) != cudaSuccess) return bail(PROST_ECUDA);
+        cudaEventRecord(b->used[t], b->stream);
+    }
+    *out = b;
+    return PROST_OK;
+}
+
+extern "C" int prost_batch_step(prost_batch *b, const void *const *frames, uint8_t *const *masks)
+{
+    if (!b) return PROST_EINVAL;
+    if (!frames) return bfail(b, PROST_EINVAL, "frames is NULL");
+    DeviceGuard dg(b->device);
+    const int t = b->buf;
+    BCK(cudaEventSynchronize(b->used[t])); // the tick before last has read this table
+    FrameArgs *tab = b->h_args[t];
+    const int n = (int)b->h.size();
+    for (int slot = 0; slot < n; ++slot) {
+        const int s = b->order[slot];
+        prost_handle *h = b->h[s];
+        const DevParams &dp = h->dp;
+        const size_t eb = frame_elem_bytes(h->prm);
+        if (!frames[s] || ((uintptr_t)frames[s] % 16) != 0 || ((size_t)dp.P * eb) % 16 != 0)
+            return bfail(b, PROST_EINVAL, "frame " + std::to_string(s) +
+                                              ": device frames of a batch must be 16-byte aligned planes");
+        FrameArgs &fa = tab[slot];
+        memset(&fa, 0, sizeof(fa));
+        fa.U = h->U;
+        fa.frame = frames[s];
+        fa.labels = h->labels;
+        fa.mask_out = masks ? masks[s] : nullptr;
+        fa.bg_out = nullptr;
+        fa.ks = h->ks;
+        fa.partials = h->partials;
+        fa.bar = h->bar;
+        fa.bar_base = h->bar_base;
+        fa.frame_pitch = dp.P;
+        fa.row_stride = (int)partial_row(h->prm.k);
+        fa.grid = b->grid[s];
+        fa.prm = dp;
+        h->bar_base += (unsigned long long)b->grid[s] * (unsigned long long)(h->prm.n_cg + 2);
+    }
+    if (b->use_graph && b->graph_ok) {
+        if (!b->gexec[t]) {
+            const int rc = capture(b, t);
+            if (rc) { // the tick runs without a graph from now on; the reason is kept
+                b->graph_ok = 0;
+                drop_graphs(b);
+                (void)cudaGetLastError(); // clear the capture's error
+            }
+        }
+        if (b->gexec[t]) BCK(cudaGraphLaunch(b->gexec[t], b->stream));
+    }
+    if (!(b->use_graph && b->graph_ok)) {
+        const int rc = enqueue_tick(b, t);
+        if (rc) return rc;
+    }
+    BCK(cudaEventRecord(b->used[t], b->stream));
+    b->buf ^= 1;
+    if (++b->ticks_since_rebase >= REBASE_EVERY) {
+        for (prost_handle *h : b->h) {
+            const int rc = rebase(h);
+            if (rc) return bfail(b, rc, h->err);
+            h->steps_since_rebase = 0;
+        }
+        b->ticks_since_rebase = 0;
+    }
+    return PROST_OK;
+}
+
+extern "C" int prost_batch_sync(prost_batch *b)
+{
+    if (!b) return PROST_EINVAL;
+    DeviceGuard dg(b->device);
+    BCK(cudaStreamSynchronize(b->stream));
+    for (prost_handle *h : b->h) {
+        const int rc = prost_sync(h);
+        if (rc) return bfail(b, rc, h->err);
+    }
+    return PROST_OK;
+}
+
+extern "C" int prost_batch_stream(prost_batch *b, int32_t i, prost_handle **h)
+{
+    if (!b || !h || i < 0 || i >= (int32_t)b->h.size()) return PROST_EINVAL;
+    *h = b->h[i];
+    return PROST_OK;
+}
+
+extern "C" int prost_batch_set_graph(prost_batch *b, int enable)
+{
+    if (!b) return PROST_EINVAL;
+    b->use_graph = enable ? 1 : 0;
+    return PROST_OK;
+}
+
+extern "C" int prost_batch_plan(prost_batch *b, int32_t *ctas_per_stream, int32_t *n_groups, float *alpha,
+                                int32_t *graph)
+{
+    if (!b) return PROST_EINVAL;
+    if (ctas_per_stream)
+        for (size_t s = 0; s < b->h.size(); ++s) ctas_per_stream[s] = b->grid[s];
+    if (n_groups) *n_groups = (int32_t)b->groups.size();
+    if (alpha) *alpha = b->alpha;
+    if (graph) *graph = b->use_graph && b->graph_ok ? 1 : 0;
+    return PROST_OK;
+}
+
+namespace {
+
+// device copies of every stream's subspace, k-space state and labels (the
+// tuner's trial ticks must not move the trackers)
+int save_states(prost_batch *b, bool restore)
+{
+    size_t need = 0;
+    for (prost_handle *h : b->h)
+        need += (size_t)h->dp.k * h->dp.C * h->dp.Pp * u_elem_bytes(h->dp) + sizeof(KState) + (size_t)h->dp.Pp + 256;
+    if (!restore && need > b->save_bytes) {
+        if (b->save) cudaFree(b->save);
+        b->save = nullptr;
+        b->save_bytes = 0;
+        BCK(cudaMalloc(&b->save, need));
+        b->save_bytes = need;
+    }
+    char *p = static_cast<char *>(b->save);
+    for (prost_handle *h : b->h) {
+        const size_t ub = (size_t)h->dp.k * h->dp.C * h->dp.Pp * u_elem_bytes(h->dp);
+        void *dst[3] = {p, p + ub, p + ub + sizeof(KState)};
+        void *src[3] = {h->U, h->ks, h->labels};
+        const size_t len[3] = {ub, sizeof(KState), (size_t)h->dp.Pp};
+        for (int i = 0; i < 3; ++i)
+            BCK(cudaMemcpyAsync(restore ? src[i] : dst[i], restore ? dst[i] : src[i], len[i],
+                                cudaMemcpyDeviceToDevice, b->stream));
+        p += (ub + sizeof(KState) + (size_t)h->dp.Pp + 255) / 256 * 256;
+    }
+    return PROST_OK;
+}
+
+} // namespace
+
+// Pick the batch plan by measurement: the CTA split exponent alpha in
+// {0.5, 0.75, 1} and the graph on or off, each timed over `ticks` ticks on the
+// given frames; the states are saved before and restored after every trial,
+// so tuning leaves the trackers where they were (the frame counters included).
+extern "C" int prost_batch_tune(prost_batch *b, const void *const *frames, int32_t ticks, float *best_ms)
+{
+    if (!b || !frames || ticks < 1) return PROST_EINVAL;
+    DeviceGuard dg(b->device);
+    int rc = save_states(b, false);
+    if (rc) return rc;
+    const float alphas[3] = {0.5f, 0.75f, 1.0f};
+    float best = 1e30f, best_alpha = b->alpha;
+    int best_graph = b->use_graph;
+    const uint32_t ticks0 = b->ticks_since_rebase;
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    for (float al : alphas) {
+        b->alpha = al;
+        drop_graphs(b);
+        rc = plan_ctas(b);
+        if (rc) break;
+        for (int gr = 0; gr < 2; ++gr) {
+            b->use_graph = gr;
+            rc = prost_batch_step(b, frames, nullptr); // warm (and capture)
+            if (!rc) rc = prost_batch_step(b, frames, nullptr);
+            if (rc) break;
+            BCK(cudaEventRecord(e0, b->stream));
+            for (int i = 0; i < ticks && !rc; ++i) rc = prost_batch_step(b, frames, nullptr);
+            BCK(cudaEventRecord(e1, b->stream));
+            BCK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            ms /= (float)ticks;
+            if (!rc && ms < best) {
+                best = ms;
+                best_alpha = al;
+                best_graph = gr;
+            }
+            const int rs = save_states(b, true);
+            if (!rc) rc = rs;
+            if (rc) break;
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->ticks_since_rebase = ticks0;
+    b->alpha = best_alpha;
+    b->use_graph = best_graph;
+    drop_graphs(b);
+    const int rp = plan_ctas(b);
+    if (!rc) rc = rp;
+    BCK(cudaStreamSynchronize(b->stream));
+    if (best_ms) *best_ms = best;
+    return rc;
+}
+
+extern "C" const char *prost_batch_last_error(const prost_batch *b)
+{
+    return b ? b->err.c_str() : g_init_err.c_str();
+}
+
+extern "C" void prost_batch_destroy(prost_batch *b)
+{
+    if (!b) return;
+    if (b->stream || !b->h.empty()) cudaStreamSynchronize(b->stream);
+    drop_graphs(b);
+    for (BatchGroup &g : b->groups)
+        if (g.d_map) cudaFree(g.d_map);
+    if (b->d_args) cudaFree(b->d_args);
+    for (int t = 0; t < 2; ++t) {
+        if (b->h_args[t]) cudaFreeHost(b->h_args[t]);
+        if (b->used[t]) cudaEventDestroy(b->used[t]);
+    }
+    if (b->save) cudaFree(b->save);
+    for (prost_handle *h : b->h) prost_destroy(h);
+    delete b;
+}

@@ -108,7 +108,7 @@ struct FrameArgs {
     unsigned long long bar_base; // bar->count at launch
     int64_t frame_pitch;
     int row_stride;
-    int pad;
+    int grid;                 // CTAs working on this stream (its grid barrier's size)
     DevParams prm;
 };
 
@@ -116,6 +116,9 @@ struct FrameArgs {
 struct KernelOps {
     cudaError_t (*frame)(const FrameArgs &, int frame_dtype, int grid, cudaStream_t);
     int (*frame_prepare)(int frame_dtype); // resident frame-kernel CTAs per SM (0: cannot run)
+    // several streams in one launch: CTA b works on stream map[b].x as its
+    // CTA map[b].y of args[map[b].x].grid (device tables)
+    cudaError_t (*frame_multi)(const FrameArgs *args, const int2 *map, int ctas, int frame_dtype, cudaStream_t);
     cudaError_t (*gram)(const GramArgs &, int grid, cudaStream_t);
     cudaError_t (*export_u)(const void *U, const KState *ks, float *out, DevParams prm,
                             cudaStream_t);

@@ -639,8 +639,9 @@ __device__ __forceinline__ void residual_pass(const FrameArgs &a, const FrameTil
     }
 }
 
+// The frame of one stream, by CTA b of the G CTAs working on it.
 template <int K, typename FT, typename UT>
-__global__ void __launch_bounds__(FCfg<K, UT>::THREADS, 1) k_frame(const FrameArgs a)
+__device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, const int b)
 {
     using F = FCfg<K, UT>;
     constexpr int TP = F::TP, RW = F::RW, IPT = F::IPT, NT = F::THREADS, NW = F::NW;
@@ -654,7 +655,6 @@ __global__ void __launch_bounds__(FCfg<K, UT>::THREADS, 1) k_frame(const FrameAr
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const DevParams &prm = a.prm;
-    const int G = gridDim.x, b = blockIdx.x;
     const FrameTiles tl(prm, G, b);
 
     if (tid == 0) {
@@ -871,6 +871,27 @@ __global__ void __launch_bounds__(FCfg<K, UT>::THREADS, 1) k_frame(const FrameAr
     if (tid == 0) a.ks->phase_ts[prm.n_cg + 2] = global_ns();
 }
 
+// One stream: the whole grid.
+template <int K, typename FT, typename UT>
+__global__ void __launch_bounds__(FCfg<K, UT>::THREADS, 1) k_frame(const FrameArgs a)
+{
+    frame_body<K, FT, UT>(a, (int)gridDim.x, (int)blockIdx.x);
+}
+
+// Several streams of one kernel family in one cooperative launch: each CTA
+// takes its stream's arguments from the device table (the grid barriers are
+// per stream, and all CTAs of the launch are resident together, so a stream's
+// CTAs wait only on each other).
+template <int K, typename FT, typename UT>
+__global__ void __launch_bounds__(FCfg<K, UT>::THREADS, 1) k_frame_multi(const FrameArgs *args, const int2 *map)
+{
+    __shared__ FrameArgs sa;
+    const int2 mb = map[blockIdx.x];
+    if (threadIdx.x == 0) sa = args[mb.x];
+    __syncthreads();
+    frame_body<K, FT, UT>(sa, sa.grid, mb.y);
+}
+
 template <int K, typename UT> struct FrameOps {
     using F = FCfg<K, UT>;
     // dynamic shared memory: the per-warp stages of the streaming form
@@ -887,6 +908,24 @@ template <int K, typename UT> struct FrameOps {
     static cudaError_t launch(const FrameArgs &a, int fdt, int grid, cudaStream_t s)
     {
         return fdt == 0 ? launch_t<uint8_t>(a, grid, s) : launch_t<float>(a, grid, s);
+    }
+    template <typename FT>
+    static cudaError_t multi_t(const FrameArgs *args, const int2 *map, int ctas, cudaStream_t s)
+    {
+        void *kargs[] = {const_cast<FrameArgs **>(&args), const_cast<int2 **>(&map)};
+        static bool attr = false; // the dynamic shared memory limit, once per instantiation
+        if (!attr && dyn_smem<FT>() > 0) {
+            const cudaError_t e = cudaFuncSetAttribute(k_frame_multi<K, FT, UT>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem<FT>());
+            if (e != cudaSuccess) return e;
+        }
+        attr = true;
+        return cudaLaunchCooperativeKernel((void *)k_frame_multi<K, FT, UT>, dim3(ctas), dim3(F::THREADS), kargs,
+                                           dyn_smem<FT>(), s);
+    }
+    static cudaError_t multi(const FrameArgs *args, const int2 *map, int ctas, int fdt, cudaStream_t s)
+    {
+        return fdt == 0 ? multi_t<uint8_t>(args, map, ctas, s) : multi_t<float>(args, map, ctas, s);
     }
     template <typename FT> static int prepare_t()
     {
@@ -906,7 +945,8 @@ template <int K, typename UT> struct FrameOps {
 
 template <int K, typename UT> const KernelOps *kernel_table()
 {
-    static const KernelOps ops = {&FrameOps<K, UT>::launch, &FrameOps<K, UT>::prepare, &Ops<K, UT>::gram,
+    static const KernelOps ops = {&FrameOps<K, UT>::launch, &FrameOps<K, UT>::prepare, &FrameOps<K, UT>::multi,
+                                  &Ops<K, UT>::gram,
                                   &Ops<K, UT>::export_u, &Ops<K, UT>::gram_occupancy, &Ops<K, UT>::rebase,
                                   Cfg<K>::VW, FCfg<K, UT>::TP, FCfg<K, UT>::THREADS};
     return &ops;

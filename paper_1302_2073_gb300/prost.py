@@ -93,6 +93,17 @@ def lib():
         L.prost_pre_destroy.argtypes = [vp]
         L.prost_pre_destroy.restype = None
         L.prost_median3x3.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int, vp]
+        L.prost_batch_init.argtypes = [P(prost_params), C.c_int32, vp, P(vp)]
+        L.prost_batch_step.argtypes = [vp, P(vp), P(vp)]
+        L.prost_batch_sync.argtypes = [vp]
+        L.prost_batch_stream.argtypes = [vp, C.c_int32, P(vp)]
+        L.prost_batch_set_graph.argtypes = [vp, C.c_int]
+        L.prost_batch_tune.argtypes = [vp, P(vp), C.c_int32, P(C.c_float)]
+        L.prost_batch_plan.argtypes = [vp, P(C.c_int32), P(C.c_int32), P(C.c_float), P(C.c_int32)]
+        L.prost_batch_last_error.argtypes = [vp]
+        L.prost_batch_last_error.restype = C.c_char_p
+        L.prost_batch_destroy.argtypes = [vp]
+        L.prost_batch_destroy.restype = None
         _lib = L
     return _lib
 
@@ -275,6 +286,78 @@ def prost_cost_grad_static(params, U, y, frame, labels, out, status_out=None, st
 def prost_destroy(h):
     if h:
         lib().prost_destroy(h)
+
+
+# ---- many streams per tick ----------------------------------------------------
+
+def _check_batch(rc, b=None):
+    if rc < 0:
+        detail = lib().prost_batch_last_error(b).decode()
+        raise ProstError(rc, f"{prost_strerror(rc)}: {detail}" if detail else prost_strerror(rc))
+    return rc
+
+
+def _ptr_array(bufs):
+    arr = (C.c_void_p * len(bufs))()
+    for i, x in enumerate(bufs):
+        arr[i] = _ptr(x)
+    return arr
+
+
+def prost_batch_init(params_list, stream=None):
+    """A batch of streams, one prost_params each; returns the batch handle."""
+    n = len(params_list)
+    arr = (prost_params * n)(*params_list)
+    out = C.c_void_p()
+    _check_batch(lib().prost_batch_init(arr, n, _stream_ptr(stream), C.byref(out)))
+    return out.value
+
+
+def prost_batch_step(b, frames, masks=None):
+    """One tick: frames[i] (device tensor) for stream i, masks[i] (device
+    tensor of P bytes) receives its labels.  Enqueues only."""
+    fa = _ptr_array(frames)
+    ma = _ptr_array(masks) if masks is not None else None
+    return _check_batch(lib().prost_batch_step(b, fa, ma), b)
+
+
+def prost_batch_sync(b):
+    return _check_batch(lib().prost_batch_sync(b), b)
+
+
+def prost_batch_stream(b, i):
+    h = C.c_void_p()
+    _check_batch(lib().prost_batch_stream(b, int(i), C.byref(h)), b)
+    return h.value
+
+
+def prost_batch_set_graph(b, enable=True):
+    return _check_batch(lib().prost_batch_set_graph(b, 1 if enable else 0), b)
+
+
+def prost_batch_tune(b, frames, ticks=5):
+    """Autotune the batch plan on these frames; returns the chosen ms per tick."""
+    ms = C.c_float(0.0)
+    _check_batch(lib().prost_batch_tune(b, _ptr_array(frames), int(ticks), C.byref(ms)), b)
+    return ms.value
+
+
+def prost_batch_plan(b, n):
+    """(CTAs per stream, kernel groups, alpha, graph on)."""
+    ctas = (C.c_int32 * n)()
+    ng, gr = C.c_int32(0), C.c_int32(0)
+    al = C.c_float(0.0)
+    _check_batch(lib().prost_batch_plan(b, ctas, C.byref(ng), C.byref(al), C.byref(gr)), b)
+    return list(ctas), ng.value, al.value, bool(gr.value)
+
+
+def prost_batch_last_error(b=None):
+    return lib().prost_batch_last_error(b).decode()
+
+
+def prost_batch_destroy(b):
+    if b:
+        lib().prost_batch_destroy(b)
 
 
 # ---- pre- and post-processing (Section 3.4) ---------------------------------

@@ -216,3 +216,28 @@ def make_workload(name: str, **video_over):
     prm.update(width=vid.width, height=vid.height, channels=vid.channels,
                frame_dtype=vid.dtype)
     return vid, prm
+
+
+# Many streams of uneven size and rank advanced together: 16 grayscale streams
+# at each of 160x120, 320x240, 640x480 and 1280x720, ranks drawn from
+# {5, 10, 15}, 3-10 % foreground as moving rectangles, noise 0.01.
+BATCH_SIZES = ((160, 120), (320, 240), (640, 480), (1280, 720))
+
+
+def batched_workload(seed: int = 4000, per_size: int = 16, n_frames: int = 500, sizes=BATCH_SIZES,
+                     ranks=(5, 10, 15)):
+    """[(SyntheticVideo, pROST parameter dict)] of the multi-stream workload."""
+    rng = np.random.default_rng(seed)
+    out = []
+    sid = 0
+    for (w, h) in sizes:
+        for _ in range(per_size):
+            k = int(rng.choice(ranks))
+            fg = float(rng.uniform(0.03, 0.10))
+            vid = SyntheticVideo(width=w, height=h, channels=1, k=k, n_frames=n_frames, fg_fraction=fg,
+                                 shape="rect", n_shapes=3, jitter=0, seed=seed + 1 + sid, dtype="u8")
+            prm = _params(vid.m, k, "u8")
+            prm.update(width=w, height=h, channels=1, frame_dtype="u8")
+            out.append((vid, prm))
+            sid += 1
+    return out
