@@ -297,6 +297,36 @@ int prost_batch_plan(prost_batch *b, int32_t *ctas_per_stream, int32_t *n_groups
 const char *prost_batch_last_error(const prost_batch *b);
 void prost_batch_destroy(prost_batch *b);
 
+/* ---- the cost over a window of frames and its gradients ------------------------
+ *
+ * Not in the paper as an interface: the cost of Eq. (spcacost) with the
+ * weighted norm of Eq. (weightedLPnorm), summed over a window of n frames,
+ *   F(U, Y, mu) = sum_t sum_e w_te ((x_te - u_e^T y_t)^2 + mu)^(p/2),
+ * and its gradients dF/dU = H Y^T, dF/dY = U^T H, dF/dmu =
+ * sum w (p/2)(r^2 + mu)^(p/2-1), with H_te = eta_te = -p w_te r_te
+ * (r_te^2 + mu)^(p/2-1) the per-frame eta of Section 3.3.  Layouts (device,
+ * float32): U m x k row-major, Y k x n row-major (column t is y_t), X n x m
+ * (row t is frame t, channel-planar), labels n x P bytes (weight omega where
+ * set, 1 elsewhere; NULL: all 1), mu one float.  m = channels * P.
+ * prost_window_eval writes the cost (one float) and, when dU, dY and dmu are
+ * all given, the gradients multiplied by *gscale (a device float, NULL: 1).
+ * prost_window_ustep moves U along the window gradient dU: the projection
+ * G = (I - U U^T) dU (Eq. gproject), V = U - t G and the Cholesky-QR
+ * retraction U_out = V R^{-1} (V^T V = R^T R in FP64); status_out (device
+ * int, or NULL) receives 0, or -1 if V^T V is not positive definite.
+ * All calls only enqueue on the window's stream.  Errors: PROST_EINVAL (sizes:
+ * 1 <= k <= 16, 1 <= n <= 128, 0 < p <= 2; NULL pointers), PROST_ENOMEM,
+ * PROST_ECUDA. */
+typedef struct prost_window prost_window;
+int prost_window_init(int64_t m, int32_t channels, int32_t k, int32_t n, double p, double omega, void *stream,
+                      prost_window **out);
+int prost_window_eval(prost_window *w, const float *U, const float *Y, const float *X, const uint8_t *labels,
+                      const float *mu, const float *gscale, float *cost, float *dU, float *dY, float *dmu);
+int prost_window_ustep(prost_window *w, const float *U, const float *dU, float t, float *U_out,
+                       int32_t *status_out);
+const char *prost_window_last_error(const prost_window *w);
+void prost_window_destroy(prost_window *w);
+
 /* ---- pre- and post-processing (Section 3.4) -------------------------------
  *
  * Pre-processing: each frame (channels planes of h_in x w_in, uint8 or

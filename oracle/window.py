@@ -48,3 +48,15 @@ def window_cost_grad(U, Y, X, W, p: float, mu: float):
     dY = U.T @ H
     dmu = float(np.sum(W.T * (0.5 * p) * Z ** (0.5 * p - 1.0)))
     return F, dU, dY, dmu
+
+
+def grassmann_window_step(U, dU, t: float):
+    """One step of U along the window gradient: the projection
+    G = (I - U U^T) dU of Eq. (gproject), V = U - t G, and the Cholesky-QR
+    retraction V R^{-1} with V^T V = R^T R (FP64)."""
+    U = np.asarray(U, np.float64)
+    dU = np.asarray(dU, np.float64)
+    G = dU - U @ (U.T @ dU)
+    V = U - t * G
+    R = np.linalg.cholesky(V.T @ V).T
+    return np.linalg.solve(R.T, V.T).T

@@ -104,6 +104,14 @@ def lib():
         L.prost_batch_last_error.restype = C.c_char_p
         L.prost_batch_destroy.argtypes = [vp]
         L.prost_batch_destroy.restype = None
+        L.prost_window_init.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_double, vp,
+                                        P(vp)]
+        L.prost_window_eval.argtypes = [vp] + [vp] * 10
+        L.prost_window_ustep.argtypes = [vp, vp, vp, C.c_float, vp, vp]
+        L.prost_window_last_error.argtypes = [vp]
+        L.prost_window_last_error.restype = C.c_char_p
+        L.prost_window_destroy.argtypes = [vp]
+        L.prost_window_destroy.restype = None
         _lib = L
     return _lib
 
@@ -358,6 +366,41 @@ def prost_batch_last_error(b=None):
 def prost_batch_destroy(b):
     if b:
         lib().prost_batch_destroy(b)
+
+
+# ---- the cost over a window of frames -----------------------------------------
+
+def _check_win(rc, w=None):
+    if rc < 0:
+        detail = lib().prost_window_last_error(w).decode()
+        raise ProstError(rc, f"{prost_strerror(rc)}: {detail}" if detail else prost_strerror(rc))
+    return rc
+
+
+def prost_window_init(m, channels, k, n, p=0.25, omega=5e-5, stream=None):
+    out = C.c_void_p()
+    _check_win(lib().prost_window_init(int(m), int(channels), int(k), int(n), float(p), float(omega),
+                                       _stream_ptr(stream), C.byref(out)))
+    return out.value
+
+
+def prost_window_eval(w, U, Y, X, labels, mu, cost, dU=None, dY=None, dmu=None, gscale=None):
+    """Cost into cost (device float); gradients too when dU, dY, dmu are given."""
+    return _check_win(lib().prost_window_eval(w, _ptr(U), _ptr(Y), _ptr(X), _ptr(labels), _ptr(mu),
+                                              _ptr(gscale), _ptr(cost), _ptr(dU), _ptr(dY), _ptr(dmu)), w)
+
+
+def prost_window_ustep(w, U, dU, t, U_out, status_out=None):
+    return _check_win(lib().prost_window_ustep(w, _ptr(U), _ptr(dU), float(t), _ptr(U_out), _ptr(status_out)), w)
+
+
+def prost_window_last_error(w=None):
+    return lib().prost_window_last_error(w).decode()
+
+
+def prost_window_destroy(w):
+    if w:
+        lib().prost_window_destroy(w)
 
 
 # ---- pre- and post-processing (Section 3.4) ---------------------------------

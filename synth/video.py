@@ -241,3 +241,19 @@ def batched_workload(seed: int = 4000, per_size: int = 16, n_frames: int = 500, 
             out.append((vid, prm))
             sid += 1
     return out
+
+
+def window_workload(width: int = 320, height: int = 240, n: int = 64, k: int = 10, outliers: float = 0.05,
+                    seed: int = 3000):
+    """A window of n grayscale frames: a planted rank-k part U0 Y0 (U0
+    orthonormal, the entries of Y0 N(0, 1) scaled to an entry deviation of
+    0.1) with a fraction `outliers` of the entries replaced by U(0, 1).
+    Returns (X n x m float32, U0 m x k, Y0 k x n, outlier mask n x m)."""
+    rng = np.random.default_rng(seed)
+    m = width * height
+    U0 = random_orthonormal(m, k, rng)
+    Y0 = rng.standard_normal((k, n)) * 0.1 * np.sqrt(m / k)
+    X = (U0 @ Y0).T
+    out = rng.random((n, m)) < outliers
+    X[out] = rng.random(int(out.sum()))
+    return np.ascontiguousarray(X, dtype=np.float32), U0, Y0, out

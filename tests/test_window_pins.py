@@ -70,3 +70,17 @@ def test_rotation_invariance():
     np.testing.assert_allclose(dU2, dU @ Q, rtol=1e-10, atol=1e-13)
     np.testing.assert_allclose(dY2, Q.T @ dY, rtol=1e-10, atol=1e-13)
     assert dmu2 == pytest.approx(dmu, rel=1e-13)
+
+
+def test_window_step_is_the_unique_qr_and_descends():
+    U, Y, X, W, p, mu = _problem(m=80, k=4, n=6, seed=5)
+    F, dU, dY, dmu = wo.window_cost_grad(U, Y, X, W, p, mu)
+    Q = wo.grassmann_window_step(U, dU, 1e-3)
+    V = U - 1e-3 * (dU - U @ (U.T @ dU))
+    q, r = np.linalg.qr(V)
+    q = q * np.sign(np.diag(r))      # positive diagonal: the unique QR
+    np.testing.assert_allclose(Q, q, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(4), atol=1e-12)
+    np.testing.assert_allclose(wo.grassmann_window_step(U, dU, 0.0), U, atol=1e-12)
+    F2 = wo.window_cost_grad(Q, Y, X, W, p, mu)[0]
+    assert F2 < F
