@@ -181,13 +181,14 @@ __device__ __forceinline__ void cons_partials(float (&v)[N], int nv, float *out,
 // As cons_partials, with a plain shuffle tree per value (static indices
 // only): for the streaming form's long per-lane vectors, where the lane-
 // dependent selects of the split reduction would put the vector in local memory.
-template <int N, int NCW, int NA>
+template <int N, int NCW, int NA, int S0 = 0, int S1 = 0>
 __device__ __forceinline__ void cons_partials_tree(float (&v)[NA], int nv, float *out, float *sred)
 {
     static_assert(N <= NA, "values beyond the array");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
+        if (i >= S0 && i < S1) continue; // values another reduction writes
         float x = v[i];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(FULL, x, off);
@@ -195,9 +196,32 @@ __device__ __forceinline__ void cons_partials_tree(float (&v)[NA], int nv, float
     }
     cons_sync<NCW * 32>();
     for (int i = threadIdx.x; i < nv; i += NCW * 32) {
+        if (i >= S0 && i < S1) continue;
         float a = 0.f;
 #pragma unroll
         for (int ww = 0; ww < NCW; ++ww) a += sred[ww * N + i];
+        out[i] = a;
+    }
+    __threadfence();
+}
+
+// The warps' 16 x 16 tensor-core results (at res_off in each warp's shared
+// memory, warp_bytes apart) summed in a fixed order into the packed upper
+// triangle out[0 .. K(K+1)/2).
+template <int K, int NCW>
+__device__ __forceinline__ void mma_row(const unsigned char *base, int warp_bytes, int res_off, float *out)
+{
+    cons_sync<NCW * 32>(); // every warp has stored its result
+    constexpr int NM = K * (K + 1) / 2;
+    for (int i = threadIdx.x; i < NM; i += NCW * 32) {
+        int j = 0, t = i;
+        while (t >= K - j) {
+            t -= K - j;
+            ++j;
+        }
+        const int l = j + t;
+        float a = 0.f;
+        for (int w = 0; w < NCW; ++w) a += reinterpret_cast<const float *>(base + w * warp_bytes + res_off)[j * 16 + l];
         out[i] = a;
     }
     __threadfence();
@@ -680,8 +704,10 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     }
 
     const bool stats = b == 0;
-    unsigned char *wstage =
-        reinterpret_cast<unsigned char *>(stage_smem) + (size_t)warp * STG_D * StageCfg<K, FT, UT>::STAGE_B;
+    using SC = StageCfg<K, FT, UT>;
+    unsigned char *const sbase = reinterpret_cast<unsigned char *>(stage_smem);
+    unsigned char *wstage = sbase + (size_t)warp * SC::WARP_B;
+    constexpr int RES_OFF = STG_D * SC::STAGE_B + 2 * SC::BT_B; // a warp's tensor-core result
     int buf = 0;
     unsigned long long target = a.bar_base;
     if (stats && tid == 0) a.ks->phase_ts[0] = global_ns();
@@ -701,10 +727,14 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             else
                 residual_pass<K, FT, true>(a, tl, sk, acc, t0);
             if (trace) a.ks->sub_ts[0] = global_ns();
-            if constexpr (F::STREAM)
+            if constexpr (F::STREAM && SC::TC) {
+                cons_partials_tree<F::NVR, NW, F::NPR, K, K + NM>(acc, F::NVR, row, sred);
+                mma_row<K, NW>(sbase, SC::WARP_B, RES_OFF, row + K);
+            } else if constexpr (F::STREAM) {
                 cons_partials_tree<F::NVR, NW>(acc, F::NVR, row, sred);
-            else
+            } else {
                 cons_partials<F::NPR, NW>(acc, F::NVR, row, sred);
+            }
             if (trace) a.ks->sub_ts[1] = global_ns();
             if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
             if (trace) a.ks->sub_ts[2] = global_ns();
@@ -750,7 +780,12 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         const uint32_t sr_key = pcg_hash(prm.sr_seed ^ pcg_hash((uint32_t)sk.frame_index));
         stream_update<K, FT, UT, NW>(a, tl.u0, tl.nupt, kv, sk.cm1, sk.snp, sk.yn, !sk.skip, sr_key, wstage, acc);
         if (tid == 0 && stats) a.ks->sub_ts[5] = global_ns();
-        cons_partials_tree<F::NVU, NW>(acc, F::NVU, row, sred);
+        if constexpr (SC::TC) {
+            cons_partials_tree<F::NVU, NW, F::NPU, 0, NM>(acc, F::NVU, row, sred);
+            mma_row<K, NW>(sbase, SC::WARP_B, RES_OFF, row);
+        } else {
+            cons_partials_tree<F::NVU, NW>(acc, F::NVU, row, sred);
+        }
     } else {
     float acc[F::NPU];
 #pragma unroll
@@ -897,7 +932,7 @@ template <int K, typename UT> struct FrameOps {
     // dynamic shared memory: the per-warp stages of the streaming form
     template <typename FT> static constexpr int dyn_smem()
     {
-        return F::STREAM ? F::NW * STG_D * StageCfg<K, FT, UT>::STAGE_B : 0;
+        return F::STREAM ? F::NW * StageCfg<K, FT, UT>::WARP_B : 0;
     }
     template <typename FT> static cudaError_t launch_t(const FrameArgs &a, int grid, cudaStream_t s)
     {

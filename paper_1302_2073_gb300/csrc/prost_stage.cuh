@@ -29,16 +29,29 @@ constexpr int STG_ROWS = 32;  // rows per step (one per lane)
 static_assert(TILE_P % STG_ROWS == 0, "whole steps per tile");
 
 template <int K, typename FT, typename UT> struct StageCfg {
-    static constexpr int UB = STG_ROWS * K * (int)sizeof(UT);            // bytes of the subspace block
+    // bfloat16 storage: the products U^T diag(c) U and the Gram on tensor
+    // cores (mma.sync m16n8k16, bf16 operands, FP32 accumulation); the stage
+    // then holds 16 columns (zero beyond K) 80 bytes apart, which puts the 8
+    // rows of every ldmatrix in distinct banks
+    static constexpr bool TC = sizeof(UT) == 2;
+    static constexpr int CS = TC ? 40 : STG_ROWS;                         // elements between columns
+    static constexpr int UCOL = TC ? 16 : K;                             // columns held
+    static constexpr int UB = UCOL * CS * (int)sizeof(UT);               // bytes of the subspace block
     static constexpr int F_OFF = UB;                                     // byte offsets
     static constexpr int L_OFF = F_OFF + STG_ROWS * (int)sizeof(FT);
-    static constexpr int STAGE_B = (L_OFF + STG_ROWS + 31) / 32 * 32;
+    static constexpr int STAGE_B = (L_OFF + STG_ROWS + 127) / 128 * 128;
     static constexpr int CPC = STG_ROWS * (int)sizeof(UT) / 16;          // chunks per column
     static constexpr int NCU = K * CPC;                                  // 16-byte chunks: subspace
     static constexpr int NCF = STG_ROWS * (int)sizeof(FT) / 16;          // frame entries
     static constexpr int NCL = STG_ROWS / 16;                            // labels
     static constexpr int NCH = NCU + NCF + NCL;
     static constexpr int STEPS_PER_TILE = TILE_P / STG_ROWS;
+    // per-warp tensor-core scratch after the stages: two row-major 32 x 16
+    // bf16 tiles (48-byte rows) and the warp's 16 x 16 FP32 result
+    static constexpr int BT_ROW = 24;                                    // bf16 elements per tile row
+    static constexpr int BT_B = STG_ROWS * BT_ROW * 2;
+    static constexpr int SCR_B = TC ? 2 * BT_B + 16 * 16 * 4 : 0;
+    static constexpr int WARP_B = STG_D * STAGE_B + SCR_B;
 };
 
 // Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
@@ -59,6 +72,57 @@ template <int N> __device__ __forceinline__ void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// ---- tensor-core helpers (bfloat16 storage) -----------------------------------
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(p))
+                 : "memory");
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(p))
+                 : "memory");
+}
+// d += a b for a 16 x 16 bf16 A (row-major) and a 16 x 8 bf16 B (column
+// fragments), FP32 accumulation
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+// this lane's row (16 values, zero beyond K) as one row of a 48-byte-row tile
+template <int K> __device__ __forceinline__ void store_tile_row(unsigned char *tile, const uint32_t (&w)[8])
+{
+    uint4 *row = reinterpret_cast<uint4 *>(tile + (threadIdx.x & 31) * 48);
+    row[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    row[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+// the rows of a warp's 16 x 16 mma result (two n-tiles) into a 16 x 16 array
+__device__ __forceinline__ void store_result(float *res, const float (&d0)[4], const float (&d1)[4])
+{
+    const int l = threadIdx.x & 31, g = l >> 2, t = l & 3;
+    res[g * 16 + 2 * t] = d0[0];
+    res[g * 16 + 2 * t + 1] = d0[1];
+    res[(g + 8) * 16 + 2 * t] = d0[2];
+    res[(g + 8) * 16 + 2 * t + 1] = d0[3];
+    res[g * 16 + 8 + 2 * t] = d1[0];
+    res[g * 16 + 8 + 2 * t + 1] = d1[1];
+    res[(g + 8) * 16 + 8 + 2 * t] = d1[2];
+    res[(g + 8) * 16 + 8 + 2 * t + 1] = d1[3];
+}
+
 // This lane's chunks of a step.  Chunk number lane + 32 q of the step's
 // subspace block is column (lane / CPC) + q (32 / CPC) at row part
 // lane % CPC, so for the NQU whole rounds one base pointer per lane serves
@@ -71,6 +135,7 @@ template <int K, typename FT, typename UT> struct Chunks {
     static constexpr int TR = (S::NCH - 32 * NQU + 31) / 32;   // rounds after them (1 or 2)
     static constexpr int QCOL = 32 / S::CPC;                   // columns per round
     static constexpr int RPC = 16 / (int)sizeof(UT);           // rows per subspace chunk
+    static constexpr int QB = QCOL * S::CS * (int)sizeof(UT);  // stage bytes between rounds
     int uoff;      // element offset of this lane's subspace chunk in round 0
     int soff;      // byte offset in the stage
     int tkind[TR]; // later rounds: 0 subspace, 1 frame, 2 labels, 3 none
@@ -80,7 +145,7 @@ template <int K, typename FT, typename UT> struct Chunks {
     __device__ __forceinline__ explicit Chunks(int lane)
     {
         uoff = (lane / S::CPC) * TILE_P + (lane % S::CPC) * RPC;
-        soff = (lane / S::CPC) * STG_ROWS * (int)sizeof(UT) + 16 * (lane % S::CPC);
+        soff = (lane / S::CPC) * S::CS * (int)sizeof(UT) + 16 * (lane % S::CPC);
 #pragma unroll
         for (int r = 0; r < TR; ++r) {
             const int ch = 32 * (NQU + r) + lane;
@@ -111,11 +176,11 @@ template <int K, typename FT, typename UT> struct Chunks {
         const UT *src = ut + uoff + rs;
         unsigned char *dst = st + soff;
 #pragma unroll
-        for (int q = 0; q < NQU; ++q) cp_async16(dst + q * 512, src + q * QCOL * TILE_P, true);
+        for (int q = 0; q < NQU; ++q) cp_async16(dst + q * QB, src + q * QCOL * TILE_P, true);
 #pragma unroll
         for (int r = 0; r < TR; ++r) {
             if (tkind[r] == 0) {
-                cp_async16(dst + (NQU + r) * 512, src + (NQU + r) * QCOL * TILE_P, true);
+                cp_async16(dst + (NQU + r) * QB, src + (NQU + r) * QCOL * TILE_P, true);
             } else if (tkind[r] == 1) {
                 const bool v = rs + toff[r] < nval;
                 cp_async16(st + tsoff[r], v ? (const void *)(ft + rs + toff[r]) : (const void *)lt, v);
@@ -138,6 +203,18 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
                                                 unsigned char *wbuf, float (&acc)[NP])
 {
     using S = StageCfg<K, FT, UT>;
+    // bfloat16 storage: U^T diag(c) U of each step on tensor cores (the warp's
+    // 16 x 16 result into the scratch after its stages), not in acc
+    constexpr bool TCM = S::TC && WM;
+    unsigned char *bhi = wbuf + STG_D * S::STAGE_B, *blo = bhi + S::BT_B;
+    float dm0[4] = {0.f, 0.f, 0.f, 0.f}, dm1[4] = {0.f, 0.f, 0.f, 0.f};
+    if constexpr (S::TC) { // zero the padded columns K .. 15 of every stage
+        for (int i = threadIdx.x & 31; i < STG_D * (16 - K) * S::CS / 2; i += 32) {
+            const int per = (16 - K) * S::CS / 2, st = i / per, w = i - st * per;
+            reinterpret_cast<uint32_t *>(wbuf + st * S::STAGE_B + K * S::CS * 2)[w] = 0u;
+        }
+        __syncwarp();
+    }
     constexpr int NM = WM ? K * (K + 1) / 2 : 0;
     constexpr int SPT = S::STEPS_PER_TILE;
     static_assert(STG_D == SPT + 1, "the copies run one tile ahead");
@@ -200,10 +277,10 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
             const unsigned char *st = wbuf + (k & (STG_D - 1)) * S::STAGE_B;
             float u[K];
 #pragma unroll
-            for (int j = 0; j < K; ++j) u[j] = ld_u(reinterpret_cast<const UT *>(st) + STG_ROWS * j + lane);
+            for (int j = 0; j < K; ++j) u[j] = ld_u(reinterpret_cast<const UT *>(st) + S::CS * j + lane);
             const FT xraw = reinterpret_cast<const FT *>(st + S::F_OFF)[lane];
             const uint8_t lb = st[S::L_OFF + lane];
-            __syncwarp(); // the stage is refilled by a later step's copies
+            if constexpr (!TCM) __syncwarp(); // the stage is refilled by a later step's copies
             const bool valid = STG_ROWS * s + lane < cur.nval;
             const float xv = valid ? (float)xraw : 0.f;
             // u . y in four independent partial sums (shorter dependency chain)
@@ -224,7 +301,36 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
             acc[K + NM + 1] = fmaf(eta, eta, acc[K + NM + 1]);
 #pragma unroll
             for (int j = 0; j < K; ++j) acc[j] = fmaf(eta, u[j], acc[j]);
-            if constexpr (WM) {
+            if constexpr (TCM) {
+                // B = diag(c) U of the step as a row-major tile, split into a
+                // bf16 leading part and a bf16 remainder (M to about FP32
+                // accuracy); A = the stage itself (columns x rows)
+                uint32_t wh[8], wl[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float v0 = 2 * q < K ? cw * u[2 * q] : 0.f;
+                    const float v1 = 2 * q + 1 < K ? cw * u[2 * q + 1] : 0.f;
+                    wh[q] = pack_bf16(v0, v1);
+                    const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&wh[q]);
+                    wl[q] = pack_bf16(v0 - __low2float(h), v1 - __high2float(h));
+                }
+                store_tile_row<K>(bhi, wh);
+                store_tile_row<K>(blo, wl);
+                __syncwarp();
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    uint32_t am[4], bh[4], bl[4];
+                    ldsm_x4(am, st + ((lane & 7) + 8 * ((lane >> 3) & 1)) * (S::CS * 2) + (16 * ks + 8 * (lane >> 4)) * 2);
+                    const int brow = 16 * ks + (lane & 7) + 8 * ((lane >> 3) & 1);
+                    ldsm_x4_t(bh, bhi + brow * 48 + 8 * (lane >> 4) * 2);
+                    ldsm_x4_t(bl, blo + brow * 48 + 8 * (lane >> 4) * 2);
+                    mma_bf16(dm0, am, bh[0], bh[1]);
+                    mma_bf16(dm0, am, bl[0], bl[1]);
+                    mma_bf16(dm1, am, bh[2], bh[3]);
+                    mma_bf16(dm1, am, bl[2], bl[3]);
+                }
+                __syncwarp(); // the tiles and the stage are rewritten later
+            } else if constexpr (WM) {
 #pragma unroll
                 for (int j = 0; j < K; ++j) {
                     const float cu = cw * u[j];
@@ -235,6 +341,7 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
         }
     }
     cp_async_wait<0>();
+    if constexpr (TCM) store_result(reinterpret_cast<float *>(blo + S::BT_B), dm0, dm1);
 }
 
 // k-space vectors of the update pass, held in registers
@@ -254,6 +361,11 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
     using S = StageCfg<K, FT, UT>;
     constexpr int NM = K * (K + 1) / 2;
     constexpr int SPT = S::STEPS_PER_TILE;
+    // bfloat16 storage: the Gram of the new rows on tensor cores (exact bf16
+    // products, FP32 accumulation), the warp's 16 x 16 result into its scratch
+    constexpr bool TC = S::TC;
+    unsigned char *gtile = wbuf + STG_D * S::STAGE_B; // the new rows, one per lane
+    float dg0[4] = {0.f, 0.f, 0.f, 0.f}, dg1[4] = {0.f, 0.f, 0.f, 0.f};
     const DevParams &prm = a.prm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float mu = prm.mu, e = prm.e, pw = prm.p, om = prm.omega, dl = prm.delta;
@@ -299,7 +411,7 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
         const unsigned char *st = wbuf + (k % STG_D) * S::STAGE_B;
         float u[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) u[j] = ld_u(reinterpret_cast<const UT *>(st) + STG_ROWS * j + lane);
+        for (int j = 0; j < K; ++j) u[j] = ld_u(reinterpret_cast<const UT *>(st) + S::CS * j + lane);
         const FT xraw = reinterpret_cast<const FT *>(st + S::F_OFF)[lane];
         const uint8_t lb = st[S::L_OFF + lane];
         __syncwarp();
@@ -347,10 +459,29 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
                 u[j] = round_bf16_sr(u[j], rk >> 16);
             }
         }
+        if constexpr (TC) {
+            // the rounded rows are bf16 values: their products are exact
+            uint32_t wr[8];
 #pragma unroll
-        for (int j = 0; j < K; ++j)
+            for (int q = 0; q < 8; ++q)
+                wr[q] = pack_bf16(2 * q < K ? u[2 * q] : 0.f, 2 * q + 1 < K ? u[2 * q + 1] : 0.f);
+            store_tile_row<K>(gtile, wr);
+            __syncwarp();
 #pragma unroll
-            for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[j], u[l2], acc[tri<K>(j, l2)]);
+            for (int ks = 0; ks < 2; ++ks) {
+                uint32_t am[4], bm[4];
+                ldsm_x4_t(am, gtile + (16 * ks + (lane & 7) + 8 * (lane >> 4)) * 48 + 8 * ((lane >> 3) & 1) * 2);
+                ldsm_x4_t(bm, gtile + (16 * ks + (lane & 7) + 8 * ((lane >> 3) & 1)) * 48 + 8 * (lane >> 4) * 2);
+                mma_bf16(dg0, am, bm[0], bm[1]);
+                mma_bf16(dg1, am, bm[2], bm[3]);
+            }
+            __syncwarp(); // the tile is rewritten by the next step
+        } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+#pragma unroll
+                for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[j], u[l2], acc[tri<K>(j, l2)]);
+        }
         if (write) {
             UT *ub = U + cc * cstride + (int64_t)cpt * K * TILE_P + row;
 #pragma unroll
@@ -372,6 +503,7 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
         }
     }
     cp_async_wait<0>();
+    if constexpr (TC) store_result(reinterpret_cast<float *>(gtile + 2 * S::BT_B), dg0, dg1);
 }
 
 } // namespace prost

@@ -78,24 +78,41 @@ __global__ void __launch_bounds__(WT) k_window(WinArgs a)
         }
         float cpart = 0.f, mpart = 0.f;
         const int64_t px = valid ? e % a.P : 0;
-        for (int t = 0; t < n; ++t) {
-            float uy = 0.f;
+        // TB frames at a time: their entries and labels are loaded before any
+        // arithmetic, so that TB loads per thread are in flight together
+        constexpr int TB = 8;
+        for (int t0 = 0; t0 < n; t0 += TB) {
+            float xv[TB];
+            bool lv[TB];
 #pragma unroll
-            for (int j = 0; j < K; ++j) uy = fmaf(u[j], Ys[j * n + t], uy);
-            float eta = 0.f;
-            if (valid) {
-                const float w = (a.labels && a.labels[(int64_t)t * a.P + px]) ? om : 1.f;
-                const float r = a.X[(int64_t)t * a.m + e] - uy;
-                const float z = fmaf(r, r, mu);
-                const float zp = __powf(z, e2);
-                cpart = fmaf(w * z, zp, cpart);
-                mpart = fmaf(w, zp, mpart);
-                eta = -pw * w * r * zp;
+            for (int q = 0; q < TB; ++q) {
+                const int t = t0 + q;
+                const bool in = valid && t < n;
+                xv[q] = in ? __ldg(a.X + (int64_t)t * a.m + e) : 0.f;
+                lv[q] = in && a.labels && __ldg(a.labels + (int64_t)t * a.P + px);
             }
-            if (GRAD) {
 #pragma unroll
-                for (int j = 0; j < K; ++j) du[j] = fmaf(eta, Ys[j * n + t], du[j]);
-                Hs[tid * (n + 1) + t] = eta;
+            for (int q = 0; q < TB; ++q) {
+                const int t = t0 + q;
+                if (t >= n) break;
+                float uy = 0.f;
+#pragma unroll
+                for (int j = 0; j < K; ++j) uy = fmaf(u[j], Ys[j * n + t], uy);
+                float eta = 0.f;
+                if (valid) {
+                    const float w = lv[q] ? om : 1.f;
+                    const float r = xv[q] - uy;
+                    const float z = fmaf(r, r, mu);
+                    const float zp = __powf(z, e2);
+                    cpart = fmaf(w * z, zp, cpart);
+                    mpart = fmaf(w, zp, mpart);
+                    eta = -pw * w * r * zp;
+                }
+                if (GRAD) {
+#pragma unroll
+                    for (int j = 0; j < K; ++j) du[j] = fmaf(eta, Ys[j * n + t], du[j]);
+                    Hs[tid * (n + 1) + t] = eta;
+                }
             }
         }
         cost += (double)cpart;
@@ -152,14 +169,28 @@ __global__ void __launch_bounds__(WT) k_window(WinArgs a)
     }
 }
 
-// fixed-order sum of the block partials: dY (scaled), the cost, dmu
+// fixed-order sum of a column of nb partial rows by one warp (each lane a
+// strided subset, then a fixed shuffle tree: short FP64 chains)
+__device__ __forceinline__ double warp_col_sum(const double *partials, int nb, int len, int i)
+{
+    double s = 0.0;
+    for (int b = threadIdx.x & 31; b < nb; b += 32) s += partials[(size_t)b * len + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// fixed-order sum of the block partials, a warp per value: dY (scaled), the
+// cost, dmu
 __global__ void k_window_finish(const double *partials, int nblocks, int kn, const float *gscale, float p,
                                 float *dY, float *cost, float *dmu)
 {
     const float gs = gscale ? *gscale : 1.f;
-    for (int i = threadIdx.x; i < kn + 2; i += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * (kn + 2) + i];
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= kn + 2) return;
+    {
+        const double s = warp_col_sum(partials, nblocks, kn + 2, i);
+        if ((threadIdx.x & 31) != 0) return;
         if (i < kn) {
             if (dY) dY[i] = gs * (float)s;
         } else if (i == kn) {
@@ -256,14 +287,13 @@ __global__ void __launch_bounds__(WT) k_vstep(const float *U, const float *D, co
     }
 }
 
-// fixed-order sum of nb partial rows of len values into out (one thread each)
+// fixed-order sum of nb partial rows of len values into out (a warp each)
 __global__ void k_sum_rows(const double *partials, int nb, int len, double *out)
 {
-    for (int i = threadIdx.x; i < len; i += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += partials[(size_t)b * len + i];
-        out[i] = s;
-    }
+    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (i >= len) return;
+    const double s = warp_col_sum(partials, nb, len, i);
+    if ((threadIdx.x & 31) == 0) out[i] = s;
 }
 
 // T = R^{-1} from the packed Gram G = R^T R (FP64, one thread: k <= 16);
@@ -290,11 +320,13 @@ template <int K> __global__ void k_chol_inv(const double *G, double *T, int *sta
             return;
         }
         const double rjj = sqrt(d);
+        const double inv = 1.0 / rjj; // one division per pivot (FP64 division is slow)
         R[j * K + j] = rjj;
+        W[j * K + j] = inv;           // the reciprocal, kept for the back substitution
         for (int c = j + 1; c < K; ++c) {
             double s = W[j * K + c];
             for (int l = 0; l < j; ++l) s -= R[l * K + j] * R[l * K + c];
-            R[j * K + c] = s / rjj;
+            R[j * K + c] = s * inv;
         }
     }
     // T = R^{-1}, upper triangular, by back substitution
@@ -303,7 +335,7 @@ template <int K> __global__ void k_chol_inv(const double *G, double *T, int *sta
         for (int i = c; i >= 0; --i) {
             double s = (i == c) ? 1.0 : 0.0;
             for (int l = i + 1; l <= c; ++l) s -= R[i * K + l] * T[l * K + c];
-            T[i * K + c] = s / R[i * K + i];
+            T[i * K + c] = s * W[i * K + i];
         }
     }
     *status = 0;
@@ -369,9 +401,10 @@ template <int K> struct WinOps {
     static cudaError_t ustep(prost_window *w, const float *U, const float *D, float t, float *Uo)
     {
         k_utd<K><<<w->nb_u, WT, 0, w->stream>>>(U, D, w->m, w->upart);
-        k_sum_rows<<<1, 256, 0, w->stream>>>(w->upart, w->nb_u, K * K, w->A);
+        k_sum_rows<<<(K * K * 32 + 255) / 256, 256, 0, w->stream>>>(w->upart, w->nb_u, K * K, w->A);
         k_vstep<K><<<w->nb_u, WT, 0, w->stream>>>(U, D, w->A, t, w->m, w->V, w->upart);
-        k_sum_rows<<<1, 256, 0, w->stream>>>(w->upart, w->nb_u, K * (K + 1) / 2, w->G);
+        k_sum_rows<<<(K * (K + 1) / 2 * 32 + 255) / 256, 256, 0, w->stream>>>(w->upart, w->nb_u, K * (K + 1) / 2,
+                                                                                w->G);
         k_chol_inv<K><<<1, 32, 0, w->stream>>>(w->G, w->T, w->status);
         k_apply_t<K><<<w->nb_u, WT, 0, w->stream>>>(w->V, w->T, w->m, Uo);
         return cudaGetLastError();
@@ -511,8 +544,10 @@ extern "C" int prost_window_eval(prost_window *w, const float *U, const float *Y
     a.p = w->p;
     a.omega = w->omega;
     WIN_CK(win_ops(w->k).eval(w, a, grad));
-    k_window_finish<<<1, 256, 0, w->stream>>>(w->partials, w->nblocks, w->k * w->n, gscale, w->p,
-                                              grad ? dY : nullptr, cost, grad ? dmu : nullptr);
+    const int nvals = w->k * w->n + 2;
+    k_window_finish<<<(nvals * 32 + 255) / 256, 256, 0, w->stream>>>(w->partials, w->nblocks, w->k * w->n, gscale,
+                                                                     w->p, grad ? dY : nullptr, cost,
+                                                                     grad ? dmu : nullptr);
     WIN_CK(cudaGetLastError());
     return PROST_OK;
 }
