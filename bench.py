@@ -422,6 +422,56 @@ def batched_study(torch, pg, dev, stream, ticks=30, n_distinct=4):
     return out
 
 
+def window_study(torch, pg, dev, reps=50):
+    """The windowed cost and its adjoint at 320x240, n = 64, k = 10 (5 %
+    outliers): forward (cost), forward + backward (cost and dU, dY, dmu), the
+    U-step; CUDA events, mean over reps after a warm-up.  The window is
+    19.7 MB of frames, read once per pass."""
+    import synth
+    X, U0, Y0, _ = synth.window_workload()
+    n, m = X.shape
+    k = U0.shape[1]
+    win = pg.window.WindowCost(m, 1, k, n, 0.25, 5e-5)
+    try:
+        U = torch.from_numpy(U0.astype(np.float32)).to(dev).requires_grad_()
+        Y = torch.from_numpy(Y0.astype(np.float32)).to(dev).requires_grad_()
+        mu = torch.tensor(0.05, dtype=torch.float32, device=dev).requires_grad_()
+        Xt = torch.from_numpy(X).to(dev)
+        out = torch.empty_like(U)
+
+        def timed(fn):
+            for _ in range(5):
+                fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                fn()
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) * 1e3 / reps
+
+        def fwd():
+            with torch.no_grad():
+                win(U, Y, mu, Xt)
+
+        def fwd_bwd():
+            U.grad = Y.grad = mu.grad = None
+            win(U, Y, mu, Xt).backward()
+
+        fwd_bwd()
+        dU = U.grad.detach().clone()
+        t_f, t_fb = timed(fwd), timed(fwd_bwd)
+        t_u = timed(lambda: win.ustep(U.detach(), dU, 1e-6, out))
+    finally:
+        win.close()
+    frame_bytes = X.nbytes
+    return {"workload": "320x240 gray, n = 64, k = 10, 5 % outliers", "forward_us": t_f,
+            "forward_backward_us": t_fb, "ustep_us": t_u,
+            "forward_GBps": frame_bytes / (t_f * 1e-6) / 1e9,
+            "backward_pass_GBps": frame_bytes / ((t_fb - t_f) * 1e-6) / 1e9 if t_fb > t_f else None}
+
+
 def _config(args, vid, wp, steps):
     return {"workload": args.workload, "width": vid.width, "height": vid.height,
             "channels": vid.channels, "k": vid.k, "n_cg": wp["n_cg"], "frame_dtype": vid.dtype,
@@ -552,6 +602,7 @@ def run_ours(args, dist):
         out["bf16_vs_fp32"] = precision_study(torch, pg, dev, stream, flush_l2)
         out["pipeline_160x120_k15"] = pipeline_study(torch, pg, dev, stream, flush_l2)
         out["batched_64_streams"] = batched_study(torch, pg, dev, stream)
+        out["window_320x240_n64_k10"] = window_study(torch, pg, dev)
     if dist.rank == 0 and n == 1 and not args.no_cpu_baseline:
         fps, nf, secs = oracle_sample(args.workload, args.cpu_seconds)
         out["cpu_baseline"] = {"value": fps, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -41,7 +41,9 @@ template <int K, typename UT = float> struct FCfg {
     // (prost_stage.cuh), 8 warps of up to 255 registers, rows staged through
     // shared memory.  One CTA per SM.
     static constexpr bool STREAM = K >= 11 || sizeof(UT) == 2;
-    static constexpr int THREADS = STREAM ? 256 : 512;
+    // bfloat16: the products of the passes on tensor cores leave a lane few
+    // sums, so 16 warps of up to 128 registers
+    static constexpr int THREADS = STREAM && sizeof(UT) == 4 ? 256 : 512;
     static constexpr int NW = THREADS / 32;
     static constexpr int TP = TILE_P;            // pixels per tile
     static constexpr int RW = 2;                 // rows per thread per item (8-byte loads)
@@ -707,7 +709,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     using SC = StageCfg<K, FT, UT>;
     unsigned char *const sbase = reinterpret_cast<unsigned char *>(stage_smem);
     unsigned char *wstage = sbase + (size_t)warp * SC::WARP_B;
-    constexpr int RES_OFF = STG_D * SC::STAGE_B + 2 * SC::BT_B; // a warp's tensor-core result
+    constexpr int RES_OFF = SC::D * SC::STAGE_B + 2 * SC::BT_B; // a warp's tensor-core result
     int buf = 0;
     unsigned long long target = a.bar_base;
     if (stats && tid == 0) a.ks->phase_ts[0] = global_ns();

@@ -51,7 +51,10 @@ template <int K, typename FT, typename UT> struct StageCfg {
     static constexpr int BT_ROW = 24;                                    // bf16 elements per tile row
     static constexpr int BT_B = STG_ROWS * BT_ROW * 2;
     static constexpr int SCR_B = TC ? 2 * BT_B + 16 * 16 * 4 : 0;
-    static constexpr int WARP_B = STG_D * STAGE_B + SCR_B;
+    // steps in flight per warp: 8 (one tile ahead) with 8 warps per SM, 4
+    // with bfloat16 storage, whose 16 warps per SM hide the latency instead
+    static constexpr int D = TC ? 4 : STG_D;
+    static constexpr int WARP_B = D * STAGE_B + SCR_B;
 };
 
 // Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
@@ -194,32 +197,33 @@ template <int K, typename FT, typename UT> struct Chunks {
 // One residual pass of this warp (all lanes) over its tiles r0 + warp,
 // r0 + warp + NW, ... of the CTA's range: per-lane sums [g_st (K) | (WM)
 // U_st^T diag(c) U_st packed | f | |eta|^2 | #non-finite], the standard
-// partial-row layout.  A tile is SPT = 7 steps and STG_D = SPT + 1, so the
-// copies run exactly one tile ahead: step s of tile t + 1 is issued while
-// step s of tile t is consumed (one pointer update per tile, a constant wait
-// depth, the steps of a tile unrolled).
+// partial-row layout; with bfloat16 storage the products U_st^T diag(c) U_st
+// are formed on tensor cores instead (the warp's 16 x 16 result into its
+// scratch).  With S::D = 8 = steps per tile + 1 the copies run exactly one
+// tile ahead (step s of tile t + 1 is issued while step s of tile t is
+// consumed: one pointer update per tile, the steps unrolled); otherwise a
+// general pipeline keeps S::D - 1 steps in flight.
 template <int K, typename FT, typename UT, bool WM, int NW, int NP>
 __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int nres, const float *yf,
                                                 unsigned char *wbuf, float (&acc)[NP])
 {
     using S = StageCfg<K, FT, UT>;
-    // bfloat16 storage: U^T diag(c) U of each step on tensor cores (the warp's
-    // 16 x 16 result into the scratch after its stages), not in acc
+    constexpr int NM = WM ? K * (K + 1) / 2 : 0;
+    constexpr int SPT = S::STEPS_PER_TILE;
+    constexpr int D = S::D;
     constexpr bool TCM = S::TC && WM;
-    unsigned char *bhi = wbuf + STG_D * S::STAGE_B, *blo = bhi + S::BT_B;
+    unsigned char *btile = wbuf + D * S::STAGE_B;
     float dm0[4] = {0.f, 0.f, 0.f, 0.f}, dm1[4] = {0.f, 0.f, 0.f, 0.f};
+    const DevParams &prm = a.prm;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if constexpr (S::TC) { // zero the padded columns K .. 15 of every stage
-        for (int i = threadIdx.x & 31; i < STG_D * (16 - K) * S::CS / 2; i += 32) {
-            const int per = (16 - K) * S::CS / 2, st = i / per, w = i - st * per;
+        constexpr int per = (16 - K) * S::CS / 2;
+        for (int i = lane; i < D * per; i += 32) {
+            const int st = i / per, w = i - st * per;
             reinterpret_cast<uint32_t *>(wbuf + st * S::STAGE_B + K * S::CS * 2)[w] = 0u;
         }
         __syncwarp();
     }
-    constexpr int NM = WM ? K * (K + 1) / 2 : 0;
-    constexpr int SPT = S::STEPS_PER_TILE;
-    static_assert(STG_D == SPT + 1, "the copies run one tile ahead");
-    const DevParams &prm = a.prm;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float y[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) y[j] = yf[j];
@@ -229,6 +233,62 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
     const Chunks<K, FT, UT> ch(lane);
     const UT *U = static_cast<const UT *>(a.U);
     const int ntile = nres > warp ? (nres - warp + NW - 1) / NW : 0;
+
+    // one step: the row `lane` of the 32 rows staged at st
+    auto step_body = [&](const unsigned char *st, bool valid) {
+        float u[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) u[j] = ld_u(reinterpret_cast<const UT *>(st) + S::CS * j + lane);
+        const FT xraw = reinterpret_cast<const FT *>(st + S::F_OFF)[lane];
+        const uint8_t lb = st[S::L_OFF + lane];
+        if constexpr (!TCM) __syncwarp(); // the stage is refilled by a later step's copies
+        const float xv = valid ? (float)xraw : 0.f;
+        // u . y in four independent partial sums (shorter dependency chain)
+        float uq[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int j = 0; j < K; ++j) uq[j & 3] = fmaf(u[j], y[j], uq[j & 3]);
+        const float uy = (uq[0] + uq[1]) + (uq[2] + uq[3]);
+        if constexpr (sizeof(FT) == 4) {
+            if (valid && !isfinite(xv)) acc[K + NM + 2] += 1.f;
+        }
+        const float res = valid ? fmaf(xv, sc, -of) - uy : 0.f;
+        const float z = fmaf(res, res, mu);
+        const float tz = __powf(z, e);
+        const float wv = valid ? (lb != 0 ? om : 1.f) : 0.f;
+        const float cw = wv * tz;
+        acc[K + NM] = fmaf(cw, z, acc[K + NM]);
+        const float eta = -pw * cw * res;
+        acc[K + NM + 1] = fmaf(eta, eta, acc[K + NM + 1]);
+#pragma unroll
+        for (int j = 0; j < K; ++j) acc[j] = fmaf(eta, u[j], acc[j]);
+        if constexpr (TCM) {
+            // B = diag(c) U of the step as a row-major bf16 tile (M feeds only
+            // the CG line step; the rounding of c u averages out over the rows),
+            // A = the stage itself (columns x rows)
+            uint32_t wb[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                wb[q] = pack_bf16(2 * q < K ? cw * u[2 * q] : 0.f, 2 * q + 1 < K ? cw * u[2 * q + 1] : 0.f);
+            store_tile_row<K>(btile, wb);
+            __syncwarp();
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+                uint32_t am[4], bm[4];
+                ldsm_x4(am, st + ((lane & 7) + 8 * ((lane >> 3) & 1)) * (S::CS * 2) + (16 * ks + 8 * (lane >> 4)) * 2);
+                ldsm_x4_t(bm, btile + (16 * ks + (lane & 7) + 8 * ((lane >> 3) & 1)) * 48 + 8 * (lane >> 4) * 2);
+                mma_bf16(dm0, am, bm[0], bm[1]);
+                mma_bf16(dm1, am, bm[2], bm[3]);
+            }
+            __syncwarp(); // the tile and the stage are rewritten later
+        } else if constexpr (WM) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const float cu = cw * u[j];
+#pragma unroll
+                for (int l2 = j; l2 < K; ++l2) acc[K + tri<K>(j, l2)] = fmaf(cu, u[l2], acc[K + tri<K>(j, l2)]);
+            }
+        }
+    };
 
     // a tile of this warp: subspace block, frame and label rows, rows in plane
     struct Tile {
@@ -252,96 +312,67 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
         }
         return t;
     };
-    Tile nxt = make_tile(), cur;
-    if (ntile > 0) {
+
+    if constexpr (D == SPT + 1) {
+        Tile nxt = make_tile(), cur;
+        if (ntile > 0) {
 #pragma unroll
-        for (int s = 0; s < SPT; ++s) {
-            ch.issue(wbuf + s * S::STAGE_B, nxt.ut, nxt.ft, nxt.lt, STG_ROWS * s, nxt.nval, true);
-            cp_async_commit();
-        }
-    }
-    for (int t = 0; t < ntile; ++t) {
-        cur = nxt;
-        const bool more = t + 1 < ntile;
-        if (more) nxt = make_tile();
-        const int kbase = SPT * t;
-#pragma unroll
-        for (int s = 0; s < SPT; ++s) {
-            const int k = kbase + s;
-            if (more)
-                ch.issue(wbuf + ((k + SPT) & (STG_D - 1)) * S::STAGE_B, nxt.ut, nxt.ft, nxt.lt, STG_ROWS * s,
-                         nxt.nval, true);
-            cp_async_commit();
-            cp_async_wait<STG_D - 1>();
-            __syncwarp();
-            const unsigned char *st = wbuf + (k & (STG_D - 1)) * S::STAGE_B;
-            float u[K];
-#pragma unroll
-            for (int j = 0; j < K; ++j) u[j] = ld_u(reinterpret_cast<const UT *>(st) + S::CS * j + lane);
-            const FT xraw = reinterpret_cast<const FT *>(st + S::F_OFF)[lane];
-            const uint8_t lb = st[S::L_OFF + lane];
-            if constexpr (!TCM) __syncwarp(); // the stage is refilled by a later step's copies
-            const bool valid = STG_ROWS * s + lane < cur.nval;
-            const float xv = valid ? (float)xraw : 0.f;
-            // u . y in four independent partial sums (shorter dependency chain)
-            float uq[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int j = 0; j < K; ++j) uq[j & 3] = fmaf(u[j], y[j], uq[j & 3]);
-            const float uy = (uq[0] + uq[1]) + (uq[2] + uq[3]);
-            if constexpr (sizeof(FT) == 4) {
-                if (valid && !isfinite(xv)) acc[K + NM + 2] += 1.f;
+            for (int s = 0; s < SPT; ++s) {
+                ch.issue(wbuf + s * S::STAGE_B, nxt.ut, nxt.ft, nxt.lt, STG_ROWS * s, nxt.nval, true);
+                cp_async_commit();
             }
-            const float res = valid ? fmaf(xv, sc, -of) - uy : 0.f;
-            const float z = fmaf(res, res, mu);
-            const float tz = __powf(z, e);
-            const float wv = valid ? (lb != 0 ? om : 1.f) : 0.f;
-            const float cw = wv * tz;
-            acc[K + NM] = fmaf(cw, z, acc[K + NM]);
-            const float eta = -pw * cw * res;
-            acc[K + NM + 1] = fmaf(eta, eta, acc[K + NM + 1]);
+        }
+        for (int t = 0; t < ntile; ++t) {
+            cur = nxt;
+            const bool more = t + 1 < ntile;
+            if (more) nxt = make_tile();
+            const int kbase = SPT * t;
 #pragma unroll
-            for (int j = 0; j < K; ++j) acc[j] = fmaf(eta, u[j], acc[j]);
-            if constexpr (TCM) {
-                // B = diag(c) U of the step as a row-major tile, split into a
-                // bf16 leading part and a bf16 remainder (M to about FP32
-                // accuracy); A = the stage itself (columns x rows)
-                uint32_t wh[8], wl[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const float v0 = 2 * q < K ? cw * u[2 * q] : 0.f;
-                    const float v1 = 2 * q + 1 < K ? cw * u[2 * q + 1] : 0.f;
-                    wh[q] = pack_bf16(v0, v1);
-                    const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&wh[q]);
-                    wl[q] = pack_bf16(v0 - __low2float(h), v1 - __high2float(h));
-                }
-                store_tile_row<K>(bhi, wh);
-                store_tile_row<K>(blo, wl);
+            for (int s = 0; s < SPT; ++s) {
+                const int k = kbase + s;
+                if (more)
+                    ch.issue(wbuf + ((k + SPT) & (D - 1)) * S::STAGE_B, nxt.ut, nxt.ft, nxt.lt, STG_ROWS * s,
+                             nxt.nval, true);
+                cp_async_commit();
+                cp_async_wait<D - 1>();
                 __syncwarp();
-#pragma unroll
-                for (int ks = 0; ks < 2; ++ks) {
-                    uint32_t am[4], bh[4], bl[4];
-                    ldsm_x4(am, st + ((lane & 7) + 8 * ((lane >> 3) & 1)) * (S::CS * 2) + (16 * ks + 8 * (lane >> 4)) * 2);
-                    const int brow = 16 * ks + (lane & 7) + 8 * ((lane >> 3) & 1);
-                    ldsm_x4_t(bh, bhi + brow * 48 + 8 * (lane >> 4) * 2);
-                    ldsm_x4_t(bl, blo + brow * 48 + 8 * (lane >> 4) * 2);
-                    mma_bf16(dm0, am, bh[0], bh[1]);
-                    mma_bf16(dm0, am, bl[0], bl[1]);
-                    mma_bf16(dm1, am, bh[2], bh[3]);
-                    mma_bf16(dm1, am, bl[2], bl[3]);
+                step_body(wbuf + (k & (D - 1)) * S::STAGE_B, STG_ROWS * s + lane < cur.nval);
+            }
+        }
+    } else {
+        // general pipeline: issue position (tile it, step is), D - 1 steps ahead
+        const int nstep = ntile * SPT;
+        Tile it = make_tile();
+        int is = 0;
+        auto issue_next = [&](int k) {
+            if (k < nstep) {
+                ch.issue(wbuf + (k % D) * S::STAGE_B, it.ut, it.ft, it.lt, STG_ROWS * is, it.nval, true);
+                if (++is == SPT && k + 1 < nstep) {
+                    is = 0;
+                    it = make_tile();
                 }
-                __syncwarp(); // the tiles and the stage are rewritten later
-            } else if constexpr (WM) {
+            }
+            cp_async_commit();
+        };
 #pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    const float cu = cw * u[j];
-#pragma unroll
-                    for (int l2 = j; l2 < K; ++l2) acc[K + tri<K>(j, l2)] = fmaf(cu, u[l2], acc[K + tri<K>(j, l2)]);
-                }
+        for (int k = 0; k < D - 1; ++k) issue_next(k);
+        int cs = 0, ctp = (r0 + warp) % npt;
+        int cnval = (int)min((int64_t)TILE_P, prm.P - (int64_t)ctp * TILE_P);
+        for (int k = 0; k < nstep; ++k) {
+            issue_next(k + D - 1);
+            cp_async_wait<D - 1>();
+            __syncwarp();
+            step_body(wbuf + (k % D) * S::STAGE_B, STG_ROWS * cs + lane < cnval);
+            if (++cs == SPT) {
+                cs = 0;
+                ctp += NW;
+                while (ctp >= npt) ctp -= npt;
+                cnval = (int)min((int64_t)TILE_P, prm.P - (int64_t)ctp * TILE_P);
             }
         }
     }
     cp_async_wait<0>();
-    if constexpr (TCM) store_result(reinterpret_cast<float *>(blo + S::BT_B), dm0, dm1);
+    if constexpr (TCM) store_result(reinterpret_cast<float *>(btile + 2 * S::BT_B), dm0, dm1);
 }
 
 // k-space vectors of the update pass, held in registers
@@ -364,7 +395,7 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
     // bfloat16 storage: the Gram of the new rows on tensor cores (exact bf16
     // products, FP32 accumulation), the warp's 16 x 16 result into its scratch
     constexpr bool TC = S::TC;
-    unsigned char *gtile = wbuf + STG_D * S::STAGE_B; // the new rows, one per lane
+    unsigned char *gtile = wbuf + S::D * S::STAGE_B; // the new rows, one per lane
     float dg0[4] = {0.f, 0.f, 0.f, 0.f}, dg1[4] = {0.f, 0.f, 0.f, 0.f};
     const DevParams &prm = a.prm;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -386,7 +417,7 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
             const UT *ut = U + icc * cstride + (int64_t)ipt * K * TILE_P;
             const FT *ft = static_cast<const FT *>(a.frame) + (int64_t)icc * a.frame_pitch + (int64_t)ipt * TILE_P;
             const uint8_t *lt = a.labels + (int64_t)ipt * TILE_P;
-            ch.issue(wbuf + (k % STG_D) * S::STAGE_B, ut, ft, lt, STG_ROWS * is, inval, icc == 0);
+            ch.issue(wbuf + (k % S::D) * S::STAGE_B, ut, ft, lt, STG_ROWS * is, inval, icc == 0);
             if (++icc == C) {
                 icc = 0;
                 if (++is == SPT) {
@@ -399,16 +430,16 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
         cp_async_commit();
     };
 #pragma unroll
-    for (int k = 0; k < STG_D - 1; ++k) issue_next(k);
+    for (int k = 0; k < S::D - 1; ++k) issue_next(k);
 
     int cs = 0, cc = 0, cpt = u0 + warp;
     int cnval = (int)min((int64_t)TILE_P, prm.P - (int64_t)cpt * TILE_P);
     float wv = 0.f, mx = 0.f;
     for (int k = 0; k < nstep; ++k) {
-        issue_next(k + STG_D - 1);
-        cp_async_wait<STG_D - 1>();
+        issue_next(k + S::D - 1);
+        cp_async_wait<S::D - 1>();
         __syncwarp();
-        const unsigned char *st = wbuf + (k % STG_D) * S::STAGE_B;
+        const unsigned char *st = wbuf + (k % S::D) * S::STAGE_B;
         float u[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) u[j] = ld_u(reinterpret_cast<const UT *>(st) + S::CS * j + lane);
