@@ -123,40 +123,84 @@ template <int K> struct SKState {
 };
 
 // Sum of all CTAs' partial rows in a fixed order (Kahan-compensated FP32),
-// by the consumer threads; identical in every CTA.
-template <int NV, int NCONS>
-__device__ __forceinline__ void reduce_rows(const float *rows, int nrows, int stride, float *tot, float *scr)
+// by the NCONS threads of the CTA, identical in every CTA.  The nrows rows are
+// dealt round-robin into ng groups of at most RED_ROWS rows (more groups when
+// nv is small, so that every thread has work); a unit (group, value) is one
+// thread's batch of loads and compensated sum, two units per thread are in
+// flight at a time, and the ng group sums of each value are added in group
+// order.  One out-of-line body serves every pass of the frame, so the code the
+// last CTA runs at the end of the frame is already in the instruction caches.
+constexpr int RED_ROWS = 24;  // rows per unit (one batch of loads)
+constexpr int RED_SCR = 1280; // floats of group sums (>= NCONS)
+
+__device__ __forceinline__ void kahan_add(float &s, float &c, float v)
 {
-    constexpr int NG = NCONS / NV;
-    constexpr int MAXR = 48; // rows per thread held in flight at once
-    const int t = threadIdx.x, comp = t % NV, grp = t / NV;
-    if (grp < NG) {
-        float s = 0.f, c = 0.f;
-        for (int b0 = grp; b0 < nrows; b0 += MAXR * NG) {
-            float v[MAXR];
+    const float yk = v - c, tk = s + yk;
+    c = (tk - s) - yk;
+    s = tk;
+}
+
+template <int NCONS>
+__device__ __noinline__ void reduce_rows(const float *rows, int nrows, int stride, int nv, float *tot, float *scr)
+{
+    static_assert(RED_SCR >= NCONS, "scratch of the group sums");
+    const int t = threadIdx.x;
+    int ng = max((nrows + RED_ROWS - 1) / RED_ROWS, NCONS / nv);
+    ng = max(1, min(ng, min(nrows, RED_SCR / nv)));
+    const int nu = ng * nv;
+    const size_t step = (size_t)ng * stride; // between the rows of a unit
+    // unit u: rows g, g + ng, ... of value c, with u = g nv + c
+    auto unit1 = [&](int u) {
+        const int g = u / nv, c = u - g * nv;
+        const float *p = rows + (size_t)g * stride + c;
+        float s = 0.f, k = 0.f;
+        for (int b0 = g; b0 < nrows; b0 += RED_ROWS * ng, p += RED_ROWS * step) {
+            float v[RED_ROWS];
 #pragma unroll
-            for (int q = 0; q < MAXR; ++q) {
-                const int b = b0 + q * NG;
-                v[q] = b < nrows ? __ldcg(rows + (size_t)b * stride + comp) : 0.f;
-            }
+            for (int q = 0; q < RED_ROWS; ++q) v[q] = b0 + q * ng < nrows ? __ldcg(p + q * step) : 0.f;
 #pragma unroll
-            for (int q = 0; q < MAXR; ++q) {
-                const float yk = v[q] - c, tk = s + yk;
-                c = (tk - s) - yk;
-                s = tk;
-            }
+            for (int q = 0; q < RED_ROWS; ++q) kahan_add(s, k, v[q]);
         }
-        scr[grp * NV + comp] = s;
+        scr[u] = s;
+    };
+    if (nu <= NCONS) {
+        if (t < nu) unit1(t);
+    } else {
+        for (int u0 = t; u0 < nu; u0 += 2 * NCONS) {
+            const int u1 = u0 + NCONS;
+            if (u1 >= nu) {
+                unit1(u0);
+                continue;
+            }
+            // two units with their loads in flight together
+            const int g0 = u0 / nv, c0 = u0 - g0 * nv;
+            const int g1 = u1 / nv, c1 = u1 - g1 * nv;
+            const float *p0 = rows + (size_t)g0 * stride + c0;
+            const float *p1 = rows + (size_t)g1 * stride + c1;
+            float s0 = 0.f, k0 = 0.f, s1 = 0.f, k1 = 0.f;
+            for (int b0 = g0, b1 = g1; b0 < nrows;
+                 b0 += RED_ROWS * ng, b1 += RED_ROWS * ng, p0 += RED_ROWS * step, p1 += RED_ROWS * step) {
+                float v0[RED_ROWS], v1[RED_ROWS];
+#pragma unroll
+                for (int q = 0; q < RED_ROWS; ++q) {
+                    v0[q] = b0 + q * ng < nrows ? __ldcg(p0 + q * step) : 0.f;
+                    v1[q] = b1 + q * ng < nrows ? __ldcg(p1 + q * step) : 0.f;
+                }
+#pragma unroll
+                for (int q = 0; q < RED_ROWS; ++q) {
+                    kahan_add(s0, k0, v0[q]);
+                    kahan_add(s1, k1, v1[q]);
+                }
+            }
+            scr[u0] = s0;
+            scr[u1] = s1;
+        }
     }
     cons_sync<NCONS>();
-    if (t < NV) {
-        float s = 0.f, c = 0.f;
-        for (int g2 = 0; g2 < NG; ++g2) {
-            const float yk = scr[g2 * NV + t] - c, tk = s + yk;
-            c = (tk - s) - yk;
-            s = tk;
-        }
-        tot[t] = s;
+    for (int c = t; c < nv; c += NCONS) {
+        float s = 0.f, k = 0.f;
+        for (int g = 0; g < ng; ++g) kahan_add(s, k, scr[g * nv + c]);
+        tot[c] = s;
     }
     cons_sync<NCONS>();
 }
@@ -269,6 +313,23 @@ __device__ __forceinline__ float wsumf(float v)
     return v;
 }
 
+// Step size of frame i (Section 3.3): t = max(exp(-tau i) t_init, t_min), to
+// FP32 accuracy, which is all that theta = sigma t (FP32) uses.  The exponent
+// is reduced as tau i = q ln 2 + r with the product and the reduction in FP64
+// (two operations; a library FP64 exponential is a long chain on GB300's
+// narrow FP64 pipe), then exp(-tau i) = 2^-q exp(-r) with |r| <= ln 2 in FP32.
+__device__ __forceinline__ float step_size(const DevParams &prm, int64_t i)
+{
+    const double a = prm.tau * (double)i;
+    float e = 0.f;
+    if (a < 200.0) {
+        const float q = rintf((float)a * 1.44269504f);
+        const float r = (float)fma(-(double)q, 0.69314718055994530942, a);
+        e = ldexpf(expf(-r) * (float)prm.t_init, -(int)q);
+    }
+    return fmaxf(e, (float)prm.t_min);
+}
+
 // CG bookkeeping at iterate `pass` from the reduced sums tot:
 //   WM:  tot = [g_st (K) | M_st packed (K(K+1)/2) | f | |eta|^2 | #non-finite]
 //   !WM: tot = [g_st (K) | f | |eta|^2 | #non-finite]
@@ -349,11 +410,9 @@ __device__ void kspace_cg(SKState<K> &sk, const DevParams &prm, const float *tot
         const float pin2 = ee - gsq;
         const float pin = pin2 > 0.f ? sqrtf(pin2) : 0.f;
         const bool upd = yn > 0.f && pin > 0.f;
-        double t = 0.0;
-        if (l == 0) t = fmax(exp(-prm.tau * (double)sk.frame_index) * prm.t_init, prm.t_min);
-        t = __shfl_sync(FULL, t, 0);
+        const float t = step_size(prm, sk.frame_index);
         const float sigma = pin * yn;
-        const float theta = sigma * (float)t;
+        const float theta = sigma * t;
         const float sh = sinf(0.5f * theta);
         // the update pass works on the stored rows u_st (u = T^T u_st): it needs
         // T v and T g for the dots and w = R^T v, since u_st + gamma R^T v is
@@ -674,7 +733,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     constexpr int NM = F::NM;
     __shared__ float sred[NW * F::NPMAX];
     __shared__ float tot[F::NVR > F::NVU ? F::NVR : F::NVU];
-    __shared__ float rscr[NT];
+    __shared__ float rscr[RED_SCR];
     __shared__ ReorthScratch<K> rs;
     __shared__ SKState<K> sk;
     extern __shared__ __align__(128) float stage_smem[]; // streaming form only
@@ -718,7 +777,6 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         float *row = a.partials + ((size_t)buf * G + b) * a.row_stride;
         const float *rows = a.partials + (size_t)buf * G * a.row_stride;
         target += (unsigned long long)G;
-        const int t0 = 0;
         if (pass < prm.n_cg) {
             const bool trace = stats && tid == 0 && pass == 1;
             float acc[F::NPR];
@@ -727,7 +785,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             if constexpr (F::STREAM)
                 stream_residual<K, FT, UT, true, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
             else
-                residual_pass<K, FT, true>(a, tl, sk, acc, t0);
+                residual_pass<K, FT, true>(a, tl, sk, acc, 0);
             if (trace) a.ks->sub_ts[0] = global_ns();
             if constexpr (F::STREAM && SC::TC) {
                 cons_partials_tree<F::NVR, NW, F::NPR, K, K + NM>(acc, F::NVR, row, sred);
@@ -740,7 +798,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             if (trace) a.ks->sub_ts[1] = global_ns();
             if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
             if (trace) a.ks->sub_ts[2] = global_ns();
-            reduce_rows<F::NVR, NT>(rows, G, a.row_stride, tot, rscr);
+            reduce_rows<NT>(rows, G, a.row_stride, F::NVR, tot, rscr);
             if (trace) a.ks->sub_ts[3] = global_ns();
             if (warp == 0) kspace_cg<K, true>(sk, prm, tot, pass, a.ks, stats);
             if (trace) a.ks->sub_ts[4] = global_ns();
@@ -751,13 +809,13 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             if constexpr (F::STREAM)
                 stream_residual<K, FT, UT, false, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
             else
-                residual_pass<K, FT, false>(a, tl, sk, acc, t0);
+                residual_pass<K, FT, false>(a, tl, sk, acc, 0);
             if constexpr (F::STREAM)
                 cons_partials_tree<F::NVF, NW>(acc, F::NVF, row, sred);
             else
                 cons_partials<F::NPF, NW>(acc, F::NVF, row, sred);
             if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
-            reduce_rows<F::NVF, NT>(rows, G, a.row_stride, tot, rscr);
+            reduce_rows<NT>(rows, G, a.row_stride, F::NVF, tot, rscr);
             if (warp == 0) kspace_cg<K, false>(sk, prm, tot, pass, a.ks, stats);
         }
         cons_sync<NT>();
@@ -805,87 +863,87 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         const volatile float *vg = sk.tg;
         const volatile float *vw = sk.w;
         const FT *frame = static_cast<const FT *>(a.frame);
-        // one pixel per thread and item, all channels' rows loaded up front
-        // (the labels of Step 3 take the maximum over the channels)
-        constexpr int CM = 4;
+        const float *Ub = static_cast<const float *>(a.U);
+        const int C = prm.C, npt = prm.npt;
+        // one step = one channel of one pixel, the channels of a pixel in
+        // turn (the label of Step 3 is the maximum over them, written after
+        // the last); the next step's row, frame entry and label are loaded
+        // while this step computes
         const int nitems = tl.nupt * TP;
-        for (int it = tid; it < nitems; it += NT) {
-            const int pt = tl.u0 + it / TP;
-            const int r0 = it - (it / TP) * TP;
+        int it = tid, c = 0;
+        float un[K], xn = 0.f;
+        uint8_t ln = 0;
+        auto fetch = [&](int it2, int c2) {
+            const int pt = tl.u0 + it2 / TP, r0 = it2 - (it2 / TP) * TP;
+            const int64_t p = (int64_t)pt * TP + r0;
+            const float *ub = Ub + ((int64_t)c2 * npt + pt) * K * TP + r0;
+#pragma unroll
+            for (int j = 0; j < K; ++j) un[j] = __ldcg(ub + j * TP);
+            xn = p < prm.P ? (float)__ldg(frame + (int64_t)c2 * a.frame_pitch + p) : 0.f;
+            if (c2 == 0) ln = a.labels[p];
+        };
+        if (it < nitems) fetch(it, 0);
+        float wv = 0.f, mx = 0.f;
+        while (it < nitems) {
+            float u[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) u[j] = un[j];
+            const float xv = xn;
+            const int pt = tl.u0 + it / TP, r0 = it - (it / TP) * TP;
             const int64_t p = (int64_t)pt * TP + r0;
             const bool valid = p < prm.P;
-            float u[CM][K], xv[CM];
-#pragma unroll
-            for (int c = 0; c < CM; ++c) {
-                if (c < prm.C) {
-                    const float *ub = static_cast<const float *>(a.U) + ((int64_t)c * prm.npt + pt) * K * TP + r0;
-#pragma unroll
-                    for (int j = 0; j < K; ++j) u[c][j] = __ldcg(ub + j * TP);
-                    xv[c] = valid ? (float)__ldg(frame + (int64_t)c * a.frame_pitch + p) : 0.f;
-                }
+            if (c == 0) {
+                wv = valid ? (ln ? om : 1.f) : 0.f;
+                mx = 0.f;
             }
-            const float wv = valid ? (a.labels[p] ? om : 1.f) : 0.f;
-            // dots of the orthonormal rows u = T^T u_st through T y, T g, T v;
-            // each k-space entry is read once per pixel for all channels
-            float uy[CM], ug[CM], uv[CM], gam[CM];
-#pragma unroll
-            for (int c = 0; c < CM; ++c) uy[c] = ug[c] = uv[c] = 0.f;
+            int itn = it, cn = c + 1;
+            if (cn == C) {
+                cn = 0;
+                itn += NT;
+            }
+            if (itn < nitems) fetch(itn, cn);
+            // dots of the orthonormal row u = T^T u_st through T y, T g, T v
+            float uy = 0.f, ug = 0.f, uv = 0.f;
 #pragma unroll
             for (int j = 0; j < K; ++j) {
-                const float yj = vy[j], gj = vg[j], vj = vv[j];
-#pragma unroll
-                for (int c = 0; c < CM; ++c) {
-                    uy[c] = fmaf(u[c][j], yj, uy[c]);
-                    ug[c] = fmaf(u[c][j], gj, ug[c]);
-                    uv[c] = fmaf(u[c][j], vj, uv[c]);
-                }
+                uy = fmaf(u[j], vy[j], uy);
+                ug = fmaf(u[j], vg[j], ug);
+                uv = fmaf(u[j], vv[j], uv);
             }
-            float mx = 0.f;
-#pragma unroll
-            for (int c = 0; c < CM; ++c) {
-                gam[c] = 0.f;
-                if (c < prm.C) {
-                    const float x = fmaf(xv[c], sc, -of);
-                    const float res = valid ? x - uy[c] : 0.f;
-                    const float z = fmaf(res, res, mu);
-                    const float tz = __powf(z, e);
-                    const float eta = -pw * wv * tz * res;
-                    // u <- u + ((cos(theta) - 1) u^T v - sin(theta) pi(eta)_e / |pi(eta)|) v
-                    gam[c] = valid ? fmaf(cm1, uv[c], -snp * (eta - ug[c])) : 0.f;
-                    const float rn = pre ? res : fmaf(-gam[c], yn, res);
-                    if (valid) {
-                        mx = fmaxf(mx, fabsf(rn));
-                        if (write && a.bg_out) a.bg_out[(int64_t)c * prm.P + p] = x - rn + of;
-                    }
-                }
+            const float x = fmaf(xv, sc, -of);
+            const float res = valid ? x - uy : 0.f;
+            const float z = fmaf(res, res, mu);
+            const float tz = __powf(z, e);
+            const float eta = -pw * wv * tz * res;
+            // u <- u + ((cos(theta) - 1) u^T v - sin(theta) pi(eta)_e / |pi(eta)|) v
+            const float gam = valid ? fmaf(cm1, uv, -snp * (eta - ug)) : 0.f;
+            const float rn = pre ? res : fmaf(-gam, yn, res);
+            if (valid) {
+                mx = fmaxf(mx, fabsf(rn));
+                if (write && a.bg_out) a.bg_out[(int64_t)c * prm.P + p] = x - rn + of;
             }
-            // stored rows of u + gamma v: u_st + gamma R^T v
+            // stored row of u + gamma v: u_st + gamma R^T v, its Gram, written back
 #pragma unroll
-            for (int j = 0; j < K; ++j) {
-                const float wj = vw[j];
+            for (int j = 0; j < K; ++j) u[j] = fmaf(gam, vw[j], u[j]);
 #pragma unroll
-                for (int c = 0; c < CM; ++c) u[c][j] = fmaf(gam[c], wj, u[c][j]);
-            }
+            for (int j = 0; j < K; ++j)
 #pragma unroll
-            for (int c = 0; c < CM; ++c) {
-                if (c < prm.C) {
-#pragma unroll
-                    for (int j = 0; j < K; ++j)
-#pragma unroll
-                        for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[c][j], u[c][l2], acc[tri<K>(j, l2)]);
-                    if (write) {
-                        float *ub = static_cast<float *>(a.U) + ((int64_t)c * prm.npt + pt) * K * TP + r0;
-#pragma unroll
-                        for (int j = 0; j < K; ++j) ub[j * TP] = u[c][j];
-                    }
-                }
-            }
-            const uint8_t nl = (valid && mx >= dl) ? 1 : 0;
-            acc[NM] += (float)nl;
+                for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[j], u[l2], acc[tri<K>(j, l2)]);
             if (write) {
-                a.labels[p] = nl;
-                if (a.mask_out && valid) a.mask_out[p] = nl;
+                float *ub = static_cast<float *>(a.U) + ((int64_t)c * npt + pt) * K * TP + r0;
+#pragma unroll
+                for (int j = 0; j < K; ++j) ub[j * TP] = u[j];
             }
+            if (c == C - 1) {
+                const uint8_t nl = (valid && mx >= dl) ? 1 : 0;
+                acc[NM] += (float)nl;
+                if (write) {
+                    a.labels[p] = nl;
+                    if (a.mask_out && valid) a.mask_out[p] = nl;
+                }
+            }
+            it = itn;
+            c = cn;
         }
     }
     if (tid == 0 && stats) a.ks->sub_ts[5] = global_ns();
@@ -901,7 +959,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     cons_sync<NT>();
     if (tid == 0 && stats) a.ks->sub_ts[7] = global_ns();
     if (!sk.last) return;
-    reduce_rows<F::NVU, NT>(a.partials + (size_t)buf * G * a.row_stride, G, a.row_stride, tot, rscr);
+    reduce_rows<NT>(a.partials + (size_t)buf * G * a.row_stride, G, a.row_stride, F::NVU, tot, rscr);
     if (tid == 0) a.ks->sub_ts[8] = global_ns();
     end_frame<K, NT>(sk, a.ks, tot, tot[NM], rs);
     if (tid == 0) a.ks->sub_ts[9] = global_ns();

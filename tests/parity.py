@@ -21,6 +21,11 @@ MASK_BAND = 1e-6
 Y_RTOL = 1e-5
 U_RTOL = 1e-5
 THETA_RTOL = 1e-4
+# The step size t = max(exp(-tau i) t_init, t_min) of Section 3.3 enters only
+# through theta = sigma t, an FP32 product, so the kernel forms t to FP32
+# accuracy: the FP32 exponential (2 ulp) of the reduced argument (rounded to
+# FP32) scaled by t_init (rounded to FP32), about 4e-7 relative at most.
+T_RTOL = 1e-6
 
 
 def oracle_params(wp: dict):
@@ -110,5 +115,5 @@ def compare_step(prm_o, wp, U64, y64, labels, i, frame, g: GpuStep, n_cg=None):
     assert err["mask_unexcused"] == 0, np.nonzero(diff & ~excused)[0][:10]
     assert abs(int(g.stats.n_foreground) - int(tr.n_foreground)) <= int(diff.sum())
     assert g.stats.frames == i + 1
-    assert abs(g.stats.t - tr.t) <= 1e-14 * tr.t
+    assert abs(g.stats.t - tr.t) <= T_RTOL * tr.t
     return err, st, res

@@ -8,7 +8,7 @@ import pytest
 import oracle
 import synth
 import paper_1302_2073_gb300 as pg
-from parity import compare_step, gpu_params, gpu_step_from, matched_start, oracle_params
+from parity import T_RTOL, compare_step, gpu_params, gpu_step_from, matched_start, oracle_params
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -114,7 +114,7 @@ def test_stats_report_the_step_size_rule():
             pg.prost_set_frame_index(h, i)
             assert pg.prost_step(h, f, np.empty(vid.P, np.uint8)) == pg.PROST_OK
             st = pg.prost_get_stats(h)
-            assert abs(st.t - oracle.step_size(prm_o, i)) <= 1e-14 * st.t
+            assert abs(st.t - oracle.step_size(prm_o, i)) <= T_RTOL * st.t
             assert st.frames == i + 1
     finally:
         pg.prost_destroy(h)
