@@ -456,79 +456,77 @@ __device__ void kspace_cg(SKState<K> &sk, const DevParams &prm, const float *tot
 __device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// 1/sqrt(d) in FP64 for d near 1 (the diagonal of the Gram of a nearly
-// orthonormal basis): Newton-Raphson for the reciprocal square root from
-// y = 1, y <- y (3 - d y^2) / 2, which converges quadratically and reaches
-// FP64 accuracy in 6 steps for |d - 1| <= 1/4.  Farther from 1 the library
-// square root and division are used.
-__device__ __forceinline__ double rsqrt_near1(double d)
+// 1/sqrt(d) in FP64: the FP32 reciprocal square root as the start, then two
+// Newton-Raphson steps y <- y (3 - d y^2) / 2, each of which squares the
+// relative error (about 1e-7, 1e-14, then FP64 rounding), so the chain is six
+// dependent FP64 operations.  d outside the normal FP32 range takes the
+// library square root and division.
+__device__ __forceinline__ double rsqrt_fp64(double d)
 {
-    if (fabs(d - 1.0) > 0.25) return 1.0 / sqrt(d);
+    const float df = (float)d;
+    if (!(df >= 1.17549435e-38f && df <= 3.0e38f)) return 1.0 / sqrt(d);
     const double hd = dmul(-0.5, d);
-    double y = 1.0;
-#pragma unroll
-    for (int i = 0; i < 6; ++i) y = dmul(y, dfma(hd, dmul(y, y), 1.5));
+    double y = (double)rsqrtf(df);
+    y = dmul(y, dfma(hd, dmul(y, y), 1.5));
+    y = dmul(y, dfma(hd, dmul(y, y), 1.5));
     return y;
 }
 
-// Cholesky-QR factors of the stored rows from their Gram matrix G (packed
-// upper, FP32 sums), in FP64 by one warp: G = R^T R, T = R^{-1} (row-major
-// k x k in sR, sT), and the coefficients y_old of the previous basis
-// U_st T_old re-expressed in the orthonormal basis U_st T: y_new = R T_old y_old.
-// Right-looking over the k^2 entries, lane-parallel.  Returns false when G is
-// not positive definite (then R = T = I and y_new = T_old y_old).
 // Right-looking FP64 Cholesky G = R^T R (G in sW, overwritten) and T = R^{-1}
-// for Gram matrices away from the identity; one warp (lanes of the calling
-// warp).  Returns false when G is not positive definite.
-template <int K>
-__device__ bool cholesky_rl(double *sR, double *sT, double *sW)
+// (row-major k x k in sR, sT) for Gram matrices away from the identity, by
+// the NT threads of the CTA, one entry of the k^2 per thread per step: GB300's
+// FP64 pipe is narrow per SM sub-partition, so the updates are spread over all
+// warps, and only warp 0 forms each pivot's reciprocal square root (inv).
+// Returns false when G is not positive definite (then R = T = I).  The pivot
+// loops stay rolled: this code runs once per frame, cold in the instruction
+// caches, where its size costs more than its loop overhead.
+template <int K, int NT>
+__device__ bool cholesky_rl(double *sR, double *sT, double *sW, double *inv)
 {
-    const int lane = threadIdx.x & 31;
-    for (int q = lane; q < K * K; q += 32) sR[q] = 0.0;
-    __syncwarp();
-    double inv[K];
+    static_assert(K * K <= NT && K <= 32, "one entry per thread, a row per warp");
+    const int t = threadIdx.x;
+    const bool el = t < K * K;
+    const int i = t / K, l = t - (t / K) * K;
+    if (el) sR[t] = 0.0;
+    cons_sync<NT>();
     bool ok = true;
-#pragma unroll
+#pragma unroll 1
     for (int a = 0; a < K; ++a) {
-        const double d = sW[a * K + a];
+        const double d = sW[a * K + a]; // the same value in every thread
         if (!(d > 0.0)) {
             ok = false;
             break;
         }
-        const double ri = rsqrt_near1(d);
-        inv[a] = ri;
-        for (int l = lane; l < K; l += 32)
-            if (l >= a) sR[a * K + l] = l == a ? dmul(d, ri) : dmul(sW[a * K + l], ri);
-        __syncwarp();
-        for (int q = lane; q < K * K; q += 32) {
-            const int i = q / K, l = q - i * K;
-            if (i > a && l >= i) sW[q] = dfma(-sR[a * K + i], sR[a * K + l], sW[q]);
+        if (t < 32) {
+            const double ri = rsqrt_fp64(d);
+            if (t == 0) inv[a] = ri;
+            if (t >= a && t < K) sR[a * K + t] = t == a ? dmul(d, ri) : dmul(sW[a * K + t], ri);
         }
-        __syncwarp();
+        cons_sync<NT>();
+        if (el && i > a && l >= i) sW[t] = dfma(-sR[a * K + i], sR[a * K + l], sW[t]);
+        cons_sync<NT>();
     }
     if (!ok) {
-        for (int q = lane; q < K * K; q += 32) sR[q] = sT[q] = (q / K == q % K) ? 1.0 : 0.0;
+        if (el) sR[t] = sT[t] = i == l ? 1.0 : 0.0;
     } else {
-        for (int q = lane; q < K * K; q += 32) sW[q] = (q / K == q % K) ? 1.0 : 0.0;
-        __syncwarp();
-#pragma unroll
+        if (el) sW[t] = i == l ? 1.0 : 0.0;
+        cons_sync<NT>();
+#pragma unroll 1
         for (int r = K - 1; r >= 0; --r) {
-            for (int l = lane; l < K; l += 32) sT[r * K + l] = dmul(sW[r * K + l], inv[r]);
-            __syncwarp();
-            for (int q = lane; q < K * K; q += 32) {
-                const int i = q / K, l = q - i * K;
-                if (i < r) sW[q] = dfma(-sR[i * K + r], sT[r * K + l], sW[q]);
-            }
-            __syncwarp();
+            if (t < K) sT[r * K + t] = dmul(sW[r * K + t], inv[r]);
+            cons_sync<NT>();
+            if (el && i < r) sW[t] = dfma(-sR[i * K + r], sT[r * K + l], sW[t]);
+            cons_sync<NT>();
         }
     }
-    __syncwarp();
+    cons_sync<NT>();
     return ok;
 }
 
 // Scratch of the end-of-frame re-orthonormalisation (last CTA).
 template <int K> struct ReorthScratch {
     double R[K * K], T[K * K], W[K * K], Told[K * K], ty[K];
+    double inv[K];
     float Xh[K * K], Xl[K * K], X2[K * K];
     float emax;
     int ok;
@@ -551,7 +549,8 @@ template <int K> struct ReorthScratch {
 // series I - X + X^2 - X^3 (the next term is below 1e-20).  The pieces are
 // summed into FP64, which gives R and T to FP64 accuracy without long FP64
 // dependency chains (GB300's FP64 pipe has a long latency).  Gram matrices
-// farther from I take the right-looking FP64 factorisation.
+// farther from I (bfloat16 stored rows, whose rounding moves the Gram away
+// from I) take the right-looking FP64 factorisation.
 template <int K, int NT>
 __device__ void end_frame(const SKState<K> &sk, KState *ks, const float *G, float n_fg, ReorthScratch<K> &rs)
 {
@@ -610,8 +609,8 @@ __device__ void end_frame(const SKState<K> &sk, KState *ks, const float *G, floa
             rs.T[t] = ((id - xh) - xl) + ((double)x2 - (double)x3);
         }
         if (t == 0) rs.ok = 1;
-    } else if (t < 32) {
-        const bool ok = cholesky_rl<K>(rs.R, rs.T, rs.W);
+    } else {
+        const bool ok = cholesky_rl<K, NT>(rs.R, rs.T, rs.W, rs.inv);
         if (t == 0) rs.ok = ok ? 1 : 0;
     }
     cons_sync<NT>();
