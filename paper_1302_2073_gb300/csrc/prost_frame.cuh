@@ -767,7 +767,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     using SC = StageCfg<K, FT, UT>;
     unsigned char *const sbase = reinterpret_cast<unsigned char *>(stage_smem);
     unsigned char *wstage = sbase + (size_t)warp * SC::WARP_B;
-    constexpr int RES_OFF = SC::D * SC::STAGE_B + 2 * SC::BT_B; // a warp's tensor-core result
+    constexpr int RES_OFF = SC::D * SC::STAGE_B + SC::RES_B; // a warp's tensor-core result
     int buf = 0;
     unsigned long long target = a.bar_base;
     if (stats && tid == 0) a.ks->phase_ts[0] = global_ns();

@@ -46,13 +46,15 @@ template <int K, typename FT, typename UT> struct StageCfg {
     static constexpr int NCL = STG_ROWS / 16;                            // labels
     static constexpr int NCH = NCU + NCF + NCL;
     static constexpr int STEPS_PER_TILE = TILE_P / STG_ROWS;
-    // per-warp tensor-core scratch after the stages: two row-major 32 x 16
-    // bf16 tiles (48-byte rows) and the warp's 16 x 16 FP32 result
+    // per-warp tensor-core scratch after the stages: one row-major 32 x 16
+    // bf16 tile (48-byte rows) and the warp's 16 x 16 FP32 result
     static constexpr int BT_ROW = 24;                                    // bf16 elements per tile row
     static constexpr int BT_B = STG_ROWS * BT_ROW * 2;
-    static constexpr int SCR_B = TC ? 2 * BT_B + 16 * 16 * 4 : 0;
+    static constexpr int RES_B = BT_B;                                   // offset of the result
+    static constexpr int SCR_B = TC ? BT_B + 16 * 16 * 4 : 0;
     // steps in flight per warp: 8 (one tile ahead) with 8 warps per SM, 4
     // with bfloat16 storage, whose 16 warps per SM hide the latency instead
+    // (6 measured no faster)
     static constexpr int D = TC ? 4 : STG_D;
     static constexpr int WARP_B = D * STAGE_B + SCR_B;
 };
@@ -372,7 +374,7 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
         }
     }
     cp_async_wait<0>();
-    if constexpr (TCM) store_result(reinterpret_cast<float *>(btile + 2 * S::BT_B), dm0, dm1);
+    if constexpr (TCM) store_result(reinterpret_cast<float *>(btile + S::RES_B), dm0, dm1);
 }
 
 // k-space vectors of the update pass, held in registers
@@ -534,7 +536,7 @@ __device__ __forceinline__ void stream_update(const FrameArgs &a, int u0, int nu
         }
     }
     cp_async_wait<0>();
-    if constexpr (TC) store_result(reinterpret_cast<float *>(gtile + 2 * S::BT_B), dg0, dg1);
+    if constexpr (TC) store_result(reinterpret_cast<float *>(gtile + S::RES_B), dg0, dg1);
 }
 
 } // namespace prost
