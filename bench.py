@@ -431,7 +431,9 @@ def window_study(torch, pg, dev, reps=50):
     """The windowed cost and its adjoint at 320x240, n = 64, k = 10 (5 %
     outliers): forward (cost), forward + backward (cost and dU, dY, dmu), the
     U-step; CUDA events, mean over reps after a warm-up.  The window is
-    19.7 MB of frames, read once per pass."""
+    19.7 MB of frames, read once per pass.  Through torch.autograd each call
+    costs more host time than device time, so the same passes are also timed
+    as back-to-back C-ABI calls, where the device sets the pace."""
     import synth
     X, U0, Y0, _ = synth.window_workload()
     n, m = X.shape
@@ -468,13 +470,21 @@ def window_study(torch, pg, dev, reps=50):
         dU = U.grad.detach().clone()
         t_f, t_fb = timed(fwd), timed(fwd_bwd)
         t_u = timed(lambda: win.ustep(U.detach(), dU, 1e-6, out))
+        # the same passes as direct C-ABI calls (no autograd bookkeeping)
+        Ud, Yd, mud = U.detach(), Y.detach(), mu.detach()
+        cost_t = torch.empty((), dtype=torch.float32, device=dev)
+        dUo, dYo, dmuo = torch.empty_like(Ud), torch.empty_like(Yd), torch.empty_like(mud)
+        t_fa = timed(lambda: pg.prost_window_eval(win.handle, Ud, Yd, Xt, None, mud, cost_t))
+        t_ga = timed(lambda: pg.prost_window_eval(win.handle, Ud, Yd, Xt, None, mud, cost_t, dUo, dYo, dmuo))
     finally:
         win.close()
     frame_bytes = X.nbytes
-    return {"workload": "320x240 gray, n = 64, k = 10, 5 % outliers", "forward_us": t_f,
-            "forward_backward_us": t_fb, "ustep_us": t_u,
-            "forward_GBps": frame_bytes / (t_f * 1e-6) / 1e9,
-            "backward_pass_GBps": frame_bytes / ((t_fb - t_f) * 1e-6) / 1e9 if t_fb > t_f else None}
+    return {"workload": "320x240 gray, n = 64, k = 10, 5 % outliers",
+            "autograd": {"forward_us": t_f, "forward_backward_us": t_fb},
+            "abi": {"cost_us": t_fa, "cost_and_gradients_us": t_ga,
+                    "cost_GBps": frame_bytes / (t_fa * 1e-6) / 1e9,
+                    "cost_and_gradients_GBps": frame_bytes / (t_ga * 1e-6) / 1e9},
+            "ustep_us": t_u}
 
 
 def _config(args, vid, wp, steps):

@@ -312,8 +312,10 @@ void prost_batch_destroy(prost_batch *b);
  * all given, the gradients multiplied by *gscale (a device float, NULL: 1).
  * prost_window_ustep moves U along the window gradient dU: the projection
  * G = (I - U U^T) dU (Eq. gproject), V = U - t G and the Cholesky-QR
- * retraction U_out = V R^{-1} (V^T V = R^T R in FP64); status_out (device
- * int, or NULL) receives 0, or -1 if V^T V is not positive definite.
+ * retraction U_out = V R^{-1} (V^T V = R^T R in FP64), one cooperative
+ * launch with two bounded grid barriers; status_out (device int, or NULL)
+ * receives 0, -1 if V^T V is not positive definite, or -2 if a grid barrier
+ * gave up (about a second); U_out is unwritten in both error cases.
  * All calls only enqueue on the window's stream.  Errors: PROST_EINVAL (sizes:
  * 1 <= k <= 16, 1 <= n <= 128, 0 < p <= 2; NULL pointers), PROST_ENOMEM,
  * PROST_ECUDA. */

@@ -19,7 +19,15 @@
 //
 // The U-step: G = (I - U U^T) dF/dU (the projection of Eq. gproject applied to
 // the window gradient), V = U - t G, and the Cholesky-QR retraction
-// U' = V R^{-1} with V^T V = R^T R factored in FP64.
+// U' = V R^{-1} with V^T V = R^T R factored in FP64, in one cooperative launch.
+//
+// The three products of the window pass were also built on tensor cores
+// (mma.sync m16n8k8 tf32, operands split hi + mid + lo, a warp per 16 rows and
+// all frames).  It matched the oracle once every product started from a zero
+// accumulator (accumulating into a large one biased dY by 1.7e-5 relative),
+// but at 16 rows per warp and up to 226 registers it ran at 8 warps per SM and
+// took 31 us (forward) and 46 us (with gradients) against this pass's 21 and
+// 34 us: at k = 10 the products are skinny and the pass is bound by its loads.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -29,6 +37,7 @@
 #include <string>
 
 #include "prost.h"
+#include "prost_frame.cuh" // reduce_rows, cholesky_rl: the frame kernel's fixed-order sum and FP64 factors
 
 namespace {
 
@@ -202,162 +211,144 @@ __global__ void k_window_finish(const double *partials, int nblocks, int kn, con
 }
 
 // ---- U-step -----------------------------------------------------------------
+//
+// One cooperative launch, one CTA per SM, each CTA a contiguous range of rows:
+//   A = U^T dU                        (partial per CTA, grid barrier, fixed-order sum)
+//   V = U - t (dU - U A), Gram V^T V  (V written; partial per CTA, grid barrier, sum)
+//   V^T V = R^T R, T = R^{-1}         (FP64, every CTA the same)
+//   U_out = V T
+// Rows go through shared memory in tiles of WT (U and dU, then V), and thread
+// i forms entry i of U^T dU or of V^T V over the tile, so no thread holds a
+// k x k accumulator.
 
-// A = U^T D (k x k), per-block partials then a fixed-order sum
-template <int K>
-__global__ void __launch_bounds__(WT) k_utd(const float *U, const float *D, int64_t m, double *partials)
-{
-    float acc[K * K];
-#pragma unroll
-    for (int i = 0; i < K * K; ++i) acc[i] = 0.f;
-    for (int64_t e = (int64_t)blockIdx.x * WT + threadIdx.x; e < m; e += (int64_t)gridDim.x * WT) {
-        float u[K], d[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            u[j] = U[e * K + j];
-            d[j] = D[e * K + j];
-        }
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-#pragma unroll
-            for (int j = 0; j < K; ++j) acc[i * K + j] = fmaf(u[i], d[j], acc[i * K + j]);
-    }
-    __shared__ float red[WT / 32][K * K];
-#pragma unroll
-    for (int i = 0; i < K * K; ++i) {
-        float v = acc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][i] = v;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < K * K; i += WT) {
-        double s = 0.0;
-        for (int w = 0; w < WT / 32; ++w) s += red[w][i];
-        partials[(size_t)blockIdx.x * K * K + i] = s;
-    }
-}
+constexpr long long UWAIT_LIMIT = 2000000000ll; // SM clock cycles (about 1 s)
+constexpr int URS = KMAXW * KMAXW;              // floats per partial row
 
-// V = U - t (D - U A): the step along the projected gradient, written to V;
-// and the Gram V^T V (packed upper) per block
-template <int K>
-__global__ void __launch_bounds__(WT) k_vstep(const float *U, const float *D, const double *A, float t, int64_t m,
-                                             float *V, double *partials)
+struct UstepArgs {
+    const float *U, *D;
+    float *V, *Uo;
+    float *rows;       // 2 x G partial rows of URS floats
+    unsigned int *bar; // arrival counter, abort flag (zeroed before the launch)
+    int *status;
+    int64_t m;
+    float t;
+};
+
+// Grid barrier: arrive, then a bounded spin; false when it gave up (the abort
+// flag then releases every other CTA too).
+__device__ bool ustep_wait(unsigned int *bar, unsigned int target)
 {
-    __shared__ float sA[K * K];
-    for (int i = threadIdx.x; i < K * K; i += WT) sA[i] = (float)A[i];
+    __shared__ int ok_s;
     __syncthreads();
-    constexpr int NM = K * (K + 1) / 2;
-    float acc[NM];
-#pragma unroll
-    for (int i = 0; i < NM; ++i) acc[i] = 0.f;
-    for (int64_t e = (int64_t)blockIdx.x * WT + threadIdx.x; e < m; e += (int64_t)gridDim.x * WT) {
-        float u[K], v[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) u[j] = U[e * K + j];
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            float ua = 0.f;
-#pragma unroll
-            for (int i = 0; i < K; ++i) ua = fmaf(u[i], sA[i * K + j], ua);
-            v[j] = u[j] - t * (D[e * K + j] - ua);
-            V[e * K + j] = v[j];
-        }
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-#pragma unroll
-            for (int j = i; j < K; ++j) {
-                const int q = i * K - (i * (i - 1)) / 2 + (j - i); // packed upper (i, j)
-                acc[q] = fmaf(v[i], v[j], acc[q]);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        int ok = 1;
+        const long long t0 = clock64();
+        unsigned int it = 0;
+        for (;;) {
+            unsigned int v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            if ((++it & 15u) == 0 && (*(volatile unsigned int *)(bar + 1) || clock64() - t0 > UWAIT_LIMIT)) {
+                atomicExch(bar + 1, 1u);
+                ok = 0;
+                break;
             }
-    }
-    __shared__ float red[WT / 32][NM];
-#pragma unroll
-    for (int i = 0; i < NM; ++i) {
-        float x = acc[i];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][i] = x;
+        }
+        ok_s = ok;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < NM; i += WT) {
-        double s = 0.0;
-        for (int w = 0; w < WT / 32; ++w) s += red[w][i];
-        partials[(size_t)blockIdx.x * NM + i] = s;
-    }
+    return ok_s != 0;
 }
 
-// fixed-order sum of nb partial rows of len values into out (a warp each)
-__global__ void k_sum_rows(const double *partials, int nb, int len, double *out)
-{
-    const int i = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    if (i >= len) return;
-    const double s = warp_col_sum(partials, nb, len, i);
-    if ((threadIdx.x & 31) == 0) out[i] = s;
-}
-
-// T = R^{-1} from the packed Gram G = R^T R (FP64, one thread: k <= 16);
-// status 0, or -1 when G is not positive definite
-template <int K> __global__ void k_chol_inv(const double *G, double *T, int *status)
-{
-    if (threadIdx.x != 0) return;
-    double R[K * K], W[K * K];
-    int q = 0;
-    for (int i = 0; i < K; ++i)
-        for (int j = 0; j < K; ++j) W[i * K + j] = 0.0;
-    for (int i = 0; i < K; ++i)
-        for (int j = i; j < K; ++j) {
-            W[i * K + j] = G[q];
-            W[j * K + i] = G[q];
-            ++q;
-        }
-    for (int i = 0; i < K * K; ++i) R[i] = 0.0;
-    for (int j = 0; j < K; ++j) {
-        double d = W[j * K + j];
-        for (int l = 0; l < j; ++l) d -= R[l * K + j] * R[l * K + j];
-        if (!(d > 0.0)) {
-            *status = -1;
-            return;
-        }
-        const double rjj = sqrt(d);
-        const double inv = 1.0 / rjj; // one division per pivot (FP64 division is slow)
-        R[j * K + j] = rjj;
-        W[j * K + j] = inv;           // the reciprocal, kept for the back substitution
-        for (int c = j + 1; c < K; ++c) {
-            double s = W[j * K + c];
-            for (int l = 0; l < j; ++l) s -= R[l * K + j] * R[l * K + c];
-            R[j * K + c] = s * inv;
-        }
-    }
-    // T = R^{-1}, upper triangular, by back substitution
-    for (int i = 0; i < K * K; ++i) T[i] = 0.0;
-    for (int c = 0; c < K; ++c) {
-        for (int i = c; i >= 0; --i) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int l = i + 1; l <= c; ++l) s -= R[i * K + l] * T[l * K + c];
-            T[i * K + c] = s * W[i * K + i];
-        }
-    }
-    *status = 0;
-}
-
-// U' = V T
 template <int K>
-__global__ void __launch_bounds__(WT) k_apply_t(const float *V, const double *T, int64_t m, float *Uo)
+__global__ void __launch_bounds__(WT, 1) k_ustep(UstepArgs a)
 {
-    __shared__ float sT[K * K];
-    for (int i = threadIdx.x; i < K * K; i += WT) sT[i] = (float)T[i];
+    constexpr int KK = K * K, NM = K * (K + 1) / 2;
+    static_assert(KK <= WT, "one k x k entry per thread");
+    __shared__ float Us[WT * K], Ds[WT * K];
+    __shared__ float tot[KK], sA[KK], sTf[KK];
+    __shared__ float scr[prost::RED_SCR];
+    __shared__ double sR[KK], sT[KK], sW[KK], sinv[K];
+    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+    const int64_t e0 = a.m * b / G, e1 = a.m * (b + 1) / G;
+    const int ri = tid / K, rl = tid - (tid / K) * K; // this thread's entry (ri, rl)
+
+    // A = U^T dU over this CTA's rows
+    float acc = 0.f;
+    for (int64_t t0 = e0; t0 < e1; t0 += WT) {
+        const int nr = (int)min((int64_t)WT, e1 - t0);
+        for (int q = tid; q < nr * K; q += WT) {
+            Us[q] = a.U[t0 * K + q];
+            Ds[q] = a.D[t0 * K + q];
+        }
+        __syncthreads();
+        if (tid < KK)
+            for (int r = 0; r < nr; ++r) acc = fmaf(Us[r * K + ri], Ds[r * K + rl], acc);
+        __syncthreads();
+    }
+    if (tid < KK) a.rows[(size_t)b * URS + tid] = acc;
+    if (!ustep_wait(a.bar, (unsigned)G)) {
+        if (b == 0 && tid == 0) *a.status = -2;
+        return;
+    }
+    prost::reduce_rows<WT>(a.rows, G, URS, KK, tot, scr);
+    for (int i = tid; i < KK; i += WT) sA[i] = tot[i];
     __syncthreads();
-    for (int64_t e = (int64_t)blockIdx.x * WT + threadIdx.x; e < m; e += (int64_t)gridDim.x * WT) {
+
+    // V = U - t (dU - U A) and its Gram
+    const bool gram = tid < KK && ri <= rl;
+    float gacc = 0.f;
+    for (int64_t t0 = e0; t0 < e1; t0 += WT) {
+        const int nr = (int)min((int64_t)WT, e1 - t0);
+        if (tid < nr) {
+            const int64_t e = t0 + tid;
+            float u[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) u[j] = a.U[e * K + j];
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                float ua = 0.f;
+#pragma unroll
+                for (int i = 0; i < K; ++i) ua = fmaf(u[i], sA[i * K + j], ua);
+                const float v = u[j] - a.t * (a.D[e * K + j] - ua);
+                a.V[e * K + j] = v;
+                Us[tid * K + j] = v;
+            }
+        }
+        __syncthreads();
+        if (gram)
+            for (int r = 0; r < nr; ++r) gacc = fmaf(Us[r * K + ri], Us[r * K + rl], gacc);
+        __syncthreads();
+    }
+    if (gram) a.rows[(size_t)(G + b) * URS + prost::tri<K>(ri, rl)] = gacc;
+    if (!ustep_wait(a.bar, 2u * (unsigned)G)) {
+        if (b == 0 && tid == 0) *a.status = -2;
+        return;
+    }
+    prost::reduce_rows<WT>(a.rows + (size_t)G * URS, G, URS, NM, tot, scr);
+    if (tid < KK) sW[tid] = (double)(ri <= rl ? tot[prost::tri<K>(ri, rl)] : tot[prost::tri<K>(rl, ri)]);
+    __syncthreads();
+    const bool ok = prost::cholesky_rl<K, WT>(sR, sT, sW, sinv);
+    if (b == 0 && tid == 0) *a.status = ok ? 0 : -1;
+    if (!ok) return;
+    if (tid < KK) sTf[tid] = (float)sT[tid];
+    __syncthreads();
+
+    // U_out = V T (each thread re-reads the rows it wrote)
+    for (int64_t t0 = e0; t0 < e1; t0 += WT) {
+        const int64_t e = t0 + tid;
+        if (e >= e1) continue;
         float v[K];
 #pragma unroll
-        for (int j = 0; j < K; ++j) v[j] = V[e * K + j];
+        for (int j = 0; j < K; ++j) v[j] = a.V[e * K + j];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             float s = 0.f;
 #pragma unroll
-            for (int i = 0; i <= j; ++i) s = fmaf(v[i], sT[i * K + j], s);
-            Uo[e * K + j] = s;
+            for (int i = 0; i <= j; ++i) s = fmaf(v[i], sTf[i * K + j], s);
+            a.Uo[e * K + j] = s;
         }
     }
 }
@@ -372,11 +363,11 @@ struct prost_window {
     float p, omega;
     cudaStream_t stream;
     int nblocks;      // window kernel
-    int nb_u;         // U-step kernels
+    int nb_u;         // U-step kernel (cooperative, one CTA per SM)
     size_t smem_grad, smem_cost;
     double *partials; // window kernel
-    double *upart;    // U-step partials
-    double *A, *G, *T;
+    float *urows;     // U-step partial rows
+    unsigned int *ubar; // U-step grid barrier
     float *V;
     int *status;
     std::string err;
@@ -400,14 +391,20 @@ template <int K> struct WinOps {
     }
     static cudaError_t ustep(prost_window *w, const float *U, const float *D, float t, float *Uo)
     {
-        k_utd<K><<<w->nb_u, WT, 0, w->stream>>>(U, D, w->m, w->upart);
-        k_sum_rows<<<(K * K * 32 + 255) / 256, 256, 0, w->stream>>>(w->upart, w->nb_u, K * K, w->A);
-        k_vstep<K><<<w->nb_u, WT, 0, w->stream>>>(U, D, w->A, t, w->m, w->V, w->upart);
-        k_sum_rows<<<(K * (K + 1) / 2 * 32 + 255) / 256, 256, 0, w->stream>>>(w->upart, w->nb_u, K * (K + 1) / 2,
-                                                                                w->G);
-        k_chol_inv<K><<<1, 32, 0, w->stream>>>(w->G, w->T, w->status);
-        k_apply_t<K><<<w->nb_u, WT, 0, w->stream>>>(w->V, w->T, w->m, Uo);
-        return cudaGetLastError();
+        cudaError_t e = cudaMemsetAsync(w->ubar, 0, 2 * sizeof(unsigned int), w->stream);
+        if (e != cudaSuccess) return e;
+        UstepArgs a;
+        a.U = U;
+        a.D = D;
+        a.V = w->V;
+        a.Uo = Uo;
+        a.rows = w->urows;
+        a.bar = w->ubar;
+        a.status = w->status;
+        a.m = w->m;
+        a.t = t;
+        void *args[] = {&a};
+        return cudaLaunchCooperativeKernel((void *)k_ustep<K>, dim3(w->nb_u), dim3(WT), args, 0, w->stream);
     }
 };
 
@@ -452,11 +449,9 @@ WinTable win_ops(int k)
 
 void win_free(prost_window *w)
 {
-    double *d[] = {w->partials, w->upart, w->A, w->G, w->T};
-    for (double *p : d)
+    void *d[] = {w->partials, w->urows, w->ubar, w->V, w->status};
+    for (void *p : d)
         if (p) cudaFree(p);
-    if (w->V) cudaFree(w->V);
-    if (w->status) cudaFree(w->status);
 }
 
 } // namespace
@@ -486,7 +481,7 @@ extern "C" int prost_window_init(int64_t m, int32_t channels, int32_t k, int32_t
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = (m + WT - 1) / WT;
     w->nblocks = (int)(tiles < 2 * sms ? tiles : 2 * sms);
-    w->nb_u = (int)(tiles < 4 * sms ? tiles : 4 * sms);
+    w->nb_u = sms; // cooperative: one CTA per SM
     w->smem_cost = (size_t)k * n * sizeof(float);
     w->smem_grad = w->smem_cost + (size_t)WT * (n + 1) * sizeof(float) + (size_t)WT * k * sizeof(float);
     auto bail = [&](int code) {
@@ -501,10 +496,8 @@ extern "C" int prost_window_init(int64_t m, int32_t channels, int32_t k, int32_t
     };
     if (!ck(win_ops(k).attrs(w->smem_grad), "shared memory") ||
         !ck(cudaMalloc(&w->partials, (size_t)w->nblocks * (k * n + 2) * sizeof(double)), "cudaMalloc") ||
-        !ck(cudaMalloc(&w->upart, (size_t)w->nb_u * k * k * sizeof(double)), "cudaMalloc") ||
-        !ck(cudaMalloc(&w->A, (size_t)k * k * sizeof(double)), "cudaMalloc") ||
-        !ck(cudaMalloc(&w->G, (size_t)k * k * sizeof(double)), "cudaMalloc") ||
-        !ck(cudaMalloc(&w->T, (size_t)k * k * sizeof(double)), "cudaMalloc") ||
+        !ck(cudaMalloc(&w->urows, (size_t)2 * w->nb_u * URS * sizeof(float)), "cudaMalloc") ||
+        !ck(cudaMalloc(&w->ubar, 2 * sizeof(unsigned int)), "cudaMalloc") ||
         !ck(cudaMalloc(&w->V, (size_t)m * k * sizeof(float)), "cudaMalloc") ||
         !ck(cudaMalloc(&w->status, sizeof(int)), "cudaMalloc"))
         return bail(PROST_ENOMEM);
