@@ -34,15 +34,15 @@
 namespace prost {
 
 template <int K, typename UT = float> struct FCfg {
-    // k <= 10: 16 warps (at most 4 per SM sub-partition, so each thread may
-    // hold 128 registers), rows loaded straight into registers; the subspace
+    // k <= 10: the register form, 16 warps (at most 4 per SM sub-partition,
+    // so each thread may hold 128 registers), rows loaded straight into
+    // registers and computed in FP32 whatever the storage type; the subspace
     // of the 640x480 workload stays in L2 across the passes of a frame.
-    // k >= 11, and any k with a bfloat16 subspace: the streaming form
-    // (prost_stage.cuh), 8 warps of up to 255 registers, rows staged through
-    // shared memory.  One CTA per SM.
-    static constexpr bool STREAM = K >= 11 || sizeof(UT) == 2;
-    // bfloat16: the products of the passes on tensor cores leave a lane few
-    // sums, so 16 warps of up to 128 registers
+    // k >= 11: the streaming form (prost_stage.cuh), rows staged through
+    // shared memory: float32 8 warps of up to 255 registers; bfloat16 16 warps
+    // of up to 128 registers (the products of the passes on tensor cores leave
+    // a lane few sums).  One CTA per SM.
+    static constexpr bool STREAM = K >= 11;
     static constexpr int THREADS = STREAM && sizeof(UT) == 4 ? 256 : 512;
     static constexpr int NW = THREADS / 32;
     static constexpr int TP = TILE_P;            // pixels per tile
@@ -659,7 +659,7 @@ struct FrameTiles {
 
 // One residual pass over this CTA's tiles: per-thread sums of the cost, U^T eta,
 // |eta|^2, the non-finite count and (WM) U^T diag(c) U.
-template <int K, typename FT, bool WM>
+template <int K, typename FT, typename UT, bool WM>
 __device__ __forceinline__ void residual_pass(const FrameArgs &a, const FrameTiles &tl, const SKState<K> &sk,
                                               float (&acc)[WM ? FCfg<K>::NPR : FCfg<K>::NPF], int t0)
 {
@@ -681,11 +681,11 @@ __device__ __forceinline__ void residual_pass(const FrameArgs &a, const FrameTil
         const int c = ti / prm.npt;
         const int64_t p = (int64_t)(ti - c * prm.npt) * TP + rp * RW;
         const int nvalid = prm.P - p < RW ? (int)(prm.P - p) : RW;
-        const float *ub = static_cast<const float *>(a.U) + (int64_t)ti * K * TP + rp * RW;
+        const UT *ub = static_cast<const UT *>(a.U) + (int64_t)ti * K * TP + rp * RW;
         float u[K][RW];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
-            const float2 v = __ldcg(reinterpret_cast<const float2 *>(ub + j * TP));
+            const float2 v = ldcg_u2(ub + j * TP);
             u[j][0] = v.x;
             u[j][1] = v.y;
         }
@@ -784,7 +784,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             if constexpr (F::STREAM)
                 stream_residual<K, FT, UT, true, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
             else
-                residual_pass<K, FT, true>(a, tl, sk, acc, 0);
+                residual_pass<K, FT, UT, true>(a, tl, sk, acc, 0);
             if (trace) a.ks->sub_ts[0] = global_ns();
             if constexpr (F::STREAM && SC::TC) {
                 cons_partials_tree<F::NVR, NW, F::NPR, K, K + NM>(acc, F::NVR, row, sred);
@@ -808,7 +808,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             if constexpr (F::STREAM)
                 stream_residual<K, FT, UT, false, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
             else
-                residual_pass<K, FT, false>(a, tl, sk, acc, 0);
+                residual_pass<K, FT, UT, false>(a, tl, sk, acc, 0);
             if constexpr (F::STREAM)
                 cons_partials_tree<F::NVF, NW>(acc, F::NVF, row, sred);
             else
@@ -862,8 +862,9 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         const volatile float *vg = sk.tg;
         const volatile float *vw = sk.w;
         const FT *frame = static_cast<const FT *>(a.frame);
-        const float *Ub = static_cast<const float *>(a.U);
+        const UT *Ub = static_cast<const UT *>(a.U);
         const int C = prm.C, npt = prm.npt;
+        const uint32_t sr_key = pcg_hash(prm.sr_seed ^ pcg_hash((uint32_t)sk.frame_index));
         // one step = one channel of one pixel, the channels of a pixel in
         // turn (the label of Step 3 is the maximum over them, written after
         // the last); the next step's row, frame entry and label are loaded
@@ -875,9 +876,9 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         auto fetch = [&](int it2, int c2) {
             const int pt = tl.u0 + it2 / TP, r0 = it2 - (it2 / TP) * TP;
             const int64_t p = (int64_t)pt * TP + r0;
-            const float *ub = Ub + ((int64_t)c2 * npt + pt) * K * TP + r0;
+            const UT *ub = Ub + ((int64_t)c2 * npt + pt) * K * TP + r0;
 #pragma unroll
-            for (int j = 0; j < K; ++j) un[j] = __ldcg(ub + j * TP);
+            for (int j = 0; j < K; ++j) un[j] = ldcg_u(ub + j * TP);
             xn = p < prm.P ? (float)__ldg(frame + (int64_t)c2 * a.frame_pitch + p) : 0.f;
             if (c2 == 0) ln = a.labels[p];
         };
@@ -921,17 +922,29 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 mx = fmaxf(mx, fabsf(rn));
                 if (write && a.bg_out) a.bg_out[(int64_t)c * prm.P + p] = x - rn + of;
             }
-            // stored row of u + gamma v: u_st + gamma R^T v, its Gram, written back
+            // stored row of u + gamma v: u_st + gamma R^T v, its Gram, written
+            // back; a bfloat16 row is rounded stochastically first, with the
+            // streaming form's generator (one hash per stored row, then the
+            // linear congruential step per entry), and its Gram taken of the
+            // stored values
 #pragma unroll
             for (int j = 0; j < K; ++j) u[j] = fmaf(gam, vw[j], u[j]);
+            if constexpr (sizeof(UT) == 2) {
+                uint32_t rk = pcg_hash(sr_key ^ (uint32_t)(c * prm.Pp + p));
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    rk = rk * 1664525u + 1013904223u;
+                    u[j] = round_bf16_sr(u[j], rk >> 16);
+                }
+            }
 #pragma unroll
             for (int j = 0; j < K; ++j)
 #pragma unroll
                 for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[j], u[l2], acc[tri<K>(j, l2)]);
             if (write) {
-                float *ub = static_cast<float *>(a.U) + ((int64_t)c * npt + pt) * K * TP + r0;
+                UT *ub = static_cast<UT *>(a.U) + ((int64_t)c * npt + pt) * K * TP + r0;
 #pragma unroll
-                for (int j = 0; j < K; ++j) ub[j * TP] = u[j];
+                for (int j = 0; j < K; ++j) st_u(ub + j * TP, u[j]); // exact for a rounded bfloat16 value
             }
             if (c == C - 1) {
                 const uint8_t nl = (valid && mx >= dl) ? 1 : 0;

@@ -36,6 +36,19 @@ __device__ __forceinline__ float ld_u(const float *p) { return *p; }
 __device__ __forceinline__ float ld_u(const bf16 *p) { return __bfloat162float(*p); }
 __device__ __forceinline__ float ldg_u(const float *p) { return __ldg(p); }
 __device__ __forceinline__ float ldg_u(const bf16 *p) { return __bfloat162float(__ldg(p)); }
+// L2-only loads (streamed rows): one entry, or the entries of two consecutive
+// rows (8 bytes of float32, 4 bytes of bfloat16 at an even row)
+__device__ __forceinline__ float ldcg_u(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg_u(const bf16 *p)
+{
+    return __uint_as_float((uint32_t)__ldcg(reinterpret_cast<const unsigned short *>(p)) << 16);
+}
+__device__ __forceinline__ float2 ldcg_u2(const float *p) { return __ldcg(reinterpret_cast<const float2 *>(p)); }
+__device__ __forceinline__ float2 ldcg_u2(const bf16 *p)
+{
+    const uint32_t w = __ldcg(reinterpret_cast<const unsigned int *>(p));
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
 // round to nearest (imports, rebase)
 __device__ __forceinline__ void st_u(float *p, float v) { *p = v; }
 __device__ __forceinline__ void st_u(bf16 *p, float v) { *p = __float2bfloat16_rn(v); }
