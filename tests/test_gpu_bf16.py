@@ -60,8 +60,9 @@ def test_bf16_initial_subspace_is_orthonormal(k):
     np.testing.assert_allclose(U.T.astype(np.float64) @ U, np.eye(k), atol=5e-6)
 
 
-def test_bf16_teacher_forced_step():
-    vid, wp = synth.make_workload("rgb640x480_k10", width=160, height=120, n_frames=4)
+@pytest.mark.parametrize("k", [10, 15])  # the register form (k <= 10) and the streaming form
+def test_bf16_teacher_forced_step(k):
+    vid, wp = synth.make_workload("rgb640x480_k10", width=160, height=120, n_frames=4, k=k)
     prm_o = oracle_params(wp)
     st = oracle.initial_state(synth.random_orthonormal(vid.m, vid.k, 21), vid.P)
     for t in range(3):
@@ -86,7 +87,7 @@ def test_bf16_teacher_forced_step():
     res_rel = np.linalg.norm(r_gpu - res.residual) / np.linalg.norm(res.residual)
     cost_rel = abs(stats.cost[0] - res.trace.cost[0]) / res.trace.cost[0]
     mask_frac = float((mask != res.labels).mean())
-    print(f"bf16 step: residual rel {res_rel:.2e}, cost rel {cost_rel:.2e}, mask disagreement {mask_frac:.2e}")
+    print(f"bf16 step k={k}: residual rel {res_rel:.2e}, cost rel {cost_rel:.2e}, mask disagreement {mask_frac:.2e}")
     assert res_rel < STEP_RES_RTOL and cost_rel < STEP_COST_RTOL and mask_frac < STEP_MASK_FRAC
 
 
