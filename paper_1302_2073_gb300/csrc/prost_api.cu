@@ -564,7 +564,7 @@ int prost_get_state(prost_handle *h, void *buf, size_t *len)
     StateHeader hd;
     memset(&hd, 0, sizeof(hd));
     memcpy(hd.magic, "PROSTST1", 8);
-    hd.version = 1;
+    hd.version = 2; // 2: the k-space state without the fields of an earlier design
     hd.header_bytes = sizeof(StateHeader);
     hd.prm = h->prm;
     hd.u_bytes = u_bytes;
@@ -592,7 +592,7 @@ int prost_set_state(prost_handle *h, const void *buf, size_t len)
     if (len < sizeof(StateHeader)) return fail(h, PROST_EINVAL, "state buffer too short");
     StateHeader hd;
     memcpy(&hd, buf, sizeof(hd));
-    if (memcmp(hd.magic, "PROSTST1", 8) != 0 || hd.version != 1 || hd.header_bytes != sizeof(StateHeader))
+    if (memcmp(hd.magic, "PROSTST1", 8) != 0 || hd.version != 2 || hd.header_bytes != sizeof(StateHeader))
         return fail(h, PROST_EINVAL, "not a prost state buffer of this version");
     prost_params a = hd.prm, b = h->prm;
     a.seed = b.seed = 0;

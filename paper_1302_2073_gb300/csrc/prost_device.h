@@ -13,26 +13,17 @@ constexpr int THREADS = 256; // threads per CTA of the Gram and layout kernels
 constexpr int TILE_P = 224;  // pixels per tile of the stored subspace (16-byte multiple for uint8)
 
 // Device-resident k-space state of one stream.  The stored subspace U_st is
-// kept in float32; its orthonormal representative is U = U_st T with
-// T = R^{-1}, U_st^T U_st = R^T R (Cholesky-QR folded into the next frame).
-// All k-space arithmetic is FP64 and is done by one warp of the last CTA of
-// each per-pixel pass; the float copies are what the per-pixel passes read.
+// kept in float32 or bfloat16; its orthonormal representative is U = U_st T
+// with T = R^{-1}, U_st^T U_st = R^T R (Cholesky-QR folded into the next
+// frame).  Every CTA of the frame kernel copies y, T y and the factors at the
+// start of a frame and runs the k-space steps on its own shared-memory copy;
+// the last CTA to finish the frame writes the new state back.
 struct KState {
     double y[KMAX];            // coefficients in the orthonormal basis U
-    double g[KMAX];            // gradient of the cost w.r.t. y at the current iterate
-    double gprev[KMAX];        // gradient at the previous iterate
-    double d[KMAX];            // CG direction
     double R[KMAX * KMAX];     // Cholesky factor of Gram(U_st), row-major upper triangular
     double T[KMAX * KMAX];     // R^{-1}, row-major upper triangular
     float yf[KMAX];            // float(T y): y for the stored rows (residual passes)
-    float ye[KMAX];            // float(y)   (Grassmann/label pass)
-    float gf[KMAX];            // float(g) at the final y
-    float vf[KMAX];            // v = y/|y|  (Eq. svd)
     float Tf[KMAX * KMAX];     // float(T)
-    float cm1;                 // cos(theta) - 1
-    float sn_pin;              // sin(theta) / |pi(eta)|
-    float ynorm;               // |y|
-    int32_t do_update;         // Step 2 not degenerate
     int64_t frame_index;       // i of the next frame (step-size rule)
     int32_t skip;              // current frame rejected (non-finite entry)
     uint32_t err_flags;        // sticky until prost_sync: 1 bad frame, 2 not SPD, 4 timeout

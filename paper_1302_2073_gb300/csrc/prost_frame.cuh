@@ -1,13 +1,14 @@
 // One persistent, cooperative launch per frame of pROST's update
 // (arXiv:1302.2073, Section 3.3) for sm_103a.
 //
-// Every CTA (one per SM, 16 warps) owns a fixed range of the stored
-// subspace's tiles for the residual passes and a fixed range of pixel tiles
-// for the update pass.  Each warp streams its rows with coalesced 8-byte loads
-// straight into registers: the subspace (36.9 MB at 640x480x3, k = 10) stays
-// resident in the 126 MB L2 across the n_cg + 2 passes of a frame, and from
-// L2 many threads with loads in flight deliver about twice the rate of a
-// single-thread bulk-copy ring.
+// Every CTA (one per SM) owns a fixed range of the stored subspace's tiles for
+// the residual passes and a fixed range of pixel tiles for the update pass.
+// In the register form (k <= 10) each warp streams its rows with coalesced
+// loads straight into registers: the subspace (36.9 MB at 640x480x3, k = 10)
+// stays resident in the 126 MB L2 across the n_cg + 2 passes of a frame, and
+// from L2 many threads with loads in flight deliver about twice the rate of a
+// single-thread bulk-copy ring.  The streaming form (k >= 11) stages rows
+// through shared memory with asynchronous copies (prost_stage.cuh).
 //
 // Phases:
 //   residual pass j = 0..n_cg: per row r = x - U y_j, the cost, U^T eta and
@@ -18,8 +19,9 @@
 //     second barrier.
 //   update pass: geodesic update of every row (written back), labels and
 //     weights of Step 3 (max over channels), optional background, Gram of the
-//     new subspace; the last CTA to arrive runs the FP64 Cholesky-QR that is
-//     folded into the next frame and writes the k-space state back.
+//     new subspace; the last CTA to arrive factors that Gram (Cholesky-QR to
+//     FP64 accuracy, folded into the next frame) and writes the k-space state
+//     back.
 //
 // Every wait is bounded (about one second of SM clock): a grid barrier that
 // does not complete sets a global abort flag and PROST_ETIMEOUT in the state
