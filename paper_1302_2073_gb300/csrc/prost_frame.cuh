@@ -528,11 +528,126 @@ __device__ bool cholesky_rl(double *sR, double *sT, double *sW, double *inv)
 // Scratch of the end-of-frame re-orthonormalisation (last CTA).
 template <int K> struct ReorthScratch {
     double R[K * K], T[K * K], W[K * K], Told[K * K], ty[K];
-    double inv[K];
-    float Xh[K * K], Xl[K * K], X2[K * K];
+    double D1[K * K], D2[K * K];
+    float Xh[K * K], Xl[K * K], X2[K * K], inv32[K];
     float emax;
     int ok;
 };
+
+// Cholesky-QR factors to FP64 accuracy for a Gram matrix away from the
+// identity (G in rs.W, full symmetric FP64), by the NT threads of the CTA:
+//   an FP32 right-looking Cholesky G ~ R0^T R0 and T0 = R0^{-1} (FP32);
+//   E = T0^T G T0 - I in FP64 (about 1e-7 whatever G is: the FP32 backward error);
+//   X upper with (I + X)^T (I + X) = I + E: X = Phi(E - X^T X), two sweeps
+//     from X = 0 (error |E|^3), Phi taking the upper triangle, diagonal halved;
+//   T = T0 (I + X)^{-1} = T0 (I - X + X^2) (error |E|^3), so T^T G T = I;
+//   R = T^T G (= R^{-T} R^T R), the upper triangle.
+// Six triangular FP64 products with chains of at most k, in place of the
+// k-step pivot sequence of FP64 square roots.  Returns false (R = T = I) when
+// the FP32 factorisation finds G not positive definite.
+template <int K, int NT>
+__device__ bool cholesky_refined(ReorthScratch<K> &rs)
+{
+    static_assert(K * K <= NT && K <= 32, "one entry per thread, a row per warp");
+    constexpr int KK = K * K;
+    const int t = threadIdx.x;
+    const bool el = t < KK;
+    const int i = t / K, l = t - (t / K) * K;
+    float *W32 = rs.Xh, *R0 = rs.Xl, *T0 = rs.X2, *inv = rs.inv32;
+    if (el) {
+        W32[t] = (float)rs.W[t];
+        R0[t] = 0.f;
+    }
+    cons_sync<NT>();
+    bool ok = true;
+#pragma unroll 1
+    for (int a = 0; a < K; ++a) {
+        const float d = W32[a * K + a]; // the same value in every thread
+        if (!(d > 0.f)) {
+            ok = false;
+            break;
+        }
+        if (t < 32) {
+            float ri = rsqrtf(d);
+            ri = ri * fmaf(-0.5f * d * ri, ri, 1.5f);
+            if (t == 0) inv[a] = ri;
+            if (t >= a && t < K) R0[a * K + t] = t == a ? d * ri : W32[a * K + t] * ri;
+        }
+        cons_sync<NT>();
+        if (el && i > a && l >= i) W32[t] = fmaf(-R0[a * K + i], R0[a * K + l], W32[t]);
+        cons_sync<NT>();
+    }
+    if (!ok) {
+        if (el) rs.R[t] = rs.T[t] = i == l ? 1.0 : 0.0;
+        cons_sync<NT>();
+        return false;
+    }
+    if (el) W32[t] = i == l ? 1.f : 0.f;
+    cons_sync<NT>();
+#pragma unroll 1
+    for (int r = K - 1; r >= 0; --r) {
+        if (t < K) T0[r * K + t] = W32[r * K + t] * inv[r];
+        cons_sync<NT>();
+        if (el && i < r) W32[t] = fmaf(-R0[i * K + r], T0[r * K + l], W32[t]);
+        cons_sync<NT>();
+    }
+    const double *G = rs.W;
+    double *A = rs.D1, *E = rs.D2, *X = rs.T;
+    auto phi = [&](double v) { return l > i ? v : (l == i ? 0.5 * v : 0.0); };
+    // A = G T0
+    if (el) {
+        double s = 0.0;
+        for (int q = 0; q <= l; ++q) s = dfma(G[i * K + q], (double)T0[q * K + l], s);
+        A[t] = s;
+    }
+    cons_sync<NT>();
+    // E = T0^T A - I (upper)
+    if (el) {
+        double s = 0.0;
+        if (i <= l)
+            for (int q = 0; q <= i; ++q) s = dfma((double)T0[q * K + i], A[q * K + l], s);
+        E[t] = i <= l ? s - (i == l ? 1.0 : 0.0) : 0.0;
+        X[t] = phi(E[t]);
+    }
+    cons_sync<NT>();
+    // X = Phi(E - X^T X) with the first sweep's X
+    double xn = 0.0;
+    if (el && i <= l) {
+        double s = 0.0;
+        for (int q = 0; q <= i; ++q) s = dfma(X[q * K + i], X[q * K + l], s);
+        xn = phi(E[t] - s);
+    }
+    cons_sync<NT>();
+    if (el) X[t] = xn;
+    cons_sync<NT>();
+    // Y = X - X^2 (upper), into A
+    if (el) {
+        double s = 0.0;
+        if (i <= l)
+            for (int q = i; q <= l; ++q) s = dfma(X[i * K + q], X[q * K + l], s);
+        A[t] = X[t] - s;
+    }
+    cons_sync<NT>();
+    // T = T0 - T0 Y (upper), into E
+    if (el) {
+        double s = 0.0;
+        if (i <= l)
+            for (int q = i; q <= l; ++q) s = dfma((double)T0[i * K + q], A[q * K + l], s);
+        E[t] = i <= l ? (double)T0[t] - s : 0.0;
+    }
+    cons_sync<NT>();
+    if (el) rs.T[t] = E[t];
+    cons_sync<NT>();
+    // R = T^T G (upper)
+    if (el) {
+        double s = 0.0;
+        if (i <= l)
+            for (int q = 0; q <= i; ++q) s = dfma(rs.T[q * K + i], G[q * K + l], s);
+        rs.R[t] = i <= l ? s : 0.0;
+    }
+    cons_sync<NT>();
+    return true;
+}
 
 // End of frame, all NT threads of the last CTA: the Cholesky-QR factors of the
 // new stored rows from their Gram matrix G (packed upper, FP32 sums) to FP64
@@ -552,7 +667,7 @@ template <int K> struct ReorthScratch {
 // summed into FP64, which gives R and T to FP64 accuracy without long FP64
 // dependency chains (GB300's FP64 pipe has a long latency).  Gram matrices
 // farther from I (bfloat16 stored rows, whose rounding moves the Gram away
-// from I) take the right-looking FP64 factorisation.
+// from I) take an FP32 factorisation refined in FP64 (cholesky_refined).
 template <int K, int NT>
 __device__ void end_frame(const SKState<K> &sk, KState *ks, const float *G, float n_fg, ReorthScratch<K> &rs)
 {
@@ -612,7 +727,7 @@ __device__ void end_frame(const SKState<K> &sk, KState *ks, const float *G, floa
         }
         if (t == 0) rs.ok = 1;
     } else {
-        const bool ok = cholesky_rl<K, NT>(rs.R, rs.T, rs.W, rs.inv);
+        const bool ok = cholesky_refined<K, NT>(rs);
         if (t == 0) rs.ok = ok ? 1 : 0;
     }
     cons_sync<NT>();
