@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0,
                     help="budget of the oracle CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--window-only", action="store_true",
+                    help="run only the windowed cost study (320x240, n = 64, k = 10) and print its JSON")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the bfloat16 against float32 storage study")
     return ap.parse_args()
@@ -639,8 +641,19 @@ def run_ours(args, dist):
     return 0
 
 
+def run_window_only():
+    import torch
+    import paper_1302_2073_gb300 as pg
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    print(json.dumps({"window_320x240_n64_k10": window_study(torch, pg, dev)}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.window_only:
+        return run_window_only()
     dist = Dist()
     if args.impl == "reference":
         return run_reference(args, dist)
