@@ -528,7 +528,7 @@ __device__ bool cholesky_rl(double *sR, double *sT, double *sW, double *inv)
 // Scratch of the end-of-frame re-orthonormalisation (last CTA).
 template <int K> struct ReorthScratch {
     double R[K * K], T[K * K], W[K * K], Told[K * K], ty[K];
-    double D1[K * K], D2[K * K];
+    double D1[K * K], D2[K * K], inv[K];
     float Xh[K * K], Xl[K * K], X2[K * K], inv32[K];
     float emax;
     int ok;
@@ -543,8 +543,11 @@ template <int K> struct ReorthScratch {
 //   T = T0 (I + X)^{-1} = T0 (I - X + X^2) (error |E|^3), so T^T G T = I;
 //   R = T^T G (= R^{-T} R^T R), the upper triangle.
 // Six triangular FP64 products with chains of at most k, in place of the
-// k-step pivot sequence of FP64 square roots.  Returns false (R = T = I) when
-// the FP32 factorisation finds G not positive definite.
+// k-step pivot sequence of FP64 square roots.  The refinement needs |E| small
+// (it is about 1e-7 for the Grams that arise here, within about 1e-3 of I);
+// when max |E| exceeds 1e-4 (an ill-conditioned G) the right-looking FP64
+// Cholesky takes over.  Returns false (R = T = I) when G is not positive
+// definite.
 template <int K, int NT>
 __device__ bool cholesky_refined(ReorthScratch<K> &rs)
 {
@@ -577,11 +580,7 @@ __device__ bool cholesky_refined(ReorthScratch<K> &rs)
         if (el && i > a && l >= i) W32[t] = fmaf(-R0[a * K + i], R0[a * K + l], W32[t]);
         cons_sync<NT>();
     }
-    if (!ok) {
-        if (el) rs.R[t] = rs.T[t] = i == l ? 1.0 : 0.0;
-        cons_sync<NT>();
-        return false;
-    }
+    if (!ok) return cholesky_rl<K, NT>(rs.R, rs.T, rs.W, rs.inv);
     if (el) W32[t] = i == l ? 1.f : 0.f;
     cons_sync<NT>();
 #pragma unroll 1
@@ -602,14 +601,20 @@ __device__ bool cholesky_refined(ReorthScratch<K> &rs)
     }
     cons_sync<NT>();
     // E = T0^T A - I (upper)
+    if (t == 0) rs.emax = 0.f;
+    cons_sync<NT>();
     if (el) {
         double s = 0.0;
         if (i <= l)
             for (int q = 0; q <= i; ++q) s = dfma((double)T0[q * K + i], A[q * K + l], s);
         E[t] = i <= l ? s - (i == l ? 1.0 : 0.0) : 0.0;
         X[t] = phi(E[t]);
+        // the bit patterns of non-negative floats order like the floats
+        const float ae = fabsf((float)E[t]);
+        if (ae > 0.f) atomicMax(reinterpret_cast<int *>(&rs.emax), __float_as_int(ae));
     }
     cons_sync<NT>();
+    if (!(rs.emax <= 1e-4f)) return cholesky_rl<K, NT>(rs.R, rs.T, rs.W, rs.inv); // also NaN
     // X = Phi(E - X^T X) with the first sweep's X
     double xn = 0.0;
     if (el && i <= l) {
