@@ -36,11 +36,22 @@ def test_resample_identity_and_mass():
     np.testing.assert_allclose(pp.resample_area(f, 23, 17), f, rtol=1e-13)
     out = pp.resample_area(f, 10, 6)
     np.testing.assert_allclose(out.sum() * (17 / 6) * (23 / 10), f.sum(), rtol=1e-12)
+    # a square frame to a non-square size: each axis takes its own operator
+    g = rng.random((1, 12, 12))
+    out = pp.resample_area(g, 4, 3)
+    assert out.shape == (1, 3, 4)
+    np.testing.assert_allclose(out, g.reshape(1, 3, 4, 4, 3).mean(axis=(2, 4)), rtol=1e-13)
 
 
-def test_running_norm_matches_the_closed_forms_and_freezes():
+@pytest.mark.parametrize("signed", [False, True])
+def test_running_norm_matches_the_closed_forms_and_freezes(signed):
+    # unsigned intensities, and signed float frames (a pre-subtracted input),
+    # where a sum of magnitudes instead of values would show
     rng = np.random.default_rng(2)
-    frames = rng.integers(0, 256, size=(7, 2, 5, 6)).astype(np.float64)
+    if signed:
+        frames = rng.standard_normal((7, 2, 5, 6)) - 0.3
+    else:
+        frames = rng.integers(0, 256, size=(7, 2, 5, 6)).astype(np.float64)
     rn = pp.RunningNorm(frames.shape[1:], i_init=4)
     for t in range(4):
         out = rn.apply(frames[t])
@@ -56,6 +67,18 @@ def test_running_norm_matches_the_closed_forms_and_freezes():
         np.testing.assert_array_equal(rn.mean, m4)
         assert rn.std() == s4
         np.testing.assert_allclose(out, (frames[t] - m4) / s4, rtol=1e-13)
+
+
+def test_running_norm_undefined_deviation_is_one():
+    # one entry seen, or all entries equal: no sample deviation, divide by 1
+    one = pp.RunningNorm((1, 1, 1), i_init=3)
+    np.testing.assert_allclose(one.apply(np.full((1, 1, 1), 7.0)), 0.0)
+    assert one.std() == 1.0
+    assert one.apply(np.full((1, 1, 1), 9.0))[0, 0, 0] == pytest.approx((9.0 - 8.0) / np.sqrt(2.0), rel=1e-13)
+    flat = pp.RunningNorm((2, 3, 4), i_init=2)
+    out = flat.apply(np.full((2, 3, 4), 5.0))
+    assert flat.std() == 1.0
+    np.testing.assert_array_equal(out, 0.0)
 
 
 def test_median_against_scipy_and_hand_cases():
