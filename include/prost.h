@@ -294,6 +294,19 @@ int prost_batch_tune(prost_batch *b, const void *const *frames, int32_t ticks, f
 /* The plan in use: CTAs per stream (n values), kernel groups, alpha, graph. */
 int prost_batch_plan(prost_batch *b, int32_t *ctas_per_stream, int32_t *n_groups, float *alpha,
                      int32_t *graph);
+/* The split of one kernel group's CTAs between its n streams that the batch
+ * plans with (host only: no device call, no state).  weight[i] > 0 is stream
+ * i's weight (the batch uses rows^alpha), cap[i] >= 1 the most CTAs it can use
+ * (one per pixel tile).  Writes ctas[i] (n values, caller-owned) with
+ *   ctas[i] = clamp(floor(budget * weight[i] / sum(weight)), 1, cap[i]),
+ * then hands the CTAs left over one at a time to the stream with the largest
+ * remaining fractional share that is under its cap (the lowest index on a
+ * tie); where the minimum of one CTA each overshoots the budget, the stream
+ * with the most CTAs (the lowest index on a tie) gives one back at a time.
+ * So sum(ctas) = min(budget, sum(cap)).  Errors: PROST_EINVAL when
+ * n < 1, budget < n, a pointer is NULL, a weight is not a positive finite
+ * number or a cap is below 1 (ctas unwritten). */
+int prost_batch_split(int32_t budget, int32_t n, const double *weight, const int32_t *cap, int32_t *ctas);
 const char *prost_batch_last_error(const prost_batch *b);
 void prost_batch_destroy(prost_batch *b);
 

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -689,6 +690,49 @@ int occupancy_ctas(prost_handle *h, const KernelOps *ops, int fdt)
 
 } // namespace
 
+extern "C" int prost_batch_split(int32_t budget, int32_t n, const double *weight, const int32_t *cap,
+                                 int32_t *ctas)
+{
+    if (n < 1 || budget < n || !weight || !cap || !ctas) return PROST_EINVAL;
+    double wsum = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (!(weight[i] > 0.0) || !std::isfinite(weight[i]) || cap[i] < 1) return PROST_EINVAL;
+        wsum += weight[i];
+    }
+    if (!std::isfinite(wsum)) return PROST_EINVAL;
+    std::vector<double> frac(n);
+    int64_t used = 0;
+    for (int i = 0; i < n; ++i) {
+        const double share = budget * weight[i] / wsum;
+        int c = (int)floor(share);
+        c = c < 1 ? 1 : c;
+        if (c > cap[i]) c = cap[i];
+        ctas[i] = c;
+        frac[i] = share - floor(share);
+        used += c;
+    }
+    // hand out what is left, largest fractional part first (lowest index on a
+    // tie), within the caps
+    while (used < budget) {
+        int best = -1;
+        for (int i = 0; i < n; ++i)
+            if (ctas[i] < cap[i] && (best < 0 || frac[i] > frac[best])) best = i;
+        if (best < 0) break;
+        ctas[best] += 1;
+        frac[best] -= 1.0;
+        used += 1;
+    }
+    // over budget (the minimum of one CTA each): take from the largest
+    while (used > budget) {
+        int big = 0;
+        for (int i = 1; i < n; ++i)
+            if (ctas[i] > ctas[big]) big = i;
+        ctas[big] -= 1;
+        used -= 1;
+    }
+    return PROST_OK;
+}
+
 struct prost_batch {
     std::vector<prost_handle *> h;
     std::vector<int> order;     // table slot -> stream index (grouped)
@@ -726,9 +770,8 @@ int bfail(prost_batch *b, int code, const std::string &why)
                          std::string(#call) + ": " + cudaGetErrorString(e_));                 \
     } while (0)
 
-// Split each group's CTA budget between its streams: shares proportional to
-// rows^alpha, at least one CTA and at most one per pixel tile for a stream,
-// remainders to the largest fractional parts.
+// Split each group's CTA budget between its streams (prost_batch_split), in
+// proportion to rows^alpha, and upload the CTA -> stream map of its launch.
 int plan_ctas(prost_batch *b)
 {
     for (BatchGroup &g : b->groups) {
@@ -736,45 +779,16 @@ int plan_ctas(prost_batch *b)
         const int budget = occupancy_ctas(h0, g.ops, g.fdt);
         if (budget < g.count) return bfail(b, PROST_EINVAL, "more streams in a group than resident CTAs");
         std::vector<double> w(g.count);
-        double wsum = 0.0;
+        std::vector<int32_t> cap(g.count), n(g.count);
         for (int i = 0; i < g.count; ++i) {
             prost_handle *h = b->h[b->order[g.first + i]];
             w[i] = pow((double)h->dp.C * (double)h->dp.P, (double)b->alpha);
-            wsum += w[i];
+            cap[i] = h->dp.npt;
         }
-        std::vector<int> n(g.count);
-        std::vector<double> frac(g.count);
+        if (prost_batch_split(budget, g.count, w.data(), cap.data(), n.data()) != PROST_OK)
+            return bfail(b, PROST_EINVAL, "CTA split");
         int used = 0;
-        for (int i = 0; i < g.count; ++i) {
-            prost_handle *h = b->h[b->order[g.first + i]];
-            const double share = budget * w[i] / wsum;
-            int c = (int)floor(share);
-            c = c < 1 ? 1 : c;
-            if (c > h->dp.npt) c = h->dp.npt;
-            n[i] = c;
-            frac[i] = share - floor(share);
-            used += c;
-        }
-        // hand out what is left, largest fractional part first, within the caps
-        while (used < budget) {
-            int best = -1;
-            for (int i = 0; i < g.count; ++i) {
-                prost_handle *h = b->h[b->order[g.first + i]];
-                if (n[i] < h->dp.npt && (best < 0 || frac[i] > frac[best])) best = i;
-            }
-            if (best < 0) break;
-            n[best] += 1;
-            frac[best] -= 1.0;
-            used += 1;
-        }
-        // over budget (the minimum of one CTA each): take from the largest
-        while (used > budget) {
-            int big = 0;
-            for (int i = 1; i < g.count; ++i)
-                if (n[i] > n[big]) big = i;
-            n[big] -= 1;
-            used -= 1;
-        }
+        for (int i = 0; i < g.count; ++i) used += n[i];
         std::vector<int2> map;
         map.reserve(used);
         for (int i = 0; i < g.count; ++i) {

@@ -100,6 +100,7 @@ def lib():
         L.prost_batch_set_graph.argtypes = [vp, C.c_int]
         L.prost_batch_tune.argtypes = [vp, P(vp), C.c_int32, P(C.c_float)]
         L.prost_batch_plan.argtypes = [vp, P(C.c_int32), P(C.c_int32), P(C.c_float), P(C.c_int32)]
+        L.prost_batch_split.argtypes = [C.c_int32, C.c_int32, P(C.c_double), P(C.c_int32), P(C.c_int32)]
         L.prost_batch_last_error.argtypes = [vp]
         L.prost_batch_last_error.restype = C.c_char_p
         L.prost_batch_destroy.argtypes = [vp]
@@ -357,6 +358,21 @@ def prost_batch_plan(b, n):
     al = C.c_float(0.0)
     _check_batch(lib().prost_batch_plan(b, ctas, C.byref(ng), C.byref(al), C.byref(gr)), b)
     return list(ctas), ng.value, al.value, bool(gr.value)
+
+
+def prost_batch_split(budget, weights, caps):
+    """The batch's split of `budget` CTAs between streams of these weights and
+    caps (host only); returns the CTAs per stream."""
+    n = len(weights)
+    if len(caps) != n:
+        raise ValueError("weights and caps differ in length")
+    w = (C.c_double * max(n, 1))(*[float(x) for x in weights])
+    cp = (C.c_int32 * max(n, 1))(*[int(x) for x in caps])
+    out = (C.c_int32 * max(n, 1))()
+    rc = lib().prost_batch_split(int(budget), n, w, cp, out)
+    if rc < 0:
+        raise ProstError(rc, prost_strerror(rc))
+    return list(out)[:n]
 
 
 def prost_batch_last_error(b=None):
