@@ -154,12 +154,13 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def profiled_traffic():
-    """DRAM bytes per launch of the frame kernel from the committed ncu
-    summary, if the kernel source is unchanged since the capture (else None)."""
+def profiled_value(key="dram_bytes_per_launch_full_size", profile=None, kernel_src=None):
+    """A figure of the committed ncu summary of the frame kernel (DRAM or L2
+    bytes per launch, the L2 peak from ncu's counters), if the kernel source
+    is unchanged since the capture (else None)."""
     try:
-        text = open(PROFILE).read()
-        src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+        text = open(profile or PROFILE).read()
+        src_hash = hashlib.sha256(open(kernel_src or KERNEL_SRC, "rb").read()).hexdigest()[:16]
     except OSError:
         return None
     vals = {}
@@ -170,9 +171,36 @@ def profiled_traffic():
     if vals.get("kernel_source_sha256_16") != src_hash:
         return None
     try:
-        return float(vals["dram_bytes_per_launch_full_size"])
+        return float(vals[key])
     except (KeyError, ValueError):
         return None
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the frame kernel (ncu), or None."""
+    return profiled_value("dram_bytes_per_launch_full_size")
+
+
+def is_profiled_case(args, k):
+    """The committed summary covers the default workload's kernel only: float32
+    storage at the workload's own k."""
+    import synth
+    return args.workload == WORKLOAD and args.u_dtype == "f32" and k == synth.WORKLOADS[WORKLOAD]["video"]["k"]
+
+
+def l2_roofline(achieved, profiled):
+    """The same achieved rate against the L2 peak that ncu's own counters give
+    (slices x sectors per cycle x 32 B x L2 clock), with the L2 bytes per
+    launch of the capture; None where no capture of this kernel and workload
+    is committed."""
+    if not profiled:
+        return None
+    peak = profiled_value("l2_peak_gbs_ncu")
+    if not peak:
+        return None
+    return {"bound": "l2", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": profiled_value("l2_bytes_per_launch_full_size"),
+            "peak_source": "derived from ncu: L2 slices x lts__t_sectors peak_sustained x 32 B x L2 clock"}
 
 
 # ---- the oracle on the host cores --------------------------------------------
@@ -602,6 +630,7 @@ def run_ours(args, dist):
     frame_bytes = algorithmic_bytes(m, P, k, n_cg, sx, 2 if args.u_dtype == "bf16" else 4)
     peak, peak_src = measured_peak_hbm()
     launch_ms = float(np.mean(step_ms))
+    profiled = is_profiled_case(args, k)
     achieved = frame_bytes / (launch_ms * 1e-3) / 1e9
     phase_ms = kern.mean(axis=0)
     share = {"cg_passes": float(phase_ms[:n_cg].sum() / phase_ms.sum()),
@@ -613,10 +642,11 @@ def run_ours(args, dist):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": _config(args, vid, wp, K),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "traffic": profiled_traffic(),
+                        "frac": achieved / peak, "traffic": profiled_traffic() if profiled else None,
                         "kernel": f"k_frame<{k},{vid.dtype}> (whole frame, one launch)",
                         "bytes_per_launch": frame_bytes, "launch_ms": launch_ms,
                         "peak_source": f"{peak_src} hbm_gbs"},
+           "roofline_l2": l2_roofline(achieved, profiled),
            "frame": {"pixels_per_s": value * P,
                      "phase_ms": [round(float(v), 5) for v in phase_ms],
                      "phase_share": share},

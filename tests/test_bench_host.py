@@ -1,0 +1,66 @@
+"""Host helpers of bench.py that need no GPU: the figures it takes from a
+committed ncu summary only while the kernel source is the one captured, and
+only for the kernel and workload captured."""
+
+import hashlib
+import os
+import sys
+import types
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _summary(tmp_path, src_text, sha=None):
+    src = tmp_path / "kernel.cuh"
+    src.write_text(src_text)
+    sha = sha or hashlib.sha256(src_text.encode()).hexdigest()[:16]
+    prof = tmp_path / "summary.md"
+    prof.write_text("# summary\n\n"
+                    f"- kernel_source_sha256_16: `{sha}`\n"
+                    "- dram_bytes_per_launch_full_size: 1234\n"
+                    "- l2_peak_gbs_ncu: 36146\n")
+    return str(prof), str(src)
+
+
+def test_profiled_value_needs_the_captured_source(tmp_path):
+    prof, src = _summary(tmp_path, "kernel v1")
+    assert bench.profiled_value("dram_bytes_per_launch_full_size", prof, src) == 1234.0
+    assert bench.profiled_value("l2_peak_gbs_ncu", prof, src) == 36146.0
+    assert bench.profiled_value("no_such_key", prof, src) is None
+    with open(src, "a") as f:
+        f.write(" changed")          # the kernel changed since the capture
+    assert bench.profiled_value("dram_bytes_per_launch_full_size", prof, src) is None
+    assert bench.profiled_value("dram_bytes_per_launch_full_size", str(tmp_path / "missing.md"), src) is None
+
+
+def test_committed_summary_matches_the_committed_kernel():
+    # the summary the bench line cites is of the kernel source in the tree
+    assert bench.profiled_traffic() == pytest.approx(38221056.0)
+    assert bench.profiled_value("l2_bytes_per_launch_full_size") == pytest.approx(395984192.0)
+
+
+def test_profiled_case_is_the_default_workload_in_float32_only():
+    A = types.SimpleNamespace
+    assert bench.is_profiled_case(A(workload=bench.WORKLOAD, u_dtype="f32"), 10)
+    assert not bench.is_profiled_case(A(workload=bench.WORKLOAD, u_dtype="bf16"), 10)
+    assert not bench.is_profiled_case(A(workload=bench.WORKLOAD, u_dtype="f32"), 12)
+    assert not bench.is_profiled_case(A(workload="rgb1920x1080_k15", u_dtype="f32"), 15)
+
+
+def test_l2_roofline_arithmetic():
+    r = bench.l2_roofline(2746.0, True)
+    assert r["bound"] == "l2" and r["unit"] == "GB/s"
+    assert r["frac"] == pytest.approx(2746.0 / r["peak"])
+    # slices x sectors/cycle x bytes/sector x L2 clock, from the capture
+    assert r["peak"] == pytest.approx(188 * 3 * 32 * 2.002765, rel=1e-4)
+    assert bench.l2_roofline(2746.0, False) is None
+
+
+def test_algorithmic_bytes_of_the_default_workload():
+    # (n_cg + 2) reads of U, one write, a frame and a label byte per pass, the mask
+    m, P, k, n_cg = 921600, 307200, 10, 5
+    assert bench.algorithmic_bytes(m, P, k, n_cg, 1, 4) == 303820800
