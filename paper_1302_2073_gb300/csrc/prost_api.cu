@@ -252,11 +252,9 @@ int prost_state_bytes(const prost_params *prm, size_t *bytes)
     int rc = check_params(prm, &dp, &why);
     if (rc) return rc;
     if (!bytes) return PROST_EINVAL;
-    const int64_t m = m_of(*prm);
     size_t b = (size_t)prm->k * dp.C * dp.Pp * u_elem_bytes(dp) + (size_t)dp.Pp + sizeof(KState) +
                sizeof(unsigned int) + sizeof(GridBar) + (size_t)4096 * partial_row(prm->k) * sizeof(float) +
                (size_t)dp.C * dp.Pp * frame_elem_bytes(*prm);
-    (void)m;
     *bytes = b;
     return PROST_OK;
 }

@@ -22,3 +22,15 @@ def golden(name):
             if line and not line.startswith("#"):
                 rows.append(line.split())
     return rows
+
+
+@pytest.fixture
+def scratch(request):
+    """A fresh, git-ignored folder inside the tree for one test's files."""
+    import pathlib
+    import shutil
+    d = pathlib.Path(ROOT, "tests", "_scratch", request.node.name.replace("[", "_").replace("]", ""))
+    if d.exists():
+        shutil.rmtree(d)
+    d.mkdir(parents=True)
+    return d

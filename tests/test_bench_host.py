@@ -14,11 +14,11 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def _summary(tmp_path, src_text, sha=None):
-    src = tmp_path / "kernel.cuh"
+def _summary(scratch, src_text, sha=None):
+    src = scratch / "kernel.cuh"
     src.write_text(src_text)
     sha = sha or hashlib.sha256(src_text.encode()).hexdigest()[:16]
-    prof = tmp_path / "summary.md"
+    prof = scratch / "summary.md"
     prof.write_text("# summary\n\n"
                     f"- kernel_source_sha256_16: `{sha}`\n"
                     "- dram_bytes_per_launch_full_size: 1234\n"
@@ -26,15 +26,15 @@ def _summary(tmp_path, src_text, sha=None):
     return str(prof), str(src)
 
 
-def test_profiled_value_needs_the_captured_source(tmp_path):
-    prof, src = _summary(tmp_path, "kernel v1")
+def test_profiled_value_needs_the_captured_source(scratch):
+    prof, src = _summary(scratch, "kernel v1")
     assert bench.profiled_value("dram_bytes_per_launch_full_size", prof, src) == 1234.0
     assert bench.profiled_value("l2_peak_gbs_ncu", prof, src) == 36146.0
     assert bench.profiled_value("no_such_key", prof, src) is None
     with open(src, "a") as f:
         f.write(" changed")          # the kernel changed since the capture
     assert bench.profiled_value("dram_bytes_per_launch_full_size", prof, src) is None
-    assert bench.profiled_value("dram_bytes_per_launch_full_size", str(tmp_path / "missing.md"), src) is None
+    assert bench.profiled_value("dram_bytes_per_launch_full_size", str(scratch / "missing.md"), src) is None
 
 
 def test_committed_summary_matches_the_committed_kernel():
