@@ -361,6 +361,49 @@ def test_frame_step_smoothed_lp_tracks_through_outliers():
     assert np.degrees(np.arccos(np.clip(cos.min(), -1, 1))) < 2.0
 
 
+def test_gray_160x120_stream_finds_the_planted_background_and_foreground():
+    """End to end on the 160x120 gray k = 5 stream (200 frames, paper
+    parameters), against the generator's planted truth rather than the
+    oracle itself.  The background coefficients drift slowly from one start,
+    so one direction of the planted subspace dominates the data: the smallest
+    principal angle to it falls from near 90 degrees to a few, and the part of
+    the noiseless background outside span(U) falls from all of it to a small
+    fraction.  After 50 frames the labels hit no background pixel, and they
+    find the foreground pixels whose value differs from the background by
+    more than delta with room for the noise.  Bars are set from the oracle's
+    own run (2.6 degrees, 0.18, precision 1.0, recall 0.997) with margin."""
+    vid, wp = synth.make_workload("gray160x120_k5", n_frames=200)
+    prm = oracle.params(**wp)
+    st = oracle.initial_state(synth.random_orthonormal(vid.m, vid.k, 5), vid.P)
+
+    def min_angle_deg(U):
+        s = np.linalg.svd(U.T @ vid.U0, compute_uv=False)
+        return math.degrees(math.acos(min(1.0, float(s.max()))))
+
+    def missed(U, t):
+        b = vid.background(t).reshape(-1) - vid.offset
+        return float(np.linalg.norm(b - U @ (U.T @ b)) / np.linalg.norm(b))
+
+    assert min_angle_deg(st.U) > 80.0 and missed(st.U, 0) > 0.99
+    tp = fp = hit = det_total = 0
+    worst_missed = 0.0
+    for t in range(200):
+        f, gt = vid.frame(t)
+        res = oracle.frame_step(prm, st, f, want_residual=False)
+        if t >= 50:
+            worst_missed = max(worst_missed, missed(st.U, t))
+            lab, g = res.labels != 0, gt.reshape(-1)
+            det = g & (np.abs(f.reshape(-1) - vid.background(t).reshape(-1)) >= wp["delta"] + 0.05)
+            tp += int((lab & g).sum())
+            fp += int((lab & ~g).sum())
+            hit += int((lab & det).sum())
+            det_total += int(det.sum())
+    assert min_angle_deg(st.U) < 5.0
+    assert worst_missed < 0.25
+    assert tp / (tp + fp) > 0.99
+    assert det_total > 10000 and hit / det_total > 0.98
+
+
 def test_frame_step_zero_frame_leaves_subspace():
     rng = RNG(18)
     m, k = 48, 3
