@@ -172,6 +172,11 @@ int prost_set_labels(prost_handle *h, const uint8_t *labels, int on_device);
 int prost_set_frame_index(prost_handle *h, int64_t i);
 
 /* Statistics of the last frame (synchronises the stream). */
+/* Statistics of the last frame (the fields of prost_stats above: the cost and
+ * gradient norm at every CG iterate of Step 1, the line steps and PR+
+ * coefficients, sigma, t and theta of Step 2, the foreground count of Step 3,
+ * the orthogonality error before the re-orthonormalisation) into *out (host).
+ * Synchronises the stream.  PROST_EINVAL for NULL arguments. */
 int prost_get_stats(prost_handle *h, prost_stats *out);
 
 /* Checkpoint.  prost_get_state() with buf = NULL stores the needed size in
