@@ -1,0 +1,219 @@
+"""CPU replays of the frame kernel's index plans (no GPU).
+
+The index arithmetic of the CUDA kernels is restated here for whole ranges of
+sizes, and every replay checks that each load and store stays inside its
+buffer with the alignment of its vector width, and that the work partitions
+cover every element exactly once.  The formulas follow prost_frame.cuh
+(FrameTiles, the residual pass's items, the update pass's items,
+reduce_rows), prost_api.cu (the frame grid and the partial-row stride) and
+prost_window.cu (the U-step's reductions); the constants are read from those
+sources, so a change of tile size or reduction shape is replayed too."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1302_2073_gb300", "csrc")
+
+
+def _src(name):
+    with open(os.path.join(CSRC, name)) as f:
+        return f.read()
+
+
+def _const(text, pattern):
+    m = re.search(pattern, text)
+    assert m, pattern
+    return int(m.group(1))
+
+
+DEVICE_H, FRAME_CUH, API_CU, WINDOW_CU = (_src(n) for n in ("prost_device.h", "prost_frame.cuh", "prost_api.cu",
+                                                          "prost_window.cu"))
+TILE_P = _const(DEVICE_H, r"constexpr int TILE_P = (\d+);")
+RW = _const(FRAME_CUH, r"static constexpr int RW = (\d+);")
+RED_ROWS = _const(FRAME_CUH, r"constexpr int RED_ROWS = (\d+);")
+RED_SCR = _const(FRAME_CUH, r"constexpr int RED_SCR = (\d+);")
+WT = _const(WINDOW_CU, r"constexpr int WT = (\d+);")
+KMAXW = _const(WINDOW_CU, r"constexpr int KMAXW = (\d+);")
+IPT = TILE_P // RW
+SMS = 152
+
+# the rules restated below, as they read in the sources
+assert "static constexpr int THREADS = STREAM && sizeof(UT) == 4 ? 256 : 512;" in FRAME_CUH
+assert "static constexpr bool STREAM = K >= 11;" in FRAME_CUH
+assert "return (size_t)k + (size_t)k * (k + 1) / 2 + 3;" in API_CU
+assert "r0 = (int)(NT * b / G);" in FRAME_CUH and "u0 = (int)((long long)prm.npt * b / G);" in FRAME_CUH
+
+
+def threads(k, bf16):
+    return 256 if (k >= 11 and not bf16) else 512
+
+
+def partial_row(k):
+    return k + k * (k + 1) // 2 + 3
+
+
+def npt_of(P):
+    return (P + TILE_P - 1) // TILE_P
+
+
+def frame_grid(P, sms=SMS, occ=1):
+    """The frame kernel's grid: one CTA per SM, at most one per pixel tile."""
+    return max(1, min(occ * sms, npt_of(P)))
+
+
+def frame_tiles(C, npt, G, b):
+    """(r0, nres, u0, nupt) of CTA b: its residual-pass tiles (over all
+    channel planes) and its update-pass pixel tiles."""
+    NT = C * npt
+    r0 = NT * b // G
+    u0 = npt * b // G
+    return r0, NT * (b + 1) // G - r0, u0, npt * (b + 1) // G - u0
+
+
+SHAPES = [(1, 1), (7, 1), (223, 1), (224, 1), (225, 3), (37 * 29, 3), (160 * 120, 1), (160 * 120, 3),
+          (320 * 240, 1), (640 * 480, 3), (1280 * 720, 1), (1920 * 1080, 3)]
+
+
+def _grids(P):
+    npt = npt_of(P)
+    return sorted({g for g in (1, 2, 7, 19, frame_grid(P), npt) if 1 <= g <= npt})
+
+
+@pytest.mark.parametrize("P,C", SHAPES)
+def test_frame_tiles_partition_the_planes(P, C):
+    npt = npt_of(P)
+    for G in _grids(P):
+        res_cover = np.zeros(C * npt, np.int64)
+        upd_cover = np.zeros(npt, np.int64)
+        for b in range(G):
+            r0, nres, u0, nupt = frame_tiles(C, npt, G, b)
+            assert nres >= 1 and nupt >= 1, (P, C, G, b)
+            res_cover[r0:r0 + nres] += 1
+            upd_cover[u0:u0 + nupt] += 1
+        assert (res_cover == 1).all() and (upd_cover == 1).all(), (P, C, G)
+
+
+@pytest.mark.parametrize("P,C", SHAPES)
+@pytest.mark.parametrize("k", [1, 10])
+def test_residual_pass_loads_stay_in_bounds_and_aligned(P, C, k):
+    """Items of the register form: tile ti, pair rp; U pair loads at
+    ti*k*TP + rp*RW + j*TP, the frame's pair (or single) load at c*pitch + p,
+    the labels' pair load at p (the label plane is padded)."""
+    npt = npt_of(P)
+    Pp = npt * TILE_P
+    ti, rp = np.meshgrid(np.arange(C * npt, dtype=np.int64), np.arange(IPT, dtype=np.int64), indexing="ij")
+    ti, rp = ti.ravel(), rp.ravel()
+    c = ti // npt
+    p = (ti - c * npt) * TILE_P + rp * RW
+    nvalid = np.minimum(P - p, RW)
+    # every entry of every plane is read exactly once, padding entries never
+    q = np.concatenate([c * P + p + r for r in range(RW)])
+    valid = np.concatenate([nvalid > r for r in range(RW)])
+    counts = np.bincount(q[valid], minlength=C * P)
+    assert counts.size == C * P and (counts == 1).all()
+    # the subspace: pair loads inside C*npt*k*TP entries, at even offsets
+    for j in (0, k - 1):
+        off = ti * k * TILE_P + rp * RW + j * TILE_P
+        assert off.min() >= 0 and (off + RW - 1).max() < C * npt * k * TILE_P
+        assert (off % RW == 0).all()
+    # the frame, direct (pitch P, only when planes are 16-byte multiples) or staged (pitch Pp)
+    for eb in (1, 4):
+        pitches = [Pp] + ([P] if (P * eb) % 16 == 0 else [])
+        for pitch in pitches:
+            base = c * pitch + p
+            pair = nvalid == RW
+            assert ((base[pair] * eb) % (RW * eb) == 0).all()
+            assert (base[pair] + RW - 1).max(initial=0) < C * pitch
+            one = (nvalid >= 1) & ~pair
+            assert base[one].max(initial=0) < C * pitch
+    # the labels: a pair load at p in a plane of Pp bytes
+    assert (p + RW - 1).max() < Pp and (p % RW == 0).all()
+
+
+@pytest.mark.parametrize("P,C", SHAPES)
+def test_update_pass_touches_every_row_once(P, C):
+    """Items of the update pass: a CTA's pixel tiles, one pixel per item, its
+    channels in turn; the row of pixel p in plane c is written once, labels
+    once per pixel."""
+    k = 3
+    npt = npt_of(P)
+    Pp = npt * TILE_P
+    G = frame_grid(P)
+    row_writes = np.zeros(C * npt * k * TILE_P, np.int64)
+    label_writes = np.zeros(Pp, np.int64)
+    for b in range(G):
+        _, _, u0, nupt = frame_tiles(C, npt, G, b)
+        it = np.arange(nupt * TILE_P, dtype=np.int64)
+        pt = u0 + it // TILE_P
+        r0 = it % TILE_P
+        p = pt * TILE_P + r0
+        for ch in range(C):
+            for j in range(k):
+                np.add.at(row_writes, (ch * npt + pt) * k * TILE_P + r0 + j * TILE_P, 1)
+            frame_off = ch * P + p[p < P]           # frame reads, direct pitch
+            assert frame_off.size == 0 or frame_off.max() < C * P
+        np.add.at(label_writes, p, 1)
+    assert (row_writes == 1).all()
+    assert (label_writes == 1).all()
+
+
+def _reduce_plan(nrows, nv, ncons):
+    """reduce_rows: the groups, the units each thread sums, and the rows each
+    unit reads."""
+    ng = max(-(-nrows // RED_ROWS), ncons // nv)
+    ng = max(1, min(ng, min(nrows, RED_SCR // nv)))
+    nu = ng * nv
+    by_thread = []
+    for t in range(ncons):
+        mine = []
+        if nu <= ncons:
+            if t < nu:
+                mine.append(t)
+        else:
+            u0 = t
+            while u0 < nu:
+                u1 = u0 + ncons
+                mine.append(u0)
+                if u1 < nu:
+                    mine.append(u1)
+                u0 += 2 * ncons
+        by_thread.append(mine)
+    return ng, nu, by_thread
+
+
+def _reduce_cases():
+    cases = set()
+    for k in range(1, 17):
+        for bf16 in (False, True):
+            nt = threads(k, bf16)
+            stride = partial_row(k)
+            for nv in (k + k * (k + 1) // 2 + 3, k + 3, k * (k + 1) // 2 + 1):
+                cases.add((nt, stride, nv))
+    for k in range(1, KMAXW + 1):
+        for nv in (k * k, k * (k + 1) // 2):
+            cases.add((WT, KMAXW * KMAXW, nv))
+    return sorted(cases)
+
+
+@pytest.mark.parametrize("ncons,stride,nv", _reduce_cases())
+def test_reduce_rows_plan_sums_every_value_of_every_row_once(ncons, stride, nv):
+    assert nv <= stride
+    for nrows in (1, 2, 23, 24, 25, 76, 151, 152, 304, 1024):
+        ng, nu, by_thread = _reduce_plan(nrows, nv, ncons)
+        assert nu <= RED_SCR                                  # scratch of the group sums
+        units = [u for mine in by_thread for u in mine]
+        assert sorted(units) == list(range(nu))               # each unit by one thread
+        seen = np.zeros((nrows, nv), np.int64)
+        for u in range(nu):
+            g, c = divmod(u, nv)
+            rows = np.arange(g, nrows, ng)
+            off = rows * stride + c
+            assert off.size == 0 or off.max() < nrows * stride
+            seen[rows, c] += 1
+        assert (seen == 1).all()
+        # the final sums read scr[g*nv + c], g < ng: exactly the units written
+        assert sorted(g * nv + c for c in range(nv) for g in range(ng)) == list(range(nu))
