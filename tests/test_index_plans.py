@@ -5,7 +5,8 @@ sizes, and every replay checks that each load and store stays inside its
 buffer with the alignment of its vector width, and that the work partitions
 cover every element exactly once.  The formulas follow prost_frame.cuh
 (FrameTiles, the residual pass's items, the update pass's items,
-reduce_rows), prost_api.cu (the frame grid and the partial-row stride) and
+reduce_rows), prost_stage.cuh (the streaming form's 16-byte copies of a
+step into its stage), prost_api.cu (the frame grid and the partial-row stride) and
 prost_window.cu (the U-step's reductions); the constants are read from those
 sources, so a change of tile size or reduction shape is replayed too."""
 
@@ -217,3 +218,102 @@ def test_reduce_rows_plan_sums_every_value_of_every_row_once(ncons, stride, nv):
         assert (seen == 1).all()
         # the final sums read scr[g*nv + c], g < ng: exactly the units written
         assert sorted(g * nv + c for c in range(nv) for g in range(ng)) == list(range(nu))
+
+
+# ---- the streaming form's staging plan (prost_stage.cuh) -----------------------
+
+STAGE_CUH = _src("prost_stage.cuh")
+STG_ROWS = _const(STAGE_CUH, r"constexpr int STG_ROWS = (\d+);")
+TC_CS = _const(STAGE_CUH, r"static constexpr int CS = TC \? (\d+) : STG_ROWS;")
+assert "static constexpr int UCOL = TC ? 16 : K;" in STAGE_CUH
+assert "uoff = (lane / S::CPC) * TILE_P + (lane % S::CPC) * RPC;" in STAGE_CUH
+assert "soff = (lane / S::CPC) * S::CS * (int)sizeof(UT) + 16 * (lane % S::CPC);" in STAGE_CUH
+
+
+def stage_cfg(k, fsize, usize):
+    tc = usize == 2
+    cs = TC_CS if tc else STG_ROWS
+    ucol = 16 if tc else k
+    ub = ucol * cs * usize
+    f_off = ub
+    l_off = f_off + STG_ROWS * fsize
+    stage_b = (l_off + STG_ROWS + 127) // 128 * 128
+    cpc = STG_ROWS * usize // 16
+    ncu = k * cpc
+    ncf = STG_ROWS * fsize // 16
+    ncl = STG_ROWS // 16
+    return dict(cs=cs, ub=ub, f_off=f_off, l_off=l_off, stage_b=stage_b, cpc=cpc, ncu=ncu, ncf=ncf, ncl=ncl,
+                nch=ncu + ncf + ncl)
+
+
+def lane_copies(k, fsize, usize, lane):
+    """(kind, stage byte offset, source offset) of every 16-byte copy lane
+    issues for one step: kind 'u' (source in elements from the tile's block at
+    row rs), 'f' (elements from the step's first frame entry), 'l' (bytes
+    from its first label)."""
+    S = stage_cfg(k, fsize, usize)
+    nqu = S["ncu"] // 32
+    tr = (S["nch"] - 32 * nqu + 31) // 32
+    qcol = 32 // S["cpc"]
+    rpc = 16 // usize
+    qb = qcol * S["cs"] * usize
+    uoff = (lane // S["cpc"]) * TILE_P + (lane % S["cpc"]) * rpc
+    soff = (lane // S["cpc"]) * S["cs"] * usize + 16 * (lane % S["cpc"])
+    out = [("u", soff + q * qb, uoff + q * qcol * TILE_P) for q in range(nqu)]
+    for r in range(tr):
+        ch = 32 * (nqu + r) + lane
+        if ch < S["ncu"]:
+            out.append(("u", soff + (nqu + r) * qb, uoff + (nqu + r) * qcol * TILE_P))
+        elif ch < S["ncu"] + S["ncf"]:
+            out.append(("f", S["f_off"] + 16 * (ch - S["ncu"]), (ch - S["ncu"]) * (16 // fsize)))
+        elif ch < S["nch"]:
+            out.append(("l", S["l_off"] + 16 * (ch - S["ncu"] - S["ncf"]), 16 * (ch - S["ncu"] - S["ncf"])))
+    return S, out
+
+
+@pytest.mark.parametrize("k", range(11, 17))
+@pytest.mark.parametrize("fsize,usize", [(1, 4), (4, 4), (1, 2), (4, 2)])
+def test_streaming_stage_copies_cover_the_step_once(k, fsize, usize):
+    copies = [c for lane in range(32) for c in lane_copies(k, fsize, usize, lane)[1]]
+    S = lane_copies(k, fsize, usize, 0)[0]
+    dst = [d for _, d, _ in copies]
+    assert len(dst) == len(set(dst))                                   # no stage byte written twice
+    assert all(d % 16 == 0 and 0 <= d and d + 16 <= S["stage_b"] for d in dst)
+    assert S["stage_b"] % 128 == 0
+    # the subspace block: column j, row part q of the step at stage j*CS*s + 16 q,
+    # read from element j*TP + q*(16/s) of the tile's block, every (j, q) once
+    u = sorted((d, s) for kind, d, s in copies if kind == "u")
+    want = sorted((j * S["cs"] * usize + 16 * q, j * TILE_P + q * (16 // usize))
+                  for j in range(k) for q in range(S["cpc"]))
+    assert u == want
+    assert all(d + 16 <= S["ub"] for d, _ in u)
+    # bfloat16: columns k .. 15 of the block are zeroed once per stage and no
+    # copy lands there
+    assert all(d + 16 <= k * S["cs"] * usize for d, _ in u)
+    # the sources are 16-byte aligned: tile bases (k*TP elements apart) and
+    # step starts (STG_ROWS rows) are, and so is every chunk offset
+    assert (k * TILE_P * usize) % 16 == 0 and (STG_ROWS * usize) % 16 == 0
+    assert all((s * usize) % 16 == 0 for _, s in u)
+    # the frame entries and labels of the step, each slot once, in order
+    f = sorted((d, s) for kind, d, s in copies if kind == "f")
+    assert f == [(S["f_off"] + 16 * i, i * (16 // fsize)) for i in range(S["ncf"])]
+    lab = sorted((d, s) for kind, d, s in copies if kind == "l")
+    assert lab == [(S["l_off"] + 16 * i, 16 * i) for i in range(S["ncl"])]
+    assert S["l_off"] + STG_ROWS <= S["stage_b"] and S["l_off"] % 16 == 0
+
+
+@pytest.mark.parametrize("P", [37 * 29, 224, 1000, 1920 * 1080])
+@pytest.mark.parametrize("fsize", [1, 4])
+def test_streaming_frame_chunks_never_cross_the_plane_end(P, fsize):
+    """A frame chunk is copied when its first entry is inside the plane
+    (rs + offset < valid rows), else zero-filled.  On the direct pitch (planes
+    are 16-byte multiples) a chunk that starts inside therefore ends inside;
+    on the staged pitch it ends inside the padded plane."""
+    per = 16 // fsize
+    npt = npt_of(P)
+    Pp = npt * TILE_P
+    starts = np.arange(0, Pp, per, dtype=np.int64)       # chunk starts: tile, step and slot multiples
+    inside = starts < P
+    assert (starts[inside] + per <= Pp).all()
+    if (P * fsize) % 16 == 0:
+        assert (starts[inside] + per <= P).all()
