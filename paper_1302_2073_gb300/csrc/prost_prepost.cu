@@ -29,19 +29,27 @@ constexpr int PB_MAX = 1024;    // blocks of the resampling launch
 
 struct PreGeom {
     int w_in, h_in, C, w_out, h_out;
-    float sx, sy;               // input pixels per output pixel
     int64_t n_out;              // C * h_out * w_out
     int64_t in_pitch;           // entries between input planes
 };
 
-// area weights along one axis: output index i covers [i s, (i + 1) s); input
-// pixel q gets |[q, q + 1) ∩ that interval| / s
-__device__ __forceinline__ void footprint(int i, float s, int n_in, int &q0, int &q1, float &lo, float &hi)
+// Area weights along one axis, in exact integers.  With s = n_in / n_out,
+// output index i covers [i s, (i + 1) s) and input pixel q gets
+// |[q, q + 1) ∩ that interval| / s.  In units of 1 / n_out the interval is
+// [i n_in, (i + 1) n_in) and the pixel [q n_out, (q + 1) n_out), so the
+// overlap is an integer ov and the weight is ov / n_in (a rounded float s
+// would put the ends of the interval off by about n_in 2^-24).
+__device__ __forceinline__ void footprint(int i, int n_in, int n_out, int &q0, int &q1, int64_t &lo, int64_t &hi)
 {
-    lo = i * s;
-    hi = (i + 1) * s;
-    q0 = (int)floorf(lo);
-    q1 = min(n_in, (int)ceilf(hi));
+    lo = (int64_t)i * n_in;
+    hi = lo + n_in;
+    q0 = (int)(lo / n_out);
+    q1 = (int)min((int64_t)n_in, (hi + n_out - 1) / n_out);
+}
+
+__device__ __forceinline__ int64_t overlap(int q, int n_out, int64_t lo, int64_t hi)
+{
+    return min(hi, (int64_t)(q + 1) * n_out) - max(lo, (int64_t)q * n_out);
 }
 
 template <typename FT>
@@ -52,22 +60,22 @@ __device__ __forceinline__ float resample_at(const FT *in, const PreGeom &g, int
     const int r = (int)(e - (int64_t)c * per);
     const int i = r / g.w_out, j = r - (r / g.w_out) * g.w_out;
     int y0, y1, x0, x1;
-    float ylo, yhi, xlo, xhi;
-    footprint(i, g.sy, g.h_in, y0, y1, ylo, yhi);
-    footprint(j, g.sx, g.w_in, x0, x1, xlo, xhi);
+    int64_t ylo, yhi, xlo, xhi;
+    footprint(i, g.h_in, g.h_out, y0, y1, ylo, yhi);
+    footprint(j, g.w_in, g.w_out, x0, x1, xlo, xhi);
     const FT *plane = in + (int64_t)c * g.in_pitch;
     float acc = 0.f;
     for (int y = y0; y < y1; ++y) {
-        const float wy = fminf(yhi, (float)(y + 1)) - fmaxf(ylo, (float)y);
-        if (wy <= 0.f) continue;
+        const int64_t oy = overlap(y, g.h_out, ylo, yhi);
+        if (oy <= 0) continue;
         float row = 0.f;
         for (int x = x0; x < x1; ++x) {
-            const float wx = fminf(xhi, (float)(x + 1)) - fmaxf(xlo, (float)x);
-            if (wx > 0.f) row = fmaf(wx, (float)plane[(int64_t)y * g.w_in + x], row);
+            const int64_t ox = overlap(x, g.w_out, xlo, xhi);
+            if (ox > 0) row = fmaf((float)ox, (float)plane[(int64_t)y * g.w_in + x], row);
         }
-        acc = fmaf(wy, row, acc);
+        acc = fmaf((float)oy, row, acc);
     }
-    return acc / (g.sx * g.sy);
+    return acc / ((float)g.h_in * (float)g.w_in);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v)
@@ -253,8 +261,6 @@ extern "C" int prost_pre_init(int32_t w_in, int32_t h_in, int32_t channels, int3
     p->g.C = channels;
     p->g.w_out = w_out;
     p->g.h_out = h_out;
-    p->g.sx = (float)w_in / (float)w_out;
-    p->g.sy = (float)h_in / (float)h_out;
     p->g.n_out = (int64_t)channels * h_out * w_out;
     p->g.in_pitch = (int64_t)w_in * h_in;
     p->fdt = frame_dtype;

@@ -30,6 +30,7 @@ def _need_gpu():
 @pytest.mark.parametrize("w_in,h_in,C,w_out,h_out,dtype", [
     (640, 480, 3, 160, 120, "u8"),   # the paper's resampling of a 640x480 stream
     (100, 75, 3, 37, 29, "u8"),      # non-integer ratios, ragged footprints
+    (1366, 768, 3, 160, 120, "u8"),  # large non-integer ratios: exact integer footprints
     (33, 21, 1, 40, 30, "f32"),      # upsampling, float frames
 ])
 def test_pre_processing_through_and_after_the_phase(w_in, h_in, C, w_out, h_out, dtype):

@@ -317,3 +317,47 @@ def test_streaming_frame_chunks_never_cross_the_plane_end(P, fsize):
     assert (starts[inside] + per <= Pp).all()
     if (P * fsize) % 16 == 0:
         assert (starts[inside] + per <= P).all()
+
+
+# ---- the pre-processing resampler's footprints (prost_prepost.cu) --------------
+
+PREPOST_CU = _src("prost_prepost.cu")
+assert "lo = (int64_t)i * n_in;" in PREPOST_CU and "hi = lo + n_in;" in PREPOST_CU
+assert "q0 = (int)(lo / n_out);" in PREPOST_CU
+assert "q1 = (int)min((int64_t)n_in, (hi + n_out - 1) / n_out);" in PREPOST_CU
+assert "return min(hi, (int64_t)(q + 1) * n_out) - max(lo, (int64_t)q * n_out);" in PREPOST_CU
+
+
+def _pairs():
+    rng = np.random.default_rng(0)
+    fixed = [(640, 160), (480, 120), (1920, 160), (1080, 120), (1366, 160), (768, 120), (100, 37), (75, 29),
+             (33, 40), (21, 30), (7, 3), (3, 8), (1, 5), (5, 1), (4096, 4095), (4095, 4096), (1, 1)]
+    rand = [tuple(int(v) for v in rng.integers(1, 4097, size=2)) for _ in range(40)]
+    return fixed + rand
+
+
+@pytest.mark.parametrize("n_in,n_out", _pairs())
+def test_resampling_footprints_stay_in_the_input_and_cover_it_exactly(n_in, n_out):
+    """Output i reads input rows [floor(i n_in / n_out), min(n_in, ceil((i + 1)
+    n_in / n_out))) with integer overlaps in units of 1 / n_out: never outside
+    the input, never empty, every overlap positive, each output's overlaps
+    adding up to n_in (weights summing to exactly one) and each input pixel's
+    to n_out (its whole area used once)."""
+    i = np.arange(n_out, dtype=np.int64)
+    lo = i * n_in
+    hi = lo + n_in
+    q0 = lo // n_out
+    q1 = np.minimum(n_in, (hi + n_out - 1) // n_out)
+    assert q0.min() >= 0 and q1.max() <= n_in and (q1 > q0).all()
+    used = np.zeros(n_in, np.int64)
+    width = q1 - q0
+    for w in np.unique(width):
+        sel = np.nonzero(width == w)[0]
+        q = q0[sel][:, None] + np.arange(w)[None, :]
+        ov = np.minimum(hi[sel][:, None], (q + 1) * n_out) - np.maximum(lo[sel][:, None], q * n_out)
+        assert (ov > 0).all()
+        assert (ov.sum(axis=1) == n_in).all()
+        np.add.at(used, q.ravel(), ov.ravel())
+    assert (used == n_out).all()
+    # the weights the kernel forms, ov as float32 (exact below 2^24)
+    assert max(n_in, n_out) < 2 ** 24
