@@ -361,3 +361,30 @@ def test_resampling_footprints_stay_in_the_input_and_cover_it_exactly(n_in, n_ou
     assert (used == n_out).all()
     # the weights the kernel forms, ov as float32 (exact below 2^24)
     assert max(n_in, n_out) < 2 ** 24
+
+
+# ---- the window kernel's shared memory (prost_window.cu) -----------------------
+
+NMAXW = _const(WINDOW_CU, r"constexpr int NMAXW = (\d+);")
+assert "float *Hs = Ys + K4 * a.n;" in WINDOW_CU
+assert "float *Us = Hs + (GRAD ? WT * (a.n + 1) : 0); // WT x K" in WINDOW_CU
+assert "w->smem_cost = (size_t)((k + 3) / 4 * 4) * n * sizeof(float);" in WINDOW_CU
+assert ("w->smem_grad = w->smem_cost + (size_t)WT * (n + 1) * sizeof(float) + (size_t)WT * k * sizeof(float);"
+        in WINDOW_CU)
+
+
+@pytest.mark.parametrize("k", range(1, KMAXW + 1))
+def test_window_shared_memory_carve_up_fits_the_launch(k):
+    """Ys (n x K4), then with gradients Hs (WT x (n + 1)) and Us (WT x k):
+    the carve-up ends inside the dynamic shared memory each launch asks for,
+    which stays inside the 227 KB a CTA may have."""
+    k4 = (k + 3) // 4 * 4
+    for n in range(1, NMAXW + 1):
+        smem_cost = k4 * n * 4
+        smem_grad = smem_cost + WT * (n + 1) * 4 + WT * k * 4
+        ys_end = k4 * n
+        assert ys_end * 4 <= smem_cost
+        hs_end = ys_end + WT * (n + 1)
+        us_end = hs_end + WT * k
+        assert us_end * 4 <= smem_grad <= 227 * 1024
+    assert (k4 * 4) % 16 == 0   # row t of Ys starts 16-byte aligned for its float4 loads
