@@ -3,6 +3,7 @@ include/prost.h; host-side argument checks work without a GPU."""
 
 import ctypes as C
 
+import numpy as np
 import pytest
 
 import paper_1302_2073_gb300 as pg
@@ -69,3 +70,48 @@ def test_null_arguments_are_rejected():
     assert L.prost_sync(None) == pg.PROST_EINVAL
     assert L.prost_get_stats(None, None) == pg.PROST_EINVAL
     L.prost_destroy(None)
+
+
+@pytest.mark.parametrize("args", [
+    (100, 3, 4, 8),          # m not a multiple of the channels
+    (100, 1, 0, 8),          # k < 1
+    (100, 1, 17, 8),         # k > 16
+    (100, 1, 4, 0),          # empty window
+    (100, 1, 4, 129),        # n > 128
+    ((1 << 30) + 1, 1, 4, 8),  # m > 2^30
+])
+def test_window_arguments_are_checked_on_the_host(args):
+    with pytest.raises(pg.ProstError) as ei:
+        pg.prost_window_init(*args)
+    assert ei.value.code == pg.PROST_EINVAL
+
+
+@pytest.mark.parametrize("p,omega", [(0.0, 0.5), (2.5, 0.5), (float("nan"), 0.5), (0.5, -0.1), (0.5, 1.5)])
+def test_window_exponent_and_weight_are_checked_on_the_host(p, omega):
+    with pytest.raises(pg.ProstError):
+        pg.prost_window_init(100, 1, 4, 8, p, omega)
+
+
+@pytest.mark.parametrize("args", [
+    (0, 480, 3, 160, 120, "u8", 100),        # empty input
+    (640, 480, 3, 0, 120, "u8", 100),        # empty output
+    (640, 480, 5, 160, 120, "u8", 100),      # more than 4 channels
+    (1 << 16, 1 << 15, 1, 160, 120, "u8", 100),  # input plane over 2^30 pixels
+    (640, 480, 3, 160, 120, 7, 100),         # unknown frame type
+    (640, 480, 3, 160, 120, "u8", 0),        # no initialisation phase
+])
+def test_pre_processing_arguments_are_checked_on_the_host(args):
+    with pytest.raises(pg.ProstError) as ei:
+        pg.prost_pre_init(*args)
+    assert ei.value.code == pg.PROST_EINVAL
+
+
+def test_batch_and_median_arguments_are_checked_on_the_host():
+    with pytest.raises(pg.ProstError):
+        pg.prost_batch_init([])
+    L = pg.lib()
+    m = np.zeros(16, np.uint8)
+    ptr = m.ctypes.data_as(C.c_void_p)
+    assert L.prost_median3x3(ptr, ptr, 0, 4, 0, None) == pg.PROST_EINVAL
+    assert L.prost_median3x3(ptr, ptr, 4, -1, 0, None) == pg.PROST_EINVAL
+    assert L.prost_median3x3(None, ptr, 4, 4, 0, None) == pg.PROST_EINVAL
