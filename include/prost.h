@@ -153,6 +153,15 @@ int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_
  * one of those was raised, else PROST_OK, and clears these flags. */
 int prost_sync(prost_handle *h);
 
+/* Fault injection for failure-detection tests, on the host (not in the
+ * paper).  Moves the handle's grid-barrier count by delta, as a frame launch
+ * that gave up part-way leaves it.  The next frame launch finds the count
+ * outside the range it expects and returns at once, leaving the state
+ * untouched.  The following prost_sync() reports PROST_ETIMEOUT and resets
+ * the barrier, and later frames run normally.  Synchronises the stream.
+ * Errors: PROST_EINVAL for a NULL handle, PROST_ECUDA. */
+int prost_inject_barrier_skew(prost_handle *h, int64_t delta);
+
 /* Copy out the current subspace (the re-orthonormalised representative,
  * m x k row-major float32) and y (k doubles).  Either pointer may be NULL.
  * on_device selects device or host pointers; synchronises when on_device = 0. */

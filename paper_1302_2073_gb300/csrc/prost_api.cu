@@ -438,6 +438,18 @@ int prost_sync(prost_handle *h)
     return PROST_OK;
 }
 
+int prost_inject_barrier_skew(prost_handle *h, int64_t delta)
+{
+    if (!h) return PROST_EINVAL;
+    DeviceGuard dg(h->device);
+    GridBar g;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(&g, h->bar, sizeof(GridBar), cudaMemcpyDeviceToHost));
+    g.count += (unsigned long long)delta;
+    CK(h, cudaMemcpy(h->bar, &g, sizeof(GridBar), cudaMemcpyHostToDevice));
+    return PROST_OK;
+}
+
 int prost_get_subspace(prost_handle *h, float *U_out, double *y_out, int on_device)
 {
     if (!h) return PROST_EINVAL;

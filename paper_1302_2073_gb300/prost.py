@@ -66,6 +66,7 @@ def lib():
         L.prost_init.argtypes = [P(prost_params), vp, P(vp)]
         L.prost_step.argtypes = [vp, vp, C.c_int, vp, vp]
         L.prost_sync.argtypes = [vp]
+        L.prost_inject_barrier_skew.argtypes = [vp, C.c_int64]
         L.prost_get_subspace.argtypes = [vp, vp, vp, C.c_int]
         L.prost_set_subspace.argtypes = [vp, vp, vp, C.c_int]
         L.prost_set_labels.argtypes = [vp, vp, C.c_int]
@@ -220,6 +221,13 @@ def prost_step(h, frame, mask_out=None, background_out=None):
 
 def prost_sync(h):
     return _check(lib().prost_sync(h), h, allow=(PROST_EBADFRAME,))
+
+
+def prost_inject_barrier_skew(h, delta):
+    """Failure-detection tests: leave the grid barrier as an aborted launch
+    would (host-side injection); the next frame is refused and prost_sync
+    raises PROST_ETIMEOUT, then the tracker recovers."""
+    return _check(lib().prost_inject_barrier_skew(h, int(delta)), h)
 
 
 def prost_get_subspace(h, U_out=None, y_out=None):

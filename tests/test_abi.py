@@ -69,6 +69,7 @@ def test_null_arguments_are_rejected():
     assert L.prost_step(None, None, 0, None, None) == pg.PROST_EINVAL
     assert L.prost_sync(None) == pg.PROST_EINVAL
     assert L.prost_get_stats(None, None) == pg.PROST_EINVAL
+    assert L.prost_inject_barrier_skew(None, 1) == pg.PROST_EINVAL
     L.prost_destroy(None)
 
 
