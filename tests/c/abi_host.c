@@ -109,6 +109,7 @@ int main(void)
     prm.p = 3.0;
     check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "p > 2 rejected");
     check(prost_init(NULL, NULL, NULL) == PROST_EINVAL, "prost_init without out");
+    check(prost_inject_barrier_skew(NULL, 1) == PROST_EINVAL, "injection without a handle");
     check(prost_batch_split(10, 3, w, cap, ctas) == PROST_OK, "batch split");
     check(ctas[0] == 4 && ctas[1] == 3 && ctas[2] == 3, "batch split of 10 over thirds");
     check(prost_batch_split(2, 3, w, cap, ctas) == PROST_EINVAL, "budget below the streams");
