@@ -154,10 +154,11 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
-def profiled_value(key="dram_bytes_per_launch_full_size", profile=None, kernel_src=None):
+def profiled_value(key="dram_bytes_per_launch_full_size", profile=None, kernel_src=None, gated=True):
     """A figure of the committed ncu summary of the frame kernel (DRAM or L2
-    bytes per launch, the L2 peak from ncu's counters), if the kernel source
-    is unchanged since the capture (else None)."""
+    bytes per launch, the L2 peak from ncu's counters).  A per-launch figure
+    (gated) is returned only while the kernel source is unchanged since the
+    capture (else None); the L2 peak is a property of the GPU and is not."""
     try:
         text = open(profile or PROFILE).read()
         src_hash = hashlib.sha256(open(kernel_src or KERNEL_SRC, "rb").read()).hexdigest()[:16]
@@ -168,7 +169,7 @@ def profiled_value(key="dram_bytes_per_launch_full_size", profile=None, kernel_s
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_sha256_16") != src_hash:
+    if gated and vals.get("kernel_source_sha256_16") != src_hash:
         return None
     try:
         return float(vals[key])
@@ -195,7 +196,7 @@ def l2_roofline(achieved, profiled):
     is committed."""
     if not profiled:
         return None
-    peak = profiled_value("l2_peak_gbs_ncu")
+    peak = profiled_value("l2_peak_gbs_ncu", gated=False)
     if not peak:
         return None
     return {"bound": "l2", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -121,6 +121,12 @@ typedef struct prost_stats {
     int64_t n_foreground;            /* pixels labelled foreground in the last frame */
     double orth_err;                 /* max |U^T U - I| of the stored subspace before its
                                         re-orthonormalisation at the end of the last frame */
+    double eta_norm;                 /* |eta| at the final y (Section 3.3) */
+    int32_t pi_explicit;             /* 1 when |pi(eta)| was formed as sum_e (eta_e - u_e^T g)^2
+                                        by an extra pass over U: the identity
+                                        |pi(eta)|^2 = |eta|^2 - |U^T eta|^2 (Eq. gproject)
+                                        loses its digits when |pi(eta)|^2 < |eta|^2 / 4 */
+    int32_t pad1;
 } prost_stats;
 
 /* Sizes of the device state of a handle with these parameters (bytes, device
@@ -141,10 +147,12 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out);
  * on_device = 1: all three are device pointers and the call only enqueues the
  * work on the handle's stream (returns PROST_OK; device-detected errors are
  * reported by prost_sync()).  on_device = 0: all three are host pointers; the
- * frame is copied to the device, the outputs back, and the call returns the
- * frame's status after the stream synchronised.  A frame with a non-finite
- * entry (float32 frames only) leaves the state unchanged and its outputs
- * unwritten (status PROST_EBADFRAME). */
+ * frame is copied to the device and the call returns the frame's status after
+ * the stream synchronised, with the outputs copied back only for a frame that
+ * completed (PROST_OK, PROST_ENOTSPD).  A frame with a non-finite entry
+ * (float32 frames only) leaves the state unchanged and, on the host path, its
+ * outputs unwritten (PROST_EBADFRAME); so does a frame refused or aborted by a
+ * bounded device-side wait (PROST_ETIMEOUT). */
 int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_out,
                float *background_out);
 
@@ -157,10 +165,26 @@ int prost_sync(prost_handle *h);
  * paper).  Moves the handle's grid-barrier count by delta, as a frame launch
  * that gave up part-way leaves it.  The next frame launch finds the count
  * outside the range it expects and returns at once, leaving the state
- * untouched.  The following prost_sync() reports PROST_ETIMEOUT and resets
- * the barrier, and later frames run normally.  Synchronises the stream.
- * Errors: PROST_EINVAL for a NULL handle, PROST_ECUDA. */
+ * untouched; on the host path prost_step() returns PROST_ETIMEOUT and leaves
+ * its outputs unwritten.  The following prost_sync() reports PROST_ETIMEOUT
+ * and resets the barrier, and later frames run normally (the refused frame
+ * does not count towards the periodic rebase).  A launch can only detect a
+ * backward skew (delta < 0) or a forward one of at least the frame kernel's
+ * grid size: a smaller forward skew looks like CTAs that already arrived, so
+ * 0 < delta < grid size returns PROST_EINVAL.  Synchronises the stream.
+ * Errors: PROST_EINVAL (NULL handle, undetectable delta), PROST_ECUDA. */
 int prost_inject_barrier_skew(prost_handle *h, int64_t delta);
+
+/* Fault injection for failure-detection tests (not in the paper): the next
+ * frame launch, at the grid barrier of residual pass `pass` (0..n_cg), waits
+ * for one arrival more than any launch makes, and gives up after `cycles` SM
+ * clock cycles (1..2e9; the default limit of every wait is 2e9, about one
+ * second).  The bounded wait then runs out as it would on a stalled GPU: the
+ * frame aborts with the state untouched (U, y, labels, frame counter), on the
+ * host path prost_step() returns PROST_ETIMEOUT, and prost_sync() reports
+ * PROST_ETIMEOUT and resets the barrier.  Applies to one launch.  Errors:
+ * PROST_EINVAL (NULL handle, pass or cycles out of range). */
+int prost_inject_wait_timeout(prost_handle *h, int32_t pass, int64_t cycles);
 
 /* Copy out the current subspace (the re-orthonormalised representative,
  * m x k row-major float32) and y (k doubles).  Either pointer may be NULL.
@@ -180,7 +204,6 @@ int prost_set_labels(prost_handle *h, const uint8_t *labels, int on_device);
 /* Set the frame counter i used by the step-size rule of the next frame. */
 int prost_set_frame_index(prost_handle *h, int64_t i);
 
-/* Statistics of the last frame (synchronises the stream). */
 /* Statistics of the last frame (the fields of prost_stats above: the cost and
  * gradient norm at every CG iterate of Step 1, the line steps and PR+
  * coefficients, sigma, t and theta of Step 2, the foreground count of Step 3,
@@ -215,16 +238,17 @@ int prost_get_timing(prost_handle *h, float *ms, int *n);
 
 /* Cost and gradient of one frame without any device allocation.
  *
- * The paper has no counterpart to this entry point; it exists for callers
- * that must not call cudaMalloc: code that runs while a CUDA graph is being
- * captured, real-time pipelines that forbid allocation after start-up
- * (cudaMalloc can synchronise the device and has no latency bound), and hosts
- * whose device memory belongs to another allocator's pool.  They cannot
- * create a handle with prost_init(), so this call takes everything from the
- * caller and keeps its scratch (the per-CTA partial sums and the arrival
- * counter of the reduction) in one file-scope static device array of about
- * 74 KB, which every GPU that loads the library holds until the process
- * exits.
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot call cudaMalloc: real-time loops that allow no allocation after
+ * start-up (cudaMalloc can synchronise the whole device and has no latency
+ * bound), plug-ins whose host application owns all device memory through its
+ * own pool or arena and hands them only the buffers they work on, and
+ * processes that reserve their memory once at start-up and run with what is
+ * left.  Such callers cannot create a handle with prost_init(), which
+ * allocates, so this call takes every buffer from the caller and keeps its
+ * only scratch (the per-CTA partial sums and the arrival counter of the
+ * reduction) in one file-scope static device array of about 74 KB, which
+ * every GPU that loads the library holds until the process exits.
  *
  * Computes, for the caller's subspace U and coefficients y, the weighted
  * smoothed l_p cost h_{mu,w}(x - U y) (Eqs. weightedLPnorm, spcacost) and its
@@ -353,6 +377,13 @@ int prost_window_eval(prost_window *w, const float *U, const float *Y, const flo
                       const float *mu, const float *gscale, float *cost, float *dU, float *dY, float *dmu);
 int prost_window_ustep(prost_window *w, const float *U, const float *dU, float t, float *U_out,
                        int32_t *status_out);
+/* Fault injection for failure-detection tests (not in the paper): the next
+ * prost_window_ustep() waits at its grid barrier `barrier` (1: after U^T dU,
+ * 2: after the Gram of V) for one arrival more than the launch makes and
+ * gives up after `cycles` SM clock cycles (1..2e9).  That U-step then writes
+ * status -2 (wait timed out) and leaves U_out unwritten; the next U-step runs
+ * normally.  Errors: PROST_EINVAL (NULL, barrier or cycles out of range). */
+int prost_window_inject_wait_timeout(prost_window *w, int32_t barrier, int64_t cycles);
 const char *prost_window_last_error(const prost_window *w);
 void prost_window_destroy(prost_window *w);
 

@@ -37,6 +37,8 @@ struct prost_handle {
     float *u_buf;          // staging of subspaces crossing the ABI from/to host memory
     int32_t *h_word;       // pinned scratch for small device -> host reads
     size_t partial_floats;
+    int stall_at;          // armed for the next frame by prost_inject_wait_timeout (0 = off)
+    long long stall_limit;
     int timing;            // record events around every kernel of prost_step()
     int timed_frames;      // traced frames since timing was enabled
     cudaEvent_t ev[CGMAX + 3];
@@ -181,9 +183,10 @@ void free_state(prost_handle *h)
     h->h_word = nullptr; h->bar = nullptr;
 }
 
-int run_gram(prost_handle *h)
+int run_gram(prost_handle *h, int after_rebase = 0)
 {
     GramArgs ga;
+    ga.after_rebase = after_rebase;
     ga.U = h->U;
     ga.ks = h->ks;
     ga.partials = h->partials;
@@ -196,10 +199,10 @@ int run_gram(prost_handle *h)
 // Move the stored rows onto the orthonormal representative (U_st <- U_st T,
 // T <- I).  A bfloat16 subspace is rounded in the move, so its Gram and
 // Cholesky-QR are taken again of the stored values.
-int rebase(prost_handle *h)
+int rebase(prost_handle *h, int force)
 {
-    CK(h, h->ops->rebase(h->U, h->ks, h->dp, h->stream));
-    if (h->dp.ubf16) return run_gram(h);
+    CK(h, h->ops->rebase(h->U, h->ks, h->dp, force, h->stream));
+    if (h->dp.ubf16) return run_gram(h, force ? 0 : 1);
     return PROST_OK;
 }
 
@@ -210,8 +213,6 @@ int read_status(prost_handle *h, int *status)
     *status = h->h_word[0];
     return PROST_OK;
 }
-
-constexpr uint32_t REBASE_EVERY = 1024;
 
 struct StateHeader {
     char magic[8];
@@ -227,7 +228,7 @@ struct StateHeader {
 
 extern "C" {
 
-int prost_version(void) { return 100; }
+int prost_version(void) { return 101; }
 
 const char *prost_strerror(int code)
 {
@@ -281,6 +282,8 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     h->counter = nullptr; h->frame_buf = nullptr; h->bg_buf = nullptr; h->u_buf = nullptr;
     h->h_word = nullptr; h->bar = nullptr; h->bar_base = 0;
     h->steps_since_rebase = 0;
+    h->stall_at = 0;
+    h->stall_limit = 0;
     h->timing = 0;
     h->timed_frames = 0;
     for (int i = 0; i < CGMAX + 3; ++i) h->ev[i] = nullptr;
@@ -332,7 +335,7 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     rc = run_gram(h);
     if (rc) return bail(rc);
     // store the orthonormal factor itself, so that the stored rows start orthonormal
-    rc = rebase(h);
+    rc = rebase(h, 1);
     if (rc) return bail(rc);
     int st = 0;
     rc = read_status(h, &st);
@@ -389,6 +392,9 @@ int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_
     fa.frame_pitch = pitch;
     fa.row_stride = (int)partial_row(h->prm.k);
     fa.grid = h->grid_frame;
+    fa.stall_at = h->stall_at;
+    fa.stall_limit = h->stall_limit;
+    h->stall_at = 0; // one launch only
     fa.prm = dp;
     if (h->timing) CK(h, cudaEventRecord(h->ev[0], h->stream));
     CK(h, h->ops->frame(fa, fdt, h->grid_frame, h->stream));
@@ -397,24 +403,29 @@ int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_
         h->timed_frames += 1;
     }
     // arrivals per frame: one per CTA at each residual pass and at the end
-    h->bar_base += (unsigned long long)h->grid_frame * (unsigned long long)(h->prm.n_cg + 2);
+    h->bar_base += (unsigned long long)h->grid_frame * (unsigned long long)frame_arrivals(h->prm.n_cg);
     // The frame kernel updates the stored rows in the stored basis (U = U_st T);
     // every REBASE_EVERY frames the stored rows are moved onto the orthonormal
-    // representative so that the conditioning of U_st cannot drift.
+    // representative so that the conditioning of U_st cannot drift.  The
+    // device counts the frames that completed, and the rebase runs only when
+    // that count is due, so a refused frame does not shift the rebase.
     if (++h->steps_since_rebase >= REBASE_EVERY) {
-        const int rc = rebase(h);
+        const int rc = rebase(h, 0);
         if (rc) return rc;
         h->steps_since_rebase = 0;
     }
     if (on_device) return PROST_OK;
+    // host outputs: only a frame that completed writes them
+    int st = 0;
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    if (st != PROST_OK && st != PROST_ENOTSPD) return st;
     if (mask_out)
         CK(h, cudaMemcpyAsync(mask_out, h->labels, (size_t)dp.P, cudaMemcpyDeviceToHost, h->stream));
     if (background_out)
         CK(h, cudaMemcpyAsync(background_out, h->bg_buf, (size_t)m * sizeof(float),
                               cudaMemcpyDeviceToHost, h->stream));
-    int st = 0;
-    int rc = read_status(h, &st);
-    if (rc) return rc;
+    if (mask_out || background_out) CK(h, cudaStreamSynchronize(h->stream));
     return st;
 }
 
@@ -427,10 +438,14 @@ int prost_sync(prost_handle *h)
     CK(h, cudaStreamSynchronize(h->stream));
     const uint32_t f = (uint32_t)h->h_word[0];
     if (f & ERR_TIMEOUT) {
-        // an aborted frame leaves the grid barrier count unknown: start it afresh
+        // an aborted frame leaves the grid barrier count unknown: start it
+        // afresh; the refused frames did not count towards the next rebase
         CK(h, cudaMemsetAsync(h->bar, 0, sizeof(GridBar), h->stream));
+        CK(h, cudaMemcpyAsync(h->h_word, &h->ks->frames_since_rebase, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                              h->stream));
         CK(h, cudaStreamSynchronize(h->stream));
         h->bar_base = 0;
+        h->steps_since_rebase = (uint32_t)h->h_word[0];
         return PROST_ETIMEOUT;
     }
     if (f & ERR_NOTSPD) return PROST_ENOTSPD;
@@ -441,12 +456,26 @@ int prost_sync(prost_handle *h)
 int prost_inject_barrier_skew(prost_handle *h, int64_t delta)
 {
     if (!h) return PROST_EINVAL;
+    // a forward skew below the grid size looks like CTAs that already arrived:
+    // the launch cannot tell it from a healthy barrier
+    if (delta > 0 && delta < (int64_t)h->grid_frame)
+        return fail(h, PROST_EINVAL, "a forward skew below the grid size is not detectable");
     DeviceGuard dg(h->device);
     GridBar g;
     CK(h, cudaStreamSynchronize(h->stream));
     CK(h, cudaMemcpy(&g, h->bar, sizeof(GridBar), cudaMemcpyDeviceToHost));
     g.count += (unsigned long long)delta;
     CK(h, cudaMemcpy(h->bar, &g, sizeof(GridBar), cudaMemcpyHostToDevice));
+    return PROST_OK;
+}
+
+int prost_inject_wait_timeout(prost_handle *h, int32_t pass, int64_t cycles)
+{
+    if (!h) return PROST_EINVAL;
+    if (pass < 0 || pass > h->prm.n_cg) return fail(h, PROST_EINVAL, "pass must be in 0..n_cg");
+    if (cycles < 1 || cycles > 2000000000ll) return fail(h, PROST_EINVAL, "cycles must be in 1..2e9");
+    h->stall_at = pass + 1;
+    h->stall_limit = cycles;
     return PROST_OK;
 }
 
@@ -500,7 +529,7 @@ int prost_set_subspace(prost_handle *h, const float *U, const double *y, int on_
     if (rc) return rc;
     if (st == PROST_ENOTSPD) return fail(h, PROST_ENOTSPD, "subspace columns are not linearly independent");
     // store the orthonormal factor itself, so that the stored rows start orthonormal
-    rc = rebase(h);
+    rc = rebase(h, 1);
     if (rc) return rc;
     CK(h, cudaStreamSynchronize(h->stream));
     return PROST_OK;
@@ -560,6 +589,8 @@ int prost_get_stats(prost_handle *h, prost_stats *out)
     out->updated = ks.updated;
     out->n_foreground = ks.n_fg;
     out->orth_err = ks.orth_err;
+    out->eta_norm = ks.eta_norm;
+    out->pi_explicit = ks.pi_explicit;
     return PROST_OK;
 }
 
@@ -575,7 +606,7 @@ int prost_get_state(prost_handle *h, void *buf, size_t *len)
     StateHeader hd;
     memset(&hd, 0, sizeof(hd));
     memcpy(hd.magic, "PROSTST1", 8);
-    hd.version = 2; // 2: the k-space state without the fields of an earlier design
+    hd.version = 3; // 3: the k-space state with |eta| and the projection-pass flag
     hd.header_bytes = sizeof(StateHeader);
     hd.prm = h->prm;
     hd.u_bytes = u_bytes;
@@ -603,7 +634,7 @@ int prost_set_state(prost_handle *h, const void *buf, size_t len)
     if (len < sizeof(StateHeader)) return fail(h, PROST_EINVAL, "state buffer too short");
     StateHeader hd;
     memcpy(&hd, buf, sizeof(hd));
-    if (memcmp(hd.magic, "PROSTST1", 8) != 0 || hd.version != 2 || hd.header_bytes != sizeof(StateHeader))
+    if (memcmp(hd.magic, "PROSTST1", 8) != 0 || hd.version != 3 || hd.header_bytes != sizeof(StateHeader))
         return fail(h, PROST_EINVAL, "not a prost state buffer of this version");
     prost_params a = hd.prm, b = h->prm;
     a.seed = b.seed = 0;
@@ -956,7 +987,7 @@ extern "C" int prost_batch_step(prost_batch *b, const void *const *frames, uint8
         fa.row_stride = (int)partial_row(h->prm.k);
         fa.grid = b->grid[s];
         fa.prm = dp;
-        h->bar_base += (unsigned long long)b->grid[s] * (unsigned long long)(h->prm.n_cg + 2);
+        h->bar_base += (unsigned long long)b->grid[s] * (unsigned long long)frame_arrivals(h->prm.n_cg);
     }
     if (b->use_graph && b->graph_ok) {
         if (!b->gexec[t]) {
@@ -977,7 +1008,7 @@ extern "C" int prost_batch_step(prost_batch *b, const void *const *frames, uint8
     b->buf ^= 1;
     if (++b->ticks_since_rebase >= REBASE_EVERY) {
         for (prost_handle *h : b->h) {
-            const int rc = rebase(h);
+            const int rc = rebase(h, 0);
             if (rc) return bfail(b, rc, h->err);
             h->steps_since_rebase = 0;
         }

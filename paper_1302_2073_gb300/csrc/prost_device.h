@@ -12,6 +12,15 @@ constexpr int CGMAX = 32;    // largest number of CG iterations per frame
 constexpr int THREADS = 256; // threads per CTA of the Gram and layout kernels
 constexpr int TILE_P = 224;  // pixels per tile of the stored subspace (16-byte multiple for uint8)
 
+// Grid-barrier arrivals of every frame-kernel CTA per frame: one per residual
+// pass (n_cg + 1), one for the projection pass (made at the end of the frame
+// when that pass does not run) and one at the end of the frame.
+__host__ __device__ constexpr int frame_arrivals(int n_cg) { return n_cg + 3; }
+
+// The stored rows are moved onto the orthonormal representative (U_st <- U_st
+// T, T <- I) after every REBASE_EVERY completed frames.
+constexpr uint32_t REBASE_EVERY = 1024;
+
 // Device-resident k-space state of one stream.  The stored subspace U_st is
 // kept in float32 or bfloat16; its orthonormal representative is U = U_st T
 // with T = R^{-1}, U_st^T U_st = R^T R (Cholesky-QR folded into the next
@@ -30,10 +39,14 @@ struct KState {
     int32_t last_status;       // status of the last frame
     int32_t n_cg_done;
     int64_t bad_frames;
+    uint32_t frames_since_rebase; // frames that reached the end of the frame kernel since the last rebase
+    int32_t rebased;              // the last rebase request ran (else it was not due)
     // statistics of the last frame
     double cost[CGMAX + 1], gnorm[CGMAX + 1], alpha[CGMAX], beta[CGMAX + 1];
     double pi_norm, y_norm, sigma, t, theta, orth_err;
-    int32_t updated, pad0;
+    double eta_norm;           // |eta| at the final y
+    int32_t updated;
+    int32_t pi_explicit;       // |pi(eta)| came from the explicit projection pass
     int64_t n_fg;
     // %globaltimer (ns): start of the frame, end of each residual pass, end of the frame
     uint64_t phase_ts[CGMAX + 3];
@@ -77,6 +90,7 @@ struct GramArgs {
     KState *ks;
     float *partials;
     unsigned int *counter;
+    int after_rebase; // 1: only if the rebase just requested ran (ks->rebased)
     DevParams prm;
 };
 
@@ -100,6 +114,11 @@ struct FrameArgs {
     int64_t frame_pitch;
     int row_stride;
     int grid;                 // CTAs working on this stream (its grid barrier's size)
+    // failure-detection tests only (0 = off): at the grid barrier of residual
+    // pass stall_at - 1 wait for one arrival more than any launch makes,
+    // giving up after stall_limit SM clock cycles
+    int stall_at;
+    long long stall_limit;
     DevParams prm;
 };
 
@@ -114,7 +133,8 @@ struct KernelOps {
     cudaError_t (*export_u)(const void *U, const KState *ks, float *out, DevParams prm,
                             cudaStream_t);
     int (*gram_occupancy)();
-    cudaError_t (*rebase)(void *U, KState *ks, DevParams prm, cudaStream_t);
+    // force = 0: only when frames_since_rebase >= REBASE_EVERY (else a no-op)
+    cudaError_t (*rebase)(void *U, KState *ks, DevParams prm, int force, cudaStream_t);
     int vw;        // pixels per thread of the Gram kernel
     int tile;      // pixels per tile of the frame kernel
     int frame_threads;
@@ -125,8 +145,9 @@ cudaError_t launch_init_gauss(void *U, DevParams prm, uint64_t seed, cudaStream_
 cudaError_t launch_import_u(const float *Urow, void *U, DevParams prm, cudaStream_t s);
 cudaError_t launch_import_labels(const uint8_t *src, uint8_t *labels, DevParams prm,
                                  cudaStream_t s);
-// after a rebase: R = T = I and the stored-row coefficients equal y
-cudaError_t launch_reset_fold(KState *ks, DevParams prm, cudaStream_t s);
+// after a rebase: R = T = I, the stored-row coefficients equal y and the
+// rebase counter restarts (force = 0: only when the counter is due)
+cudaError_t launch_reset_fold(KState *ks, DevParams prm, int force, cudaStream_t s);
 
 // per-k kernel sets, filled by the instantiation units
 void register_ops_k01_02(const KernelOps **f32, const KernelOps **bf16);

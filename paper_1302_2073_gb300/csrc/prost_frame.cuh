@@ -117,6 +117,7 @@ template <int K> struct SKState {
     float Tf[K * K];   // T = R^{-1}, row-major upper triangular
     float Rf[K * K];   // R, row-major upper triangular
     float cm1, snp, yn;
+    int proj;          // |pi(eta)| is formed by the explicit projection pass
     int skip;          // frame rejected (non-finite entry)
     int err;           // a grid barrier gave up
     int last;          // this CTA arrived last at the end of the frame
@@ -276,8 +277,11 @@ __device__ __forceinline__ void mma_row(const unsigned char *base, int warp_byte
 }
 
 // Grid barrier: arrive, wait (bounded) until all CTAs arrived.
+// A wait that gives up (or sees another CTA's abort) marks the frame timed
+// out: the abort flag, ERR_TIMEOUT and the frame's status PROST_ETIMEOUT.
 template <int NCONS>
-__device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target, int *s_err, KState *ks)
+__device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target, int *s_err, KState *ks,
+                                          long long limit = WAIT_LIMIT)
 {
     cons_sync<NCONS>();
     if (threadIdx.x == 0) {
@@ -288,7 +292,7 @@ __device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target
             unsigned it = 0;
             while (ld_acquire_u64(&gb->count) < target) {
                 if ((++it & 15u) == 0) {
-                    if (*(volatile int *)&gb->abort || clock64() - t0 > WAIT_LIMIT) {
+                    if (*(volatile int *)&gb->abort || clock64() - t0 > limit) {
                         ok = 0;
                         break;
                     }
@@ -298,6 +302,7 @@ __device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target
         if (!ok) {
             atomicExch(&gb->abort, 1);
             atomicOr(&ks->err_flags, ERR_TIMEOUT);
+            ks->last_status = -5; // PROST_ETIMEOUT
             *s_err = 1;
         }
         __threadfence();
@@ -330,6 +335,34 @@ __device__ __forceinline__ float step_size(const DevParams &prm, int64_t i)
         e = ldexpf(expf(-r) * (float)prm.t_init, -(int)q);
     }
     return fmaxf(e, (float)prm.t_min);
+}
+
+// Below this fraction of |eta|^2, |pi(eta)|^2 is formed by the explicit
+// projection pass rather than as |eta|^2 - |U^T eta|^2: above it the FP32
+// sums (relative error about 1e-6) leave |pi(eta)| accurate to about 2e-6.
+constexpr float PROJ_RATIO = 0.25f;
+
+// Step 2's angle from |pi(eta)| (one thread): sigma = |pi(eta)| |y| (Eq. svd),
+// theta = sigma t (Eq. geodesic), skipped when |y| = 0 or |pi(eta)| = 0.
+template <int K>
+__device__ __forceinline__ void step_angle(SKState<K> &sk, const DevParams &prm, float pin, KState *gks, bool stats)
+{
+    const float yn = sk.yn;
+    const bool upd = yn > 0.f && pin > 0.f;
+    const float t = step_size(prm, sk.frame_index);
+    const float sigma = pin * yn;
+    const float theta = sigma * t;
+    const float sh = sinf(0.5f * theta);
+    sk.cm1 = upd ? -2.f * sh * sh : 0.f;
+    sk.snp = upd ? sinf(theta) / pin : 0.f;
+    if (stats) {
+        gks->pi_norm = pin;
+        gks->y_norm = yn;
+        gks->sigma = sigma;
+        gks->t = t;
+        gks->theta = upd ? theta : 0.f;
+        gks->updated = upd ? 1 : 0;
+    }
 }
 
 // CG bookkeeping at iterate `pass` from the reduced sums tot:
@@ -409,13 +442,14 @@ __device__ void kspace_cg(SKState<K> &sk, const DevParams &prm, const float *tot
     } else {
         const float yl = act ? (float)sk.y[l] : 0.f;
         const float yn = sqrtf(wsumf(yl * yl));
+        // |pi(eta)|^2 = |eta|^2 - |U^T eta|^2 (Eq. gproject, U orthonormal)
+        // cancels when most of eta lies in span(U): below a quarter of |eta|^2
+        // the FP32 sums would leave too few digits, and the explicit pass
+        // sum_e (eta_e - u_e^T g)^2 (proj_pass) forms the norm instead
         const float pin2 = ee - gsq;
-        const float pin = pin2 > 0.f ? sqrtf(pin2) : 0.f;
-        const bool upd = yn > 0.f && pin > 0.f;
-        const float t = step_size(prm, sk.frame_index);
-        const float sigma = pin * yn;
-        const float theta = sigma * t;
-        const float sh = sinf(0.5f * theta);
+        const bool proj = yn > 0.f && ee > 0.f && !(pin2 > PROJ_RATIO * ee);
+        const float pin = (!proj && pin2 > 0.f) ? sqrtf(pin2) : 0.f;
+        const bool upd = yn > 0.f && (proj || pin > 0.f);
         // the update pass works on the stored rows u_st (u = T^T u_st): it needs
         // T v and T g for the dots and w = R^T v, since u_st + gamma R^T v is
         // the stored row of u + gamma v
@@ -437,18 +471,14 @@ __device__ void kspace_cg(SKState<K> &sk, const DevParams &prm, const float *tot
             sk.w[l] = wl;
         }
         if (l == 0) {
-            sk.cm1 = upd ? -2.f * sh * sh : 0.f;
-            sk.snp = upd ? sinf(theta) / pin : 0.f;
             sk.yn = yn;
+            sk.proj = proj ? 1 : 0;
             if (stats) {
-                gks->pi_norm = pin;
-                gks->y_norm = yn;
-                gks->sigma = sigma;
-                gks->t = t;
-                gks->theta = upd ? theta : 0.f;
-                gks->updated = upd ? 1 : 0;
+                gks->eta_norm = sqrtf(fmaxf(ee, 0.f));
+                gks->pi_explicit = proj ? 1 : 0;
                 gks->n_cg_done = prm.n_cg;
             }
+            if (!proj) step_angle(sk, prm, pin, gks, stats);
         }
     }
 }
@@ -684,6 +714,7 @@ __device__ void end_frame(const SKState<K> &sk, KState *ks, const float *G, floa
             ks->err_flags |= ERR_BADFRAME;
             ks->last_status = -4; // PROST_EBADFRAME
             ks->bad_frames += 1;
+            ks->frames_since_rebase += 1;
         }
         return;
     }
@@ -760,6 +791,7 @@ __device__ void end_frame(const SKState<K> &sk, KState *ks, const float *G, floa
         if (!ok) ks->err_flags |= ERR_NOTSPD;
         ks->n_fg = (int64_t)n_fg;
         ks->frame_index = sk.frame_index + 1;
+        ks->frames_since_rebase += 1;
         ks->last_status = ok ? 0 : -6; // PROST_ENOTSPD
         ks->skip = 0;
     }
@@ -845,6 +877,62 @@ __device__ __forceinline__ void residual_pass(const FrameArgs &a, const FrameTil
     }
 }
 
+// The explicit projection pass over this CTA's tiles (register form): the
+// per-thread sum of pi(eta)_e^2 = (eta_e - u_e^T g)^2 at the final y
+// (Eq. gproject), with u_e^T g = u_st,e^T (T g).
+template <int K, typename FT, typename UT>
+__device__ __forceinline__ void proj_pass(const FrameArgs &a, const FrameTiles &tl, const SKState<K> &sk,
+                                          float &acc)
+{
+    using F = FCfg<K, UT>;
+    constexpr int TP = F::TP, RW = F::RW, IPT = F::IPT;
+    const DevParams &prm = a.prm;
+    float y[K], tg[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        y[j] = sk.yf[j];
+        tg[j] = sk.tg[j];
+    }
+    const float mu = prm.mu, e = prm.e, pw = prm.p, om = prm.omega;
+    const float sc = prm.in_scale, of = prm.in_offset;
+    const FT *frame = static_cast<const FT *>(a.frame);
+    const int nitems = tl.nres * IPT;
+    for (int it = threadIdx.x; it < nitems; it += F::THREADS) {
+        const int ti = tl.r0 + it / IPT;
+        const int rp = it - (it / IPT) * IPT;
+        const int c = ti / prm.npt;
+        const int64_t p = (int64_t)(ti - c * prm.npt) * TP + rp * RW;
+        const int nvalid = prm.P - p < RW ? (int)(prm.P - p) : RW;
+        const UT *ub = static_cast<const UT *>(a.U) + (int64_t)ti * K * TP + rp * RW;
+        float u[K][RW];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const float2 v = ldcg_u2(ub + j * TP);
+            u[j][0] = v.x;
+            u[j][1] = v.y;
+        }
+        float xv[RW], lb[RW];
+        ld2(frame + (int64_t)c * a.frame_pitch + p, nvalid == RW, nvalid, xv);
+        ld2(a.labels + p, true, RW, lb);
+#pragma unroll
+        for (int r = 0; r < RW; ++r) {
+            const bool valid = r < nvalid;
+            float uy = 0.f, ug = 0.f;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                uy = fmaf(u[j][r], y[j], uy);
+                ug = fmaf(u[j][r], tg[j], ug);
+            }
+            const float res = valid ? fmaf(xv[r], sc, -of) - uy : 0.f;
+            const float z = fmaf(res, res, mu);
+            const float wv = valid ? (lb[r] != 0.f ? om : 1.f) : 0.f;
+            const float eta = -pw * (wv * __powf(z, e)) * res;
+            const float pe = valid ? eta - ug : 0.f;
+            acc = fmaf(pe, pe, acc);
+        }
+    }
+}
+
 // The frame of one stream, by CTA b of the G CTAs working on it.
 template <int K, typename FT, typename UT>
 __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, const int b)
@@ -868,6 +956,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         sk.err = (c0 < a.bar_base || c0 >= a.bar_base + (unsigned long long)G) ? 1 : 0;
         sk.skip = 0;
         sk.last = 0;
+        sk.proj = 0;
         sk.frame_index = a.ks->frame_index;
     }
     for (int i = tid; i < K * K; i += NT) {
@@ -881,7 +970,10 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     }
     __syncthreads();
     if (sk.err) {
-        if (tid == 0 && b == 0) atomicOr(&a.ks->err_flags, ERR_TIMEOUT);
+        if (tid == 0 && b == 0) {
+            atomicOr(&a.ks->err_flags, ERR_TIMEOUT);
+            a.ks->last_status = -5; // PROST_ETIMEOUT: the frame was refused
+        }
         return;
     }
 
@@ -917,7 +1009,9 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 cons_partials<F::NPR, NW>(acc, F::NVR, row, sred);
             }
             if (trace) a.ks->sub_ts[1] = global_ns();
-            if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
+            if (!grid_wait<NT>(a.bar, target + (pass + 1 == a.stall_at ? 1ull : 0ull), &sk.err, a.ks,
+                               pass + 1 == a.stall_at ? a.stall_limit : WAIT_LIMIT))
+                return;
             if (trace) a.ks->sub_ts[2] = global_ns();
             reduce_rows<NT>(rows, G, a.row_stride, F::NVR, tot, rscr);
             if (trace) a.ks->sub_ts[3] = global_ns();
@@ -935,12 +1029,33 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 cons_partials_tree<F::NVF, NW>(acc, F::NVF, row, sred);
             else
                 cons_partials<F::NPF, NW>(acc, F::NVF, row, sred);
-            if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
+            if (!grid_wait<NT>(a.bar, target + (pass + 1 == a.stall_at ? 1ull : 0ull), &sk.err, a.ks,
+                               pass + 1 == a.stall_at ? a.stall_limit : WAIT_LIMIT))
+                return;
             reduce_rows<NT>(rows, G, a.row_stride, F::NVF, tot, rscr);
             if (warp == 0) kspace_cg<K, false>(sk, prm, tot, pass, a.ks, stats);
         }
         cons_sync<NT>();
         if (stats && tid == 0) a.ks->phase_ts[pass + 1] = global_ns();
+        buf ^= 1;
+    }
+
+    // ---- |pi(eta)| by the explicit projection pass, where the norm identity
+    // of the final pass cancels (the same decision in every CTA) ----
+    if (sk.proj) {
+        float *prow = a.partials + ((size_t)buf * G + b) * a.row_stride;
+        const float *prows = a.partials + (size_t)buf * G * a.row_stride;
+        target += (unsigned long long)G;
+        float acc1[1] = {0.f};
+        if constexpr (F::STREAM)
+            stream_residual<K, FT, UT, false, NW, 1, true>(a, tl.r0, tl.nres, sk.yf, wstage, acc1, sk.tg);
+        else
+            proj_pass<K, FT, UT>(a, tl, sk, acc1[0]);
+        cons_partials_tree<1, NW, 1>(acc1, 1, prow, sred);
+        if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
+        reduce_rows<NT>(prows, G, a.row_stride, 1, tot, rscr);
+        if (tid == 0) step_angle(sk, prm, sqrtf(fmaxf(tot[0], 0.f)), a.ks, stats);
+        cons_sync<NT>();
         buf ^= 1;
     }
 
@@ -1086,8 +1201,12 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     cons_sync<NT>();
     if (tid == 0 && stats) a.ks->sub_ts[6] = global_ns();
     if (tid == 0) {
-        const unsigned long long old = atomicAdd(&a.bar->count, 1ull);
-        sk.last = old == target + (unsigned long long)G - 1ull;
+        // every CTA arrives FRAME_ARRIVALS(n_cg) times per frame: once per
+        // residual pass, once at the projection barrier (counted here when that
+        // pass did not run) and once here; the last arrival of all is here
+        const unsigned long long inc = sk.proj ? 1ull : 2ull;
+        const unsigned long long old = atomicAdd(&a.bar->count, inc);
+        sk.last = old + inc == a.bar_base + (unsigned long long)G * (unsigned long long)frame_arrivals(prm.n_cg);
         __threadfence();
     }
     cons_sync<NT>();

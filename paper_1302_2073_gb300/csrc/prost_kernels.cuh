@@ -354,6 +354,7 @@ __global__ void __launch_bounds__(THREADS) k_gram(const GramArgs a)
     __shared__ double tot[NM];
     __shared__ double sR[K * K], sT[K * K];
     const DevParams &prm = a.prm;
+    if (a.after_rebase && !a.ks->rebased) return; // the periodic rebase was not due
     float acc[NP];
 #pragma unroll
     for (int i = 0; i < NP; ++i) acc[i] = 0.f;
@@ -416,8 +417,11 @@ __global__ void __launch_bounds__(THREADS) k_export(const UT *U, const KState *k
 // Rebase of the stored rows onto the orthonormal representative: U_st <- U_st T
 // (each row u_st becomes T^T u_st), after which the fold is the identity.
 template <int K, typename UT>
-__global__ void __launch_bounds__(THREADS) k_rebase(UT *U, const KState *ks, DevParams prm)
+__global__ void __launch_bounds__(THREADS) k_rebase(UT *U, const KState *ks, DevParams prm, int force)
 {
+    // unforced, it runs only when the frames since the last rebase are due (a
+    // frame refused by a stale barrier does not count)
+    if (!force && ks->frames_since_rebase < REBASE_EVERY) return;
     __shared__ float sT[K * K];
     for (int i = threadIdx.x; i < K * K; i += THREADS) sT[i] = ks->Tf[i];
     __syncthreads();
@@ -457,13 +461,13 @@ template <int K, typename UT> struct Ops {
         k_export<K, UT><<<grid, THREADS, 0, s>>>(static_cast<const UT *>(U), ks, out, prm);
         return cudaGetLastError();
     }
-    static cudaError_t rebase(void *U, KState *ks, DevParams prm, cudaStream_t s)
+    static cudaError_t rebase(void *U, KState *ks, DevParams prm, int force, cudaStream_t s)
     {
         const int64_t nb = ((int64_t)prm.C * prm.Pp + THREADS - 1) / THREADS;
-        k_rebase<K, UT><<<(int)(nb < 4096 ? nb : 4096), THREADS, 0, s>>>(static_cast<UT *>(U), ks, prm);
+        k_rebase<K, UT><<<(int)(nb < 4096 ? nb : 4096), THREADS, 0, s>>>(static_cast<UT *>(U), ks, prm, force);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        return launch_reset_fold(ks, prm, s);
+        return launch_reset_fold(ks, prm, force, s);
     }
     static int gram_occupancy()
     {

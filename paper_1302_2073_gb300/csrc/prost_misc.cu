@@ -82,8 +82,13 @@ __global__ void k_import_labels(const uint8_t *src, uint8_t *labels, DevParams p
         labels[q] = (src && q < prm.P && src[q]) ? 1 : 0;
 }
 
-__global__ void k_reset_fold(KState *ks, int k)
+__global__ void k_reset_fold(KState *ks, int k, int force)
 {
+    const bool due = force || ks->frames_since_rebase >= REBASE_EVERY;
+    __syncthreads(); // every thread has read the counter before it restarts
+    if (threadIdx.x == 0) ks->rebased = due ? 1 : 0;
+    if (!due) return;
+    if (threadIdx.x == 0) ks->frames_since_rebase = 0;
     for (int q = threadIdx.x; q < KMAX * KMAX; q += blockDim.x) {
         const int i = q / KMAX, j = q % KMAX;
         ks->R[q] = ks->T[q] = (i == j) ? 1.0 : 0.0;
@@ -118,9 +123,9 @@ cudaError_t launch_import_u(const float *Urow, void *U, DevParams prm, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset_fold(KState *ks, DevParams prm, cudaStream_t s)
+cudaError_t launch_reset_fold(KState *ks, DevParams prm, int force, cudaStream_t s)
 {
-    k_reset_fold<<<1, 256, 0, s>>>(ks, prm.k);
+    k_reset_fold<<<1, 256, 0, s>>>(ks, prm.k, force);
     return cudaGetLastError();
 }
 

@@ -205,10 +205,14 @@ template <int K, typename FT, typename UT> struct Chunks {
 // tile ahead (step s of tile t + 1 is issued while step s of tile t is
 // consumed: one pointer update per tile, the steps unrolled); otherwise a
 // general pipeline keeps S::D - 1 steps in flight.
-template <int K, typename FT, typename UT, bool WM, int NW, int NP>
+//
+// PJ: the explicit projection pass instead, the one sum acc[0] of
+// (eta_e - u_st,e^T tg)^2 = |pi(eta)|^2 with tg = T g (Eq. gproject).
+template <int K, typename FT, typename UT, bool WM, int NW, int NP, bool PJ = false>
 __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int nres, const float *yf,
-                                                unsigned char *wbuf, float (&acc)[NP])
+                                                unsigned char *wbuf, float (&acc)[NP], const float *tgv = nullptr)
 {
+    static_assert(!(PJ && WM), "the projection pass forms no products");
     using S = StageCfg<K, FT, UT>;
     constexpr int NM = WM ? K * (K + 1) / 2 : 0;
     constexpr int SPT = S::STEPS_PER_TILE;
@@ -226,9 +230,13 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
         }
         __syncwarp();
     }
-    float y[K];
+    float y[K], tg[PJ ? K : 1];
 #pragma unroll
     for (int j = 0; j < K; ++j) y[j] = yf[j];
+    if constexpr (PJ) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) tg[j] = tgv[j];
+    }
     const float mu = prm.mu, e = prm.e, pw = prm.p, om = prm.omega;
     const float sc = prm.in_scale, of = prm.in_offset;
     const int npt = prm.npt;
@@ -250,6 +258,17 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
 #pragma unroll
         for (int j = 0; j < K; ++j) uq[j & 3] = fmaf(u[j], y[j], uq[j & 3]);
         const float uy = (uq[0] + uq[1]) + (uq[2] + uq[3]);
+        if constexpr (PJ) {
+            const float res = valid ? fmaf(xv, sc, -of) - uy : 0.f;
+            const float z = fmaf(res, res, mu);
+            const float wv = valid ? (lb != 0 ? om : 1.f) : 0.f;
+            const float eta = -pw * (wv * __powf(z, e)) * res;
+            float gq[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < K; ++j) gq[j & 3] = fmaf(u[j], tg[j], gq[j & 3]);
+            const float pe = valid ? eta - ((gq[0] + gq[1]) + (gq[2] + gq[3])) : 0.f;
+            acc[0] = fmaf(pe, pe, acc[0]);
+        } else {
         if constexpr (sizeof(FT) == 4) {
             if (valid && !isfinite(xv)) acc[K + NM + 2] += 1.f;
         }
@@ -289,6 +308,7 @@ __device__ __forceinline__ void stream_residual(const FrameArgs &a, int r0, int 
 #pragma unroll
                 for (int l2 = j; l2 < K; ++l2) acc[K + tri<K>(j, l2)] = fmaf(cu, u[l2], acc[K + tri<K>(j, l2)]);
             }
+        }
         }
     };
 

@@ -250,11 +250,15 @@ struct UstepArgs {
     int *status;
     int64_t m;
     float t;
+    // failure-detection tests only (0 = off): barrier stall_at waits for one
+    // arrival more than the launch makes and gives up after stall_limit cycles
+    int stall_at;
+    long long stall_limit;
 };
 
 // Grid barrier: arrive, then a bounded spin; false when it gave up (the abort
 // flag then releases every other CTA too).
-__device__ bool ustep_wait(unsigned int *bar, unsigned int target)
+__device__ bool ustep_wait(unsigned int *bar, unsigned int target, long long limit = UWAIT_LIMIT)
 {
     __shared__ int ok_s;
     __syncthreads();
@@ -268,7 +272,7 @@ __device__ bool ustep_wait(unsigned int *bar, unsigned int target)
             unsigned int v;
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
             if (v >= target) break;
-            if ((++it & 15u) == 0 && (*(volatile unsigned int *)(bar + 1) || clock64() - t0 > UWAIT_LIMIT)) {
+            if ((++it & 15u) == 0 && (*(volatile unsigned int *)(bar + 1) || clock64() - t0 > limit)) {
                 atomicExch(bar + 1, 1u);
                 ok = 0;
                 break;
@@ -307,7 +311,7 @@ __global__ void __launch_bounds__(WT, 1) k_ustep(UstepArgs a)
         __syncthreads();
     }
     if (tid < KK) a.rows[(size_t)b * URS + tid] = acc;
-    if (!ustep_wait(a.bar, (unsigned)G)) {
+    if (!ustep_wait(a.bar, (unsigned)G + (a.stall_at == 1 ? 1u : 0u), a.stall_at == 1 ? a.stall_limit : UWAIT_LIMIT)) {
         if (b == 0 && tid == 0) *a.status = -2;
         return;
     }
@@ -341,7 +345,8 @@ __global__ void __launch_bounds__(WT, 1) k_ustep(UstepArgs a)
         __syncthreads();
     }
     if (gram) a.rows[(size_t)(G + b) * URS + prost::tri<K>(ri, rl)] = gacc;
-    if (!ustep_wait(a.bar, 2u * (unsigned)G)) {
+    if (!ustep_wait(a.bar, 2u * (unsigned)G + (a.stall_at == 2 ? 1u : 0u),
+                    a.stall_at == 2 ? a.stall_limit : UWAIT_LIMIT)) {
         if (b == 0 && tid == 0) *a.status = -2;
         return;
     }
@@ -388,6 +393,8 @@ struct prost_window {
     unsigned int *ubar; // U-step grid barrier
     float *V;
     int *status;
+    int stall_at;       // armed for the next U-step by prost_window_inject_wait_timeout
+    long long stall_limit;
     std::string err;
 };
 
@@ -421,6 +428,9 @@ template <int K> struct WinOps {
         a.status = w->status;
         a.m = w->m;
         a.t = t;
+        a.stall_at = w->stall_at;
+        a.stall_limit = w->stall_limit;
+        w->stall_at = 0; // one launch only
         void *args[] = {&a};
         return cudaLaunchCooperativeKernel((void *)k_ustep<K>, dim3(w->nb_u), dim3(WT), args, 0, w->stream);
     }
@@ -573,6 +583,18 @@ extern "C" int prost_window_ustep(prost_window *w, const float *U, const float *
     }
     WIN_CK(win_ops(w->k).ustep(w, U, dU, t, U_out));
     if (status_out) WIN_CK(cudaMemcpyAsync(status_out, w->status, sizeof(int), cudaMemcpyDeviceToDevice, w->stream));
+    return PROST_OK;
+}
+
+extern "C" int prost_window_inject_wait_timeout(prost_window *w, int32_t barrier, int64_t cycles)
+{
+    if (!w) return PROST_EINVAL;
+    if (barrier < 1 || barrier > 2 || cycles < 1 || cycles > UWAIT_LIMIT) {
+        w->err = "barrier must be 1 or 2 and cycles in 1..2e9";
+        return PROST_EINVAL;
+    }
+    w->stall_at = barrier;
+    w->stall_limit = cycles;
     return PROST_OK;
 }
 

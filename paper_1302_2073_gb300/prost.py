@@ -48,7 +48,8 @@ class prost_stats(C.Structure):
                 ("beta", C.c_double * (PROST_MAX_CG + 1)), ("pi_norm", C.c_double),
                 ("y_norm", C.c_double), ("sigma", C.c_double), ("t", C.c_double),
                 ("theta", C.c_double), ("updated", C.c_int32), ("pad0", C.c_int32),
-                ("n_foreground", C.c_int64), ("orth_err", C.c_double)]
+                ("n_foreground", C.c_int64), ("orth_err", C.c_double),
+                ("eta_norm", C.c_double), ("pi_explicit", C.c_int32), ("pad1", C.c_int32)]
 
 
 _lib = None
@@ -67,6 +68,7 @@ def lib():
         L.prost_step.argtypes = [vp, vp, C.c_int, vp, vp]
         L.prost_sync.argtypes = [vp]
         L.prost_inject_barrier_skew.argtypes = [vp, C.c_int64]
+        L.prost_inject_wait_timeout.argtypes = [vp, C.c_int32, C.c_int64]
         L.prost_get_subspace.argtypes = [vp, vp, vp, C.c_int]
         L.prost_set_subspace.argtypes = [vp, vp, vp, C.c_int]
         L.prost_set_labels.argtypes = [vp, vp, C.c_int]
@@ -110,6 +112,7 @@ def lib():
                                         P(vp)]
         L.prost_window_eval.argtypes = [vp] + [vp] * 10
         L.prost_window_ustep.argtypes = [vp, vp, vp, C.c_float, vp, vp]
+        L.prost_window_inject_wait_timeout.argtypes = [vp, C.c_int32, C.c_int64]
         L.prost_window_last_error.argtypes = [vp]
         L.prost_window_last_error.restype = C.c_char_p
         L.prost_window_destroy.argtypes = [vp]
@@ -228,6 +231,13 @@ def prost_inject_barrier_skew(h, delta):
     would (host-side injection); the next frame is refused and prost_sync
     raises PROST_ETIMEOUT, then the tracker recovers."""
     return _check(lib().prost_inject_barrier_skew(h, int(delta)), h)
+
+
+def prost_inject_wait_timeout(h, pass_index, cycles):
+    """Failure-detection tests: the next frame's grid barrier of residual
+    pass pass_index waits for an arrival that never comes and gives up after
+    `cycles` SM clock cycles (the bounded wait runs out)."""
+    return _check(lib().prost_inject_wait_timeout(h, int(pass_index), int(cycles)), h)
 
 
 def prost_get_subspace(h, U_out=None, y_out=None):
@@ -416,6 +426,12 @@ def prost_window_eval(w, U, Y, X, labels, mu, cost, dU=None, dY=None, dmu=None, 
 
 def prost_window_ustep(w, U, dU, t, U_out, status_out=None):
     return _check_win(lib().prost_window_ustep(w, _ptr(U), _ptr(dU), float(t), _ptr(U_out), _ptr(status_out)), w)
+
+
+def prost_window_inject_wait_timeout(w, barrier, cycles):
+    """Failure-detection tests: the next U-step's grid barrier `barrier` (1 or
+    2) gives up after `cycles` SM clock cycles; that U-step reports -2."""
+    return _check_win(lib().prost_window_inject_wait_timeout(w, int(barrier), int(cycles)), w)
 
 
 def prost_window_last_error(w=None):

@@ -93,8 +93,11 @@ int main(void)
     FIELD(prost_stats, pad0);
     FIELD(prost_stats, n_foreground);
     FIELD(prost_stats, orth_err);
+    FIELD(prost_stats, eta_norm);
+    FIELD(prost_stats, pi_explicit);
+    FIELD(prost_stats, pad1);
 
-    check(prost_version() == 100, "prost_version");
+    check(prost_version() == 101, "prost_version");
     check(prost_strerror(PROST_EINVAL) != NULL && strlen(prost_strerror(PROST_EINVAL)) > 0, "strerror");
     check(prost_state_bytes(&prm, &bytes) == PROST_OK, "state bytes of valid parameters");
     check(bytes > (size_t)64 * 48 * 3 * 10 * 4, "state holds at least the subspace");
@@ -110,6 +113,8 @@ int main(void)
     check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "p > 2 rejected");
     check(prost_init(NULL, NULL, NULL) == PROST_EINVAL, "prost_init without out");
     check(prost_inject_barrier_skew(NULL, 1) == PROST_EINVAL, "injection without a handle");
+    check(prost_inject_wait_timeout(NULL, 0, 1000) == PROST_EINVAL, "wait injection without a handle");
+    check(prost_window_inject_wait_timeout(NULL, 1, 1000) == PROST_EINVAL, "window wait injection without a window");
     check(prost_batch_split(10, 3, w, cap, ctas) == PROST_OK, "batch split");
     check(ctas[0] == 4 && ctas[1] == 3 && ctas[2] == 3, "batch split of 10 over thirds");
     check(prost_batch_split(2, 3, w, cap, ctas) == PROST_EINVAL, "budget below the streams");

@@ -23,7 +23,7 @@ def test_binding_covers_every_declared_symbol():
 
 
 def test_version_and_error_strings():
-    assert pg.prost_version() == 100
+    assert pg.prost_version() == 101
     assert pg.prost_strerror(pg.PROST_EBADFRAME) == "frame has a non-finite entry"
     assert pg.prost_strerror(12345) == "unknown error"
 
@@ -70,6 +70,8 @@ def test_null_arguments_are_rejected():
     assert L.prost_sync(None) == pg.PROST_EINVAL
     assert L.prost_get_stats(None, None) == pg.PROST_EINVAL
     assert L.prost_inject_barrier_skew(None, 1) == pg.PROST_EINVAL
+    assert L.prost_inject_wait_timeout(None, 0, 1000) == pg.PROST_EINVAL
+    assert L.prost_window_inject_wait_timeout(None, 1, 1000) == pg.PROST_EINVAL
     L.prost_destroy(None)
 
 

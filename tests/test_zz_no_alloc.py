@@ -1,11 +1,12 @@
-"""prost_cost_grad_static(): the entry point for callers that must not
-allocate device memory (code running under CUDA graph capture, real-time
-loops that forbid cudaMalloc after start-up, hosts whose memory belongs to
-another allocator).  It keeps its reduction scratch in a static device array
-inside the library, so it is checked here against what the allocating path
-(prost_init / prost_step) reports for the same frame: the cost and the
-gradient norm at the warm-start coefficients.  Two calls run back to back to
-show that the shared static scratch is cleared between calls.
+"""prost_cost_grad_static(): the entry point for callers that cannot
+allocate device memory (real-time loops that allow no cudaMalloc after
+start-up, because it can synchronise the device and has no latency bound;
+plug-ins whose host owns all device memory and passes them only their
+buffers).  It keeps its reduction scratch in a static device array inside the
+library, so it is checked here against what the allocating path (prost_init /
+prost_step) reports for the same frame: the cost and the gradient norm at the
+warm-start coefficients.  Two calls run back to back to show that the shared
+static scratch is cleared between calls.
 
 This file sorts last so that a run stopping at the first failure has already
 run every other test; it also passes on its own in a fresh process."""
