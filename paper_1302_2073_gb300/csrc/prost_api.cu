@@ -24,6 +24,7 @@ struct prost_handle {
     int device;
     int num_sms;
     int grid_frame, grid_gram;
+    int prefetch;          // the frame kernel bulk-prefetches its first pass (U small enough for L2)
     void *U;               // stored subspace (C x npt tile blocks of k x TILE_P float32 or bfloat16)
     uint8_t *labels;       // previous labels (Pp bytes)
     KState *ks;
@@ -154,6 +155,9 @@ size_t frame_elem_bytes(const prost_params &p) { return p.frame_dtype == PROST_U
 
 // partial rows of the widest reduction: a CG pass has k + k(k+1)/2 + 3 floats
 size_t partial_row(int k) { return (size_t)k + (size_t)k * (k + 1) / 2 + 3; }
+
+// entries per value of the frame kernel's value-major partials (16-byte loads)
+int col_stride(int grid) { return (grid + 3) / 4 * 4; }
 
 int grid_of(int occ, int sms, int64_t items)
 {
@@ -311,11 +315,21 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     if (ops->tile != TILE_P) { h->err = "tile size mismatch"; return bail(PROST_ECUDA); }
     int64_t gf = (int64_t)occ * h->num_sms;
     if (gf > dp.npt) gf = dp.npt;  // every CTA gets at least one pixel tile
+    // the cross-CTA reduction's unit sums fit its shared scratch
+    if (gf > max_frame_grid((int)partial_row(prm->k))) gf = max_frame_grid((int)partial_row(prm->k));
     h->grid_frame = (int)(gf > 0 ? gf : 1);
     h->grid_gram = grid_of(ops->gram_occupancy(), h->num_sms, (int64_t)dp.C * dp.npt * (TILE_P / ops->vw));
-    int gmax = 2 * h->grid_frame;
-    if (h->grid_gram > gmax) gmax = h->grid_gram;
-    h->partial_floats = (size_t)gmax * partial_row(prm->k);
+    {
+        // the first pass's data is prefetched into L2 when the subspace takes
+        // at most half of it, so that the later passes still find it there
+        int l2 = 0;
+        CKI(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device));
+        const size_t ub = (size_t)prm->k * dp.C * dp.Pp * u_elem_bytes(dp);
+        h->prefetch = l2 > 0 && ub <= (size_t)l2 / 2 ? 1 : 0;
+    }
+    // the Gram kernel's rows, or the frame kernel's two value-major buffers
+    h->partial_floats = std::max((size_t)h->grid_gram * partial_row(prm->k),
+                                 (size_t)2 * col_stride(h->grid_frame) * partial_row(prm->k));
 
     CKI(cudaMalloc(&h->U, (size_t)prm->k * dp.C * dp.Pp * u_elem_bytes(dp)));
     CKI(cudaMalloc(&h->labels, (size_t)dp.Pp));
@@ -390,11 +404,12 @@ int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_
     fa.bar = h->bar;
     fa.bar_base = h->bar_base;
     fa.frame_pitch = pitch;
-    fa.row_stride = (int)partial_row(h->prm.k);
+    fa.col_stride = col_stride(h->grid_frame);
     fa.grid = h->grid_frame;
     fa.stall_at = h->stall_at;
     fa.stall_limit = h->stall_limit;
     h->stall_at = 0; // one launch only
+    fa.prefetch = h->prefetch;
     fa.prm = dp;
     if (h->timing) CK(h, cudaEventRecord(h->ev[0], h->stream));
     CK(h, h->ops->frame(fa, fdt, h->grid_frame, h->stream));
@@ -845,7 +860,7 @@ int plan_ctas(prost_batch *b)
     }
     // partial-row space: every stream's handle holds rows for its own grid
     for (size_t s = 0; s < b->h.size(); ++s)
-        if ((size_t)2 * b->grid[s] * partial_row(b->h[s]->prm.k) > b->h[s]->partial_floats)
+        if ((size_t)2 * col_stride(b->grid[s]) * partial_row(b->h[s]->prm.k) > b->h[s]->partial_floats)
             return bfail(b, PROST_EINVAL, "partial rows");
     return PROST_OK;
 }
@@ -984,7 +999,7 @@ extern "C" int prost_batch_step(prost_batch *b, const void *const *frames, uint8
         fa.bar = h->bar;
         fa.bar_base = h->bar_base;
         fa.frame_pitch = dp.P;
-        fa.row_stride = (int)partial_row(h->prm.k);
+        fa.col_stride = col_stride(b->grid[s]);
         fa.grid = b->grid[s];
         fa.prm = dp;
         h->bar_base += (unsigned long long)b->grid[s] * (unsigned long long)frame_arrivals(h->prm.n_cg);

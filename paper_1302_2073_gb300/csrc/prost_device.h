@@ -12,6 +12,14 @@ constexpr int CGMAX = 32;    // largest number of CG iterations per frame
 constexpr int THREADS = 256; // threads per CTA of the Gram and layout kernels
 constexpr int TILE_P = 224;  // pixels per tile of the stored subspace (16-byte multiple for uint8)
 
+// Cross-CTA reductions (reduce_rows, reduce_cols): rows per unit, one batch
+// of loads; floats of the per-unit sums in shared memory.  reduce_cols needs
+// ceil(grid / RED_ROWS) * values <= RED_SCR, which the host keeps by capping
+// the frame kernel's grid (max_frame_grid).
+constexpr int RED_ROWS = 24;
+constexpr int RED_SCR = 1280;
+__host__ __device__ constexpr int max_frame_grid(int nv) { return RED_SCR / nv * RED_ROWS; }
+
 // Grid-barrier arrivals of every frame-kernel CTA per frame: one per residual
 // pass (n_cg + 1), one for the projection pass (made at the end of the frame
 // when that pass does not run) and one at the end of the frame.
@@ -108,17 +116,18 @@ struct FrameArgs {
     uint8_t *mask_out;        // optional copy of the labels (device, P bytes)
     float *bg_out;            // optional background U y + in_offset (device, m floats)
     KState *ks;
-    float *partials;          // 2 x gridDim.x rows of row_stride floats
+    float *partials;          // 2 buffers, each value-major: value c of CTA b at [c * col_stride + b]
     GridBar *bar;
     unsigned long long bar_base; // bar->count at launch
     int64_t frame_pitch;
-    int row_stride;
+    int col_stride;           // entries per value: the grid size rounded up to a multiple of 4
     int grid;                 // CTAs working on this stream (its grid barrier's size)
     // failure-detection tests only (0 = off): at the grid barrier of residual
     // pass stall_at - 1 wait for one arrival more than any launch makes,
     // giving up after stall_limit SM clock cycles
     int stall_at;
     long long stall_limit;
+    int prefetch;             // register form: bulk-prefetch the first pass's data into L2
     DevParams prm;
 };
 

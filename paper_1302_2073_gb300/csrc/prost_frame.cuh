@@ -133,8 +133,6 @@ template <int K> struct SKState {
 // flight at a time, and the ng group sums of each value are added in group
 // order.  One out-of-line body serves every pass of the frame, so the code the
 // last CTA runs at the end of the frame is already in the instruction caches.
-constexpr int RED_ROWS = 24;  // rows per unit (one batch of loads)
-constexpr int RED_SCR = 1280; // floats of group sums (>= NCONS)
 
 __device__ __forceinline__ void kahan_add(float &s, float &c, float v)
 {
@@ -208,9 +206,53 @@ __device__ __noinline__ void reduce_rows(const float *rows, int nrows, int strid
     cons_sync<NCONS>();
 }
 
-// CTA sum of N per-thread values (all threads), first nv written to out
+// Sum of all CTAs' partial values in a fixed order (Kahan-compensated FP32),
+// by the NCONS threads of the CTA, identical in every CTA, for the frame
+// kernel's value-major layout: value c of CTA b at cols[c * cstride + b]
+// (cstride a multiple of 4, at least nrows).  A unit (value c, chunk q) sums
+// rows [q RED_ROWS, (q + 1) RED_ROWS) of one value with 16-byte loads, a
+// load only where it starts below nrows (so it ends inside the value's
+// cstride entries); units of one value are then added in chunk order.
+template <int NCONS>
+__device__ __noinline__ void reduce_cols(const float *cols, int nrows, int cstride, int nv, float *tot, float *scr)
+{
+    static_assert(RED_ROWS % 4 == 0, "whole 16-byte loads per chunk");
+    const int t = threadIdx.x;
+    const int nq = (nrows + RED_ROWS - 1) / RED_ROWS;
+    const int nu = nq * nv; // unit u = c nq + q
+    for (int u = t; u < nu; u += NCONS) {
+        const int c = u / nq, q = u - c * nq;
+        const int r0 = q * RED_ROWS;
+        const float4 *p = reinterpret_cast<const float4 *>(cols + (size_t)c * cstride + r0);
+        float4 v[RED_ROWS / 4];
+#pragma unroll
+        for (int i = 0; i < RED_ROWS / 4; ++i)
+            v[i] = r0 + 4 * i < nrows ? __ldcg(p + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float s = 0.f, k = 0.f;
+#pragma unroll
+        for (int i = 0; i < RED_ROWS / 4; ++i) {
+            const int r = r0 + 4 * i;
+            kahan_add(s, k, r < nrows ? v[i].x : 0.f);
+            kahan_add(s, k, r + 1 < nrows ? v[i].y : 0.f);
+            kahan_add(s, k, r + 2 < nrows ? v[i].z : 0.f);
+            kahan_add(s, k, r + 3 < nrows ? v[i].w : 0.f);
+        }
+        scr[u] = s;
+    }
+    cons_sync<NCONS>();
+    for (int c = t; c < nv; c += NCONS) {
+        float s = 0.f, k = 0.f;
+        for (int q = 0; q < nq; ++q) kahan_add(s, k, scr[c * nq + q]);
+        tot[c] = s;
+    }
+    cons_sync<NCONS>();
+}
+
+// CTA sum of N per-thread values (all threads), the first nv written to
+// out[i * os].  The grid barrier that follows orders these stores before
+// its arrival (CTA barrier, then one fence by the arriving thread).
 template <int N, int NCW>
-__device__ __forceinline__ void cons_partials(float (&v)[N], int nv, float *out, float *sred)
+__device__ __forceinline__ void cons_partials(float (&v)[N], int nv, float *out, float *sred, int os)
 {
     warp_split_reduce<N>(v);
     constexpr int PER = N / 32;
@@ -222,16 +264,15 @@ __device__ __forceinline__ void cons_partials(float (&v)[N], int nv, float *out,
         float a = 0.f;
 #pragma unroll
         for (int ww = 0; ww < NCW; ++ww) a += sred[ww * N + i];
-        out[i] = a;
+        out[(size_t)i * os] = a;
     }
-    __threadfence();
 }
 
 // As cons_partials, with a plain shuffle tree per value (static indices
 // only): for the streaming form's long per-lane vectors, where the lane-
 // dependent selects of the split reduction would put the vector in local memory.
 template <int N, int NCW, int NA, int S0 = 0, int S1 = 0>
-__device__ __forceinline__ void cons_partials_tree(float (&v)[NA], int nv, float *out, float *sred)
+__device__ __forceinline__ void cons_partials_tree(float (&v)[NA], int nv, float *out, float *sred, int os)
 {
     static_assert(N <= NA, "values beyond the array");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -249,16 +290,15 @@ __device__ __forceinline__ void cons_partials_tree(float (&v)[NA], int nv, float
         float a = 0.f;
 #pragma unroll
         for (int ww = 0; ww < NCW; ++ww) a += sred[ww * N + i];
-        out[i] = a;
+        out[(size_t)i * os] = a;
     }
-    __threadfence();
 }
 
 // The warps' 16 x 16 tensor-core results (at res_off in each warp's shared
 // memory, warp_bytes apart) summed in a fixed order into the packed upper
 // triangle out[0 .. K(K+1)/2).
 template <int K, int NCW>
-__device__ __forceinline__ void mma_row(const unsigned char *base, int warp_bytes, int res_off, float *out)
+__device__ __forceinline__ void mma_row(const unsigned char *base, int warp_bytes, int res_off, float *out, int os)
 {
     cons_sync<NCW * 32>(); // every warp has stored its result
     constexpr int NM = K * (K + 1) / 2;
@@ -271,9 +311,8 @@ __device__ __forceinline__ void mma_row(const unsigned char *base, int warp_byte
         const int l = j + t;
         float a = 0.f;
         for (int w = 0; w < NCW; ++w) a += reinterpret_cast<const float *>(base + w * warp_bytes + res_off)[j * 16 + l];
-        out[i] = a;
+        out[(size_t)i * os] = a;
     }
-    __threadfence();
 }
 
 // Grid barrier: arrive, wait (bounded) until all CTAs arrived.
@@ -287,6 +326,7 @@ __device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target
     if (threadIdx.x == 0) {
         int ok = *s_err == 0;
         if (ok) {
+            __threadfence(); // the CTA's partial values (ordered by the CTA barrier) before the arrival
             atomicAdd(&gb->count, 1ull);
             const long long t0 = clock64();
             unsigned it = 0;
@@ -386,9 +426,11 @@ __device__ void kspace_cg(SKState<K> &sk, const DevParams &prm, const float *tot
         if (l == 0) sk.skip = 1;
         __syncwarp();
     }
+    // g = T^T g_st (T upper triangular): every product issued at once
     float gl = 0.f;
-    if (act)
-        for (int i = 0; i <= l; ++i) gl = fmaf(sk.Tf[i * K + l], tot[i], gl);
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+        if (act && i <= l) gl = fmaf(sk.Tf[i * K + l], tot[i], gl);
     const float gsq = wsumf(act ? gl * gl : 0.f);
     float beta = 0.f, dl;
     if (pass == 0) {
@@ -407,7 +449,8 @@ __device__ void kspace_cg(SKState<K> &sk, const DevParams &prm, const float *tot
     }
     if (sk.skip) return;
     if (pass < prm.n_cg) {
-        float dst = 0.f;
+        const float dg = wsumf(act ? dl * gl : 0.f);
+        float dst = 0.f; // (T d)_l, the direction in the stored basis
 #pragma unroll
         for (int i = 0; i < K; ++i) {
             const float di = __shfl_sync(FULL, dl, i);
@@ -422,21 +465,13 @@ __device__ void kspace_cg(SKState<K> &sk, const DevParams &prm, const float *tot
             }
         }
         const float den = prm.p * wsumf(act ? dst * md : 0.f);
-        const float dg = wsumf(act ? dl * gl : 0.f);
         const float alpha = den > 0.f ? -dg / den : 0.f;
-        const double yl = act ? sk.y[l] + (double)alpha * (double)dl : 0.0;
-        const float ylf = (float)yl;
-        float ys = 0.f;
-#pragma unroll
-        for (int i = 0; i < K; ++i) {
-            const float yi = __shfl_sync(FULL, ylf, i);
-            if (act && i >= l) ys = fmaf(sk.Tf[l * K + i], yi, ys);
-        }
         if (act) {
-            sk.y[l] = yl;
+            // y in FP64; the stored-basis coefficients T y move along T d
+            sk.y[l] = fma((double)alpha, (double)dl, sk.y[l]);
+            sk.yf[l] = fmaf(alpha, dst, sk.yf[l]);
             sk.d[l] = dl;
             sk.gprev[l] = gl;
-            sk.yf[l] = ys;
         }
         if (stats && l == 0) gks->alpha[pass] = alpha;
     } else {
@@ -933,6 +968,42 @@ __device__ __forceinline__ void proj_pass(const FrameArgs &a, const FrameTiles &
     }
 }
 
+// Prefetch into L2 of what this CTA's first residual pass reads (register
+// form, when the host found the subspace small enough to stay in L2): its
+// tiles of the stored subspace, and the frame entries and labels of the same
+// tiles.  Every thread issues non-blocking line prefetches (one per 128-byte
+// line) before its first loads, so the whole range streams from HBM at once
+// and the pass's loads then find their lines in L2.  Every prefetched
+// address lies inside its buffer.
+__device__ __forceinline__ void prefetch_line(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+template <int K, typename FT, typename UT>
+__device__ __forceinline__ void prefetch_first_pass(const FrameArgs &a, const FrameTiles &tl, int nthreads)
+{
+    if (tl.nres <= 0) return;
+    const DevParams &prm = a.prm;
+    const char *ub = static_cast<const char *>(a.U) + (size_t)tl.r0 * K * TILE_P * sizeof(UT);
+    const int ulines = (int)(((size_t)tl.nres * K * TILE_P * sizeof(UT) + 127) / 128);
+    for (int q = threadIdx.x; q < ulines; q += nthreads) prefetch_line(ub + (size_t)q * 128);
+    // frame and label tiles, one channel plane at a time
+    const int ti1 = tl.r0 + tl.nres - 1;
+    const int c0 = tl.r0 / prm.npt, c1 = ti1 / prm.npt;
+    for (int c = c0; c <= c1; ++c) {
+        const int pa = c == c0 ? tl.r0 - c0 * prm.npt : 0;
+        const int pb = c == c1 ? ti1 - c1 * prm.npt : prm.npt - 1;
+        const char *fb = static_cast<const char *>(a.frame) + (size_t)c * a.frame_pitch * sizeof(FT);
+        const size_t f0 = (size_t)pa * TILE_P * sizeof(FT);
+        const size_t fend = min((size_t)(pb + 1) * TILE_P, (size_t)prm.P) * sizeof(FT);
+        for (size_t o = f0 + (size_t)threadIdx.x * 128; o < fend; o += (size_t)nthreads * 128) prefetch_line(fb + o);
+        const size_t l1 = (size_t)(pb + 1) * TILE_P;
+        for (size_t o = (size_t)pa * TILE_P + (size_t)threadIdx.x * 128; o < l1; o += (size_t)nthreads * 128)
+            prefetch_line(a.labels + o);
+    }
+}
+
 // The frame of one stream, by CTA b of the G CTAs working on it.
 template <int K, typename FT, typename UT>
 __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, const int b)
@@ -976,6 +1047,9 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         }
         return;
     }
+    if constexpr (!F::STREAM) {
+        if (a.prefetch) prefetch_first_pass<K, FT, UT>(a, tl, NT);
+    }
 
     const bool stats = b == 0;
     using SC = StageCfg<K, FT, UT>;
@@ -987,8 +1061,9 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     if (stats && tid == 0) a.ks->phase_ts[0] = global_ns();
 
     for (int pass = 0; pass <= prm.n_cg; ++pass) {
-        float *row = a.partials + ((size_t)buf * G + b) * a.row_stride;
-        const float *rows = a.partials + (size_t)buf * G * a.row_stride;
+        const int cs = a.col_stride;
+        const float *cols = a.partials + (size_t)buf * F::NVR * cs;
+        float *col = const_cast<float *>(cols) + b;
         target += (unsigned long long)G;
         if (pass < prm.n_cg) {
             const bool trace = stats && tid == 0 && pass == 1;
@@ -1001,19 +1076,19 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 residual_pass<K, FT, UT, true>(a, tl, sk, acc, 0);
             if (trace) a.ks->sub_ts[0] = global_ns();
             if constexpr (F::STREAM && SC::TC) {
-                cons_partials_tree<F::NVR, NW, F::NPR, K, K + NM>(acc, F::NVR, row, sred);
-                mma_row<K, NW>(sbase, SC::WARP_B, RES_OFF, row + K);
+                cons_partials_tree<F::NVR, NW, F::NPR, K, K + NM>(acc, F::NVR, col, sred, cs);
+                mma_row<K, NW>(sbase, SC::WARP_B, RES_OFF, col + (size_t)K * cs, cs);
             } else if constexpr (F::STREAM) {
-                cons_partials_tree<F::NVR, NW>(acc, F::NVR, row, sred);
+                cons_partials_tree<F::NVR, NW>(acc, F::NVR, col, sred, cs);
             } else {
-                cons_partials<F::NPR, NW>(acc, F::NVR, row, sred);
+                cons_partials<F::NPR, NW>(acc, F::NVR, col, sred, cs);
             }
             if (trace) a.ks->sub_ts[1] = global_ns();
             if (!grid_wait<NT>(a.bar, target + (pass + 1 == a.stall_at ? 1ull : 0ull), &sk.err, a.ks,
                                pass + 1 == a.stall_at ? a.stall_limit : WAIT_LIMIT))
                 return;
             if (trace) a.ks->sub_ts[2] = global_ns();
-            reduce_rows<NT>(rows, G, a.row_stride, F::NVR, tot, rscr);
+            reduce_cols<NT>(cols, G, cs, F::NVR, tot, rscr);
             if (trace) a.ks->sub_ts[3] = global_ns();
             if (warp == 0) kspace_cg<K, true>(sk, prm, tot, pass, a.ks, stats);
             if (trace) a.ks->sub_ts[4] = global_ns();
@@ -1026,13 +1101,13 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             else
                 residual_pass<K, FT, UT, false>(a, tl, sk, acc, 0);
             if constexpr (F::STREAM)
-                cons_partials_tree<F::NVF, NW>(acc, F::NVF, row, sred);
+                cons_partials_tree<F::NVF, NW>(acc, F::NVF, col, sred, cs);
             else
-                cons_partials<F::NPF, NW>(acc, F::NVF, row, sred);
+                cons_partials<F::NPF, NW>(acc, F::NVF, col, sred, cs);
             if (!grid_wait<NT>(a.bar, target + (pass + 1 == a.stall_at ? 1ull : 0ull), &sk.err, a.ks,
                                pass + 1 == a.stall_at ? a.stall_limit : WAIT_LIMIT))
                 return;
-            reduce_rows<NT>(rows, G, a.row_stride, F::NVF, tot, rscr);
+            reduce_cols<NT>(cols, G, cs, F::NVF, tot, rscr);
             if (warp == 0) kspace_cg<K, false>(sk, prm, tot, pass, a.ks, stats);
         }
         cons_sync<NT>();
@@ -1043,24 +1118,24 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     // ---- |pi(eta)| by the explicit projection pass, where the norm identity
     // of the final pass cancels (the same decision in every CTA) ----
     if (sk.proj) {
-        float *prow = a.partials + ((size_t)buf * G + b) * a.row_stride;
-        const float *prows = a.partials + (size_t)buf * G * a.row_stride;
+        const float *pcols = a.partials + (size_t)buf * F::NVR * a.col_stride;
         target += (unsigned long long)G;
         float acc1[1] = {0.f};
         if constexpr (F::STREAM)
             stream_residual<K, FT, UT, false, NW, 1, true>(a, tl.r0, tl.nres, sk.yf, wstage, acc1, sk.tg);
         else
             proj_pass<K, FT, UT>(a, tl, sk, acc1[0]);
-        cons_partials_tree<1, NW, 1>(acc1, 1, prow, sred);
+        cons_partials_tree<1, NW, 1>(acc1, 1, const_cast<float *>(pcols) + b, sred, a.col_stride);
         if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
-        reduce_rows<NT>(prows, G, a.row_stride, 1, tot, rscr);
+        reduce_cols<NT>(pcols, G, a.col_stride, 1, tot, rscr);
         if (tid == 0) step_angle(sk, prm, sqrtf(fmaxf(tot[0], 0.f)), a.ks, stats);
         cons_sync<NT>();
         buf ^= 1;
     }
 
     // ---- update pass: Step 2 on every row, Step 3 labels, Gram of the new rows ----
-    float *row = a.partials + ((size_t)buf * G + b) * a.row_stride;
+    const float *ucols = a.partials + (size_t)buf * F::NVR * a.col_stride;
+    float *ucol = const_cast<float *>(ucols) + b;
     if constexpr (F::STREAM) {
         float acc[F::NPU];
 #pragma unroll
@@ -1077,10 +1152,10 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         stream_update<K, FT, UT, NW>(a, tl.u0, tl.nupt, kv, sk.cm1, sk.snp, sk.yn, !sk.skip, sr_key, wstage, acc);
         if (tid == 0 && stats) a.ks->sub_ts[5] = global_ns();
         if constexpr (SC::TC) {
-            cons_partials_tree<F::NVU, NW, F::NPU, 0, NM>(acc, F::NVU, row, sred);
-            mma_row<K, NW>(sbase, SC::WARP_B, RES_OFF, row);
+            cons_partials_tree<F::NVU, NW, F::NPU, 0, NM>(acc, F::NVU, ucol, sred, a.col_stride);
+            mma_row<K, NW>(sbase, SC::WARP_B, RES_OFF, ucol, a.col_stride);
         } else {
-            cons_partials_tree<F::NVU, NW>(acc, F::NVU, row, sred);
+            cons_partials_tree<F::NVU, NW>(acc, F::NVU, ucol, sred, a.col_stride);
         }
     } else {
     float acc[F::NPU];
@@ -1196,7 +1271,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         }
     }
     if (tid == 0 && stats) a.ks->sub_ts[5] = global_ns();
-    cons_partials<F::NPU, NW>(acc, F::NVU, row, sred);
+    cons_partials<F::NPU, NW>(acc, F::NVU, ucol, sred, a.col_stride);
     }
     cons_sync<NT>();
     if (tid == 0 && stats) a.ks->sub_ts[6] = global_ns();
@@ -1204,6 +1279,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         // every CTA arrives FRAME_ARRIVALS(n_cg) times per frame: once per
         // residual pass, once at the projection barrier (counted here when that
         // pass did not run) and once here; the last arrival of all is here
+        __threadfence(); // the CTA's partial values before the arrival
         const unsigned long long inc = sk.proj ? 1ull : 2ull;
         const unsigned long long old = atomicAdd(&a.bar->count, inc);
         sk.last = old + inc == a.bar_base + (unsigned long long)G * (unsigned long long)frame_arrivals(prm.n_cg);
@@ -1212,7 +1288,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     cons_sync<NT>();
     if (tid == 0 && stats) a.ks->sub_ts[7] = global_ns();
     if (!sk.last) return;
-    reduce_rows<NT>(a.partials + (size_t)buf * G * a.row_stride, G, a.row_stride, F::NVU, tot, rscr);
+    reduce_cols<NT>(ucols, G, a.col_stride, F::NVU, tot, rscr);
     if (tid == 0) a.ks->sub_ts[8] = global_ns();
     end_frame<K, NT>(sk, a.ks, tot, tot[NM], rs);
     if (tid == 0) a.ks->sub_ts[9] = global_ns();

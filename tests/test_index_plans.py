@@ -35,8 +35,10 @@ DEVICE_H, FRAME_CUH, API_CU, WINDOW_CU = (_src(n) for n in ("prost_device.h", "p
                                                           "prost_window.cu"))
 TILE_P = _const(DEVICE_H, r"constexpr int TILE_P = (\d+);")
 RW = _const(FRAME_CUH, r"static constexpr int RW = (\d+);")
-RED_ROWS = _const(FRAME_CUH, r"constexpr int RED_ROWS = (\d+);")
-RED_SCR = _const(FRAME_CUH, r"constexpr int RED_SCR = (\d+);")
+RED_ROWS = _const(DEVICE_H, r"constexpr int RED_ROWS = (\d+);")
+RED_SCR = _const(DEVICE_H, r"constexpr int RED_SCR = (\d+);")
+assert "constexpr int max_frame_grid(int nv) { return RED_SCR / nv * RED_ROWS; }" in DEVICE_H
+assert "int col_stride(int grid) { return (grid + 3) / 4 * 4; }" in API_CU
 WT = _const(WINDOW_CU, r"constexpr int WT = (\d+);")
 KMAXW = _const(WINDOW_CU, r"constexpr int KMAXW = (\d+);")
 IPT = TILE_P // RW
@@ -61,9 +63,10 @@ def npt_of(P):
     return (P + TILE_P - 1) // TILE_P
 
 
-def frame_grid(P, sms=SMS, occ=1):
-    """The frame kernel's grid: one CTA per SM, at most one per pixel tile."""
-    return max(1, min(occ * sms, npt_of(P)))
+def frame_grid(P, sms=SMS, occ=1, k=1):
+    """The frame kernel's grid: one CTA per SM, at most one per pixel tile,
+    at most what the reduction's scratch takes."""
+    return max(1, min(occ * sms, npt_of(P), RED_SCR // partial_row(k) * RED_ROWS))
 
 
 def frame_tiles(C, npt, G, b):
@@ -218,6 +221,47 @@ def test_reduce_rows_plan_sums_every_value_of_every_row_once(ncons, stride, nv):
         assert (seen == 1).all()
         # the final sums read scr[g*nv + c], g < ng: exactly the units written
         assert sorted(g * nv + c for c in range(nv) for g in range(ng)) == list(range(nu))
+
+
+def _cols_cases():
+    cases = set()
+    for k in range(1, 17):
+        for bf16 in (False, True):
+            for nv in (k + k * (k + 1) // 2 + 3, k + 3, k * (k + 1) // 2 + 1, 1):
+                cases.add((threads(k, bf16), partial_row(k), nv))
+    return sorted(cases)
+
+
+@pytest.mark.parametrize("ncons,nvmax,nv", _cols_cases())
+def test_reduce_cols_plan_sums_every_value_of_every_cta_once(ncons, nvmax, nv):
+    """reduce_cols: value c of CTA b at c * cstride + b, cstride = the grid
+    rounded up to 4; unit u = c nq + q sums rows [q RED_ROWS, (q+1) RED_ROWS)
+    with 16-byte loads, each issued only where it starts below nrows."""
+    assert RED_ROWS % 4 == 0
+    for nrows in sorted({1, 2, 3, 4, 5, 23, 24, 25, 76, 151, 152, SMS, RED_SCR // nvmax * RED_ROWS}):
+        if nrows > RED_SCR // nvmax * RED_ROWS:
+            continue
+        cs = (nrows + 3) // 4 * 4
+        nq = -(-nrows // RED_ROWS)
+        nu = nq * nv
+        assert nu <= RED_SCR                                   # the unit sums fit the scratch
+        buf = nvmax * cs                                       # one buffer of the frame kernel
+        seen = np.zeros((nv, nrows), np.int64)
+        for u in range(nu):
+            c, q = divmod(u, nq)
+            r0 = q * RED_ROWS
+            for i in range(RED_ROWS // 4):
+                r = r0 + 4 * i
+                if r >= nrows:
+                    continue
+                off = c * cs + r
+                assert off % 4 == 0 and off + 3 < (c + 1) * cs <= buf  # inside the value's entries
+                for j in range(4):
+                    if r + j < nrows:
+                        seen[c, r + j] += 1
+        assert (seen == 1).all()
+        # the per-value sums read scr[c nq + q], exactly the units written
+        assert sorted(c * nq + q for c in range(nv) for q in range(nq)) == list(range(nu))
 
 
 # ---- the streaming form's staging plan (prost_stage.cuh) -----------------------
