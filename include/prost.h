@@ -79,6 +79,19 @@ extern "C" {
 #define PROST_MASK_POST_UPDATE 0 /* Step 3 uses the subspace after Step 2 (default) */
 #define PROST_MASK_PRE_UPDATE 1  /* Step 3 uses the subspace before Step 2 */
 
+/* Kernel forms of a frame (not in the paper; the results agree within the
+ * parity tolerances, the summation orders differ).  GRID: one cooperative
+ * launch of one CTA per SM with bounded grid barriers in global memory.
+ * CLUSTER: one thread-block cluster of up to 16 CTAs whose barriers are the
+ * hardware cluster barrier, for small subspaces where the grid barriers of
+ * many CTAs would cost more than the streaming.  AUTO picks CLUSTER when the
+ * stored subspace takes at most PROST_CLUSTER_MAX_U_BYTES and a cluster fits
+ * the device, else GRID.  Failure injection (prost_inject_*) needs GRID. */
+#define PROST_FORM_AUTO 0
+#define PROST_FORM_GRID 1
+#define PROST_FORM_CLUSTER 2
+#define PROST_CLUSTER_MAX_U_BYTES (1u << 20)
+
 #define PROST_MAX_K 16
 #define PROST_MAX_CG 32
 
@@ -98,7 +111,7 @@ typedef struct prost_params {
     int32_t frame_dtype;             /* PROST_U8 or PROST_F32 */
     int32_t u_dtype;                 /* PROST_F32 or PROST_BF16 (subspace storage) */
     int32_t mask_from;               /* PROST_MASK_POST_UPDATE or PROST_MASK_PRE_UPDATE */
-    int32_t reserved;                /* must be 0 */
+    int32_t form;                    /* kernel form: PROST_FORM_AUTO (0), PROST_FORM_GRID or PROST_FORM_CLUSTER */
     uint64_t seed;                   /* seed of the random initial subspace (Section 3.4) */
 } prost_params;
 
@@ -126,7 +139,7 @@ typedef struct prost_stats {
                                         by an extra pass over U: the identity
                                         |pi(eta)|^2 = |eta|^2 - |U^T eta|^2 (Eq. gproject)
                                         loses its digits when |pi(eta)|^2 < |eta|^2 / 4 */
-    int32_t pad1;
+    int32_t form;                    /* PROST_FORM_GRID or PROST_FORM_CLUSTER: the handle's frame kernel */
 } prost_stats;
 
 /* Sizes of the device state of a handle with these parameters (bytes, device
@@ -156,6 +169,24 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out);
 int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_out,
                float *background_out);
 
+/* Pipelined host frames (not in the paper).  prost_step_async() enqueues one
+ * frame from host memory and returns without waiting: the frame is copied in
+ * on a copy stream of the handle while the previous frame's kernel runs, the
+ * frame's kernel runs on the handle's stream, and its labels (mask_out, P
+ * bytes, nullable) and background (background_out, m floats, nullable) are
+ * copied out on a second copy stream while the next frame's kernel runs.  All
+ * three buffers are host memory that must stay valid, and frame unchanged,
+ * until prost_wait() has returned this frame; page-locked memory lets the
+ * copies overlap the kernels.  At most two frames are in flight: a third call
+ * returns PROST_EINVAL.  prost_wait() waits for the oldest frame in flight and
+ * returns its status (PROST_OK, PROST_EBADFRAME, PROST_ETIMEOUT or
+ * PROST_ENOTSPD; PROST_EINVAL when none is in flight); the outputs of a frame
+ * whose status is not PROST_OK or PROST_ENOTSPD hold no meaningful values.
+ * prost_step() refuses (PROST_EINVAL) while such frames are in flight; the
+ * other calls work on the handle's stream, ordered after the kernels. */
+int prost_step_async(prost_handle *h, const void *frame, uint8_t *mask_out, float *background_out);
+int prost_wait(prost_handle *h);
+
 /* Synchronise the handle's stream.  Returns PROST_EBADFRAME if a frame was
  * skipped since the previous prost_sync(), PROST_ENOTSPD / PROST_ETIMEOUT if
  * one of those was raised, else PROST_OK, and clears these flags. */
@@ -166,7 +197,8 @@ int prost_sync(prost_handle *h);
  * that gave up part-way leaves it.  The next frame launch finds the count
  * outside the range it expects and returns at once, leaving the state
  * untouched; on the host path prost_step() returns PROST_ETIMEOUT and leaves
- * its outputs unwritten.  The following prost_sync() reports PROST_ETIMEOUT
+ * its outputs unwritten.  Grid form only (PROST_EINVAL for the cluster form,
+ * which has no software barrier).  The following prost_sync() reports PROST_ETIMEOUT
  * and resets the barrier, and later frames run normally (the refused frame
  * does not count towards the periodic rebase).  A launch can only detect a
  * backward skew (delta < 0) or a forward one of at least the frame kernel's
@@ -182,8 +214,9 @@ int prost_inject_barrier_skew(prost_handle *h, int64_t delta);
  * second).  The bounded wait then runs out as it would on a stalled GPU: the
  * frame aborts with the state untouched (U, y, labels, frame counter), on the
  * host path prost_step() returns PROST_ETIMEOUT, and prost_sync() reports
- * PROST_ETIMEOUT and resets the barrier.  Applies to one launch.  Errors:
- * PROST_EINVAL (NULL handle, pass or cycles out of range). */
+ * PROST_ETIMEOUT and resets the barrier.  Applies to one launch.  Grid form
+ * only.  Errors: PROST_EINVAL (NULL handle, pass or cycles out of range, the
+ * cluster form). */
 int prost_inject_wait_timeout(prost_handle *h, int32_t pass, int64_t cycles);
 
 /* Copy out the current subspace (the re-orthonormalised representative,

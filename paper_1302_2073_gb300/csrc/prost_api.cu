@@ -24,7 +24,7 @@ struct prost_handle {
     int device;
     int num_sms;
     int grid_frame, grid_gram;
-    int prefetch;          // the frame kernel bulk-prefetches its first pass (U small enough for L2)
+    int cluster_grid;      // > 0: the frame kernel runs as one cluster of this many CTAs
     void *U;               // stored subspace (C x npt tile blocks of k x TILE_P float32 or bfloat16)
     uint8_t *labels;       // previous labels (Pp bytes)
     KState *ks;
@@ -40,6 +40,17 @@ struct prost_handle {
     size_t partial_floats;
     int stall_at;          // armed for the next frame by prost_inject_wait_timeout (0 = off)
     long long stall_limit;
+    // pipelined host frames (prost_step_async / prost_wait): two slots, each
+    // with device staging of its frame, labels and background, and status words
+    cudaStream_t s_in, s_out;     // host-to-device and device-to-host copy streams
+    void *af_buf[2];
+    uint8_t *am_buf[2];
+    float *ab_buf[2];
+    int32_t *ast_dev;             // 2 device status words
+    int32_t *ast_host;            // 2 pinned status words
+    cudaEvent_t ev_in[2], ev_done[2], ev_out[2];
+    int a_head, a_count;          // oldest slot in flight, frames in flight
+    int a_used[2];                // the slot has carried a frame (its events are recorded)
     int timing;            // record events around every kernel of prost_step()
     int timed_frames;      // traced frames since timing was enabled
     cudaEvent_t ev[CGMAX + 3];
@@ -124,7 +135,7 @@ int check_params(const prost_params *prm, DevParams *dp, std::string *why)
     if (p.frame_dtype != PROST_U8 && p.frame_dtype != PROST_F32) { *why = "frame_dtype must be PROST_U8 or PROST_F32"; return PROST_EINVAL; }
     if (p.u_dtype != PROST_F32 && p.u_dtype != PROST_BF16) { *why = "u_dtype must be PROST_F32 or PROST_BF16"; return PROST_EINVAL; }
     if (p.mask_from != PROST_MASK_POST_UPDATE && p.mask_from != PROST_MASK_PRE_UPDATE) { *why = "mask_from must be 0 or 1"; return PROST_EINVAL; }
-    if (p.reserved != 0) { *why = "reserved must be 0"; return PROST_EINVAL; }
+    if (p.form != PROST_FORM_AUTO && p.form != PROST_FORM_GRID && p.form != PROST_FORM_CLUSTER) { *why = "form must be PROST_FORM_AUTO, PROST_FORM_GRID or PROST_FORM_CLUSTER"; return PROST_EINVAL; }
     if (dp) {
         memset(dp, 0, sizeof(*dp));
         dp->P = P;
@@ -179,6 +190,21 @@ void free_state(prost_handle *h)
     if (h->bg_buf) cudaFree(h->bg_buf);
     if (h->u_buf) cudaFree(h->u_buf);
     if (h->h_word) cudaFreeHost(h->h_word);
+    for (int i = 0; i < 2; ++i) {
+        if (h->af_buf[i]) cudaFree(h->af_buf[i]);
+        if (h->am_buf[i]) cudaFree(h->am_buf[i]);
+        if (h->ab_buf[i]) cudaFree(h->ab_buf[i]);
+        if (h->ev_in[i]) cudaEventDestroy(h->ev_in[i]);
+        if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
+        if (h->ev_out[i]) cudaEventDestroy(h->ev_out[i]);
+        h->af_buf[i] = nullptr; h->am_buf[i] = nullptr; h->ab_buf[i] = nullptr;
+        h->ev_in[i] = h->ev_done[i] = h->ev_out[i] = nullptr;
+    }
+    if (h->ast_dev) cudaFree(h->ast_dev);
+    if (h->ast_host) cudaFreeHost(h->ast_host);
+    if (h->s_in) cudaStreamDestroy(h->s_in);
+    if (h->s_out) cudaStreamDestroy(h->s_out);
+    h->ast_dev = nullptr; h->ast_host = nullptr; h->s_in = h->s_out = nullptr;
     for (int i = 0; i < CGMAX + 3; ++i)
         if (h->ev[i]) cudaEventDestroy(h->ev[i]);
     for (int i = 0; i < CGMAX + 3; ++i) h->ev[i] = nullptr;
@@ -319,13 +345,22 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     if (gf > max_frame_grid((int)partial_row(prm->k))) gf = max_frame_grid((int)partial_row(prm->k));
     h->grid_frame = (int)(gf > 0 ? gf : 1);
     h->grid_gram = grid_of(ops->gram_occupancy(), h->num_sms, (int64_t)dp.C * dp.npt * (TILE_P / ops->vw));
+    // the cluster form for small subspaces: one cluster of up to 16 CTAs (a
+    // power of two, at most one per pixel tile) that fits the device
+    h->cluster_grid = 0;
     {
-        // the first pass's data is prefetched into L2 when the subspace takes
-        // at most half of it, so that the later passes still find it there
-        int l2 = 0;
-        CKI(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device));
         const size_t ub = (size_t)prm->k * dp.C * dp.Pp * u_elem_bytes(dp);
-        h->prefetch = l2 > 0 && ub <= (size_t)l2 / 2 ? 1 : 0;
+        if (prm->form == PROST_FORM_CLUSTER || (prm->form == PROST_FORM_AUTO && ub <= PROST_CLUSTER_MAX_U_BYTES)) {
+            int g = 16;
+            while (g > 1 && (g > dp.npt || g > h->grid_frame)) g /= 2;
+            while (g >= 1 && ops->cluster_fit(fdt, g) < 1) g /= 2;
+            if (g >= 1) h->cluster_grid = g;
+            (void)cudaGetLastError(); // a refused cluster query leaves no error behind
+            if (!h->cluster_grid && prm->form == PROST_FORM_CLUSTER) {
+                h->err = "the cluster form does not fit this device";
+                return bail(PROST_EINVAL);
+            }
+        }
     }
     // the Gram kernel's rows, or the frame kernel's two value-major buffers
     h->partial_floats = std::max((size_t)h->grid_gram * partial_row(prm->k),
@@ -360,15 +395,69 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     return PROST_OK;
 }
 
+namespace {
+
+// Enqueue one frame launch on the handle's stream (and the periodic rebase):
+// frame planes at fptr, `pitch` entries apart; outputs and status optional.
+int launch_frame(prost_handle *h, const void *fptr, int64_t pitch, uint8_t *mask_dev, float *bg_dev,
+                 int32_t *status_dev)
+{
+    FrameArgs fa;
+    memset(&fa, 0, sizeof(fa));
+    fa.U = h->U;
+    fa.frame = fptr;
+    fa.labels = h->labels;
+    fa.mask_out = mask_dev;
+    fa.bg_out = bg_dev;
+    fa.ks = h->ks;
+    fa.partials = h->partials;
+    fa.bar = h->bar;
+    fa.bar_base = h->bar_base;
+    fa.frame_pitch = pitch;
+    const bool cl = h->cluster_grid > 0;
+    const int grid = cl ? h->cluster_grid : h->grid_frame;
+    fa.col_stride = col_stride(grid);
+    fa.grid = grid;
+    fa.stall_at = h->stall_at;
+    fa.stall_limit = h->stall_limit;
+    fa.status_out = status_dev;
+    h->stall_at = 0; // one launch only
+    fa.prm = h->dp;
+    if (h->timing) CK(h, cudaEventRecord(h->ev[0], h->stream));
+    if (cl)
+        CK(h, h->ops->frame_cluster(fa, h->prm.frame_dtype, grid, h->stream));
+    else
+        CK(h, h->ops->frame(fa, h->prm.frame_dtype, grid, h->stream));
+    if (h->timing) {
+        CK(h, cudaEventRecord(h->ev[1], h->stream));
+        h->timed_frames += 1;
+    }
+    // the grid barrier's arrivals (the cluster form does not use it)
+    if (!cl) h->bar_base += (unsigned long long)grid * (unsigned long long)frame_arrivals(h->prm.n_cg);
+    // The frame kernel updates the stored rows in the stored basis (U = U_st T);
+    // every REBASE_EVERY frames the stored rows are moved onto the orthonormal
+    // representative so that the conditioning of U_st cannot drift.  The
+    // device counts the frames that completed, and the rebase runs only when
+    // that count is due, so a refused frame does not shift the rebase.
+    if (++h->steps_since_rebase >= REBASE_EVERY) {
+        const int rc = rebase(h, 0);
+        if (rc) return rc;
+        h->steps_since_rebase = 0;
+    }
+    return PROST_OK;
+}
+
+} // namespace
+
 int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_out,
                float *background_out)
 {
     if (!h) return PROST_EINVAL;
     if (!frame) return fail(h, PROST_EINVAL, "frame is NULL");
+    if (h->a_count > 0) return fail(h, PROST_EINVAL, "prost_step with frames of prost_step_async in flight");
     DeviceGuard dg(h->device);
     const DevParams &dp = h->dp;
     const int64_t m = m_of(h->prm);
-    const int fdt = h->prm.frame_dtype;
     const size_t eb = frame_elem_bytes(h->prm);
     // The frame kernel copies frame planes with 16-byte bulk copies: a device
     // frame whose planes start on 16-byte boundaries is read in place, any
@@ -392,47 +481,12 @@ int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_
             bg_dev = h->bg_buf;
         }
     }
-    FrameArgs fa;
-    memset(&fa, 0, sizeof(fa));
-    fa.U = h->U;
-    fa.frame = fptr;
-    fa.labels = h->labels;
-    fa.mask_out = on_device ? mask_out : nullptr;
-    fa.bg_out = bg_dev;
-    fa.ks = h->ks;
-    fa.partials = h->partials;
-    fa.bar = h->bar;
-    fa.bar_base = h->bar_base;
-    fa.frame_pitch = pitch;
-    fa.col_stride = col_stride(h->grid_frame);
-    fa.grid = h->grid_frame;
-    fa.stall_at = h->stall_at;
-    fa.stall_limit = h->stall_limit;
-    h->stall_at = 0; // one launch only
-    fa.prefetch = h->prefetch;
-    fa.prm = dp;
-    if (h->timing) CK(h, cudaEventRecord(h->ev[0], h->stream));
-    CK(h, h->ops->frame(fa, fdt, h->grid_frame, h->stream));
-    if (h->timing) {
-        CK(h, cudaEventRecord(h->ev[1], h->stream));
-        h->timed_frames += 1;
-    }
-    // arrivals per frame: one per CTA at each residual pass and at the end
-    h->bar_base += (unsigned long long)h->grid_frame * (unsigned long long)frame_arrivals(h->prm.n_cg);
-    // The frame kernel updates the stored rows in the stored basis (U = U_st T);
-    // every REBASE_EVERY frames the stored rows are moved onto the orthonormal
-    // representative so that the conditioning of U_st cannot drift.  The
-    // device counts the frames that completed, and the rebase runs only when
-    // that count is due, so a refused frame does not shift the rebase.
-    if (++h->steps_since_rebase >= REBASE_EVERY) {
-        const int rc = rebase(h, 0);
-        if (rc) return rc;
-        h->steps_since_rebase = 0;
-    }
+    int rc = launch_frame(h, fptr, pitch, on_device ? mask_out : nullptr, bg_dev, nullptr);
+    if (rc) return rc;
     if (on_device) return PROST_OK;
     // host outputs: only a frame that completed writes them
     int st = 0;
-    int rc = read_status(h, &st);
+    rc = read_status(h, &st);
     if (rc) return rc;
     if (st != PROST_OK && st != PROST_ENOTSPD) return st;
     if (mask_out)
@@ -444,10 +498,72 @@ int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_
     return st;
 }
 
+int prost_step_async(prost_handle *h, const void *frame, uint8_t *mask_out, float *background_out)
+{
+    if (!h) return PROST_EINVAL;
+    if (!frame) return fail(h, PROST_EINVAL, "frame is NULL");
+    if (h->a_count >= 2) return fail(h, PROST_EINVAL, "two frames in flight: call prost_wait first");
+    DeviceGuard dg(h->device);
+    const DevParams &dp = h->dp;
+    const int64_t m = m_of(h->prm);
+    const size_t eb = frame_elem_bytes(h->prm);
+    if (!h->s_in) {
+        CK(h, cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
+        CK(h, cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
+        CK(h, cudaMalloc(&h->ast_dev, 2 * sizeof(int32_t)));
+        CK(h, cudaMallocHost(&h->ast_host, 2 * sizeof(int32_t)));
+        for (int i = 0; i < 2; ++i) {
+            CK(h, cudaMalloc(&h->af_buf[i], (size_t)dp.C * dp.Pp * eb));
+            CK(h, cudaMalloc(&h->am_buf[i], (size_t)dp.Pp));
+            CK(h, cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming));
+            CK(h, cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming));
+            CK(h, cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming));
+        }
+    }
+    const int slot = (h->a_head + h->a_count) & 1;
+    if (background_out && !h->ab_buf[slot]) CK(h, cudaMalloc(&h->ab_buf[slot], (size_t)m * sizeof(float)));
+    // the copy in waits until the kernel that last read this slot's frame has
+    // finished (it ran two frames ago); the compute stream waits for the copy
+    // and for the copies out of this slot's previous outputs
+    if (h->a_used[slot]) CK(h, cudaStreamWaitEvent(h->s_in, h->ev_done[slot], 0));
+    CK(h, cudaMemcpy2DAsync(h->af_buf[slot], (size_t)dp.Pp * eb, frame, (size_t)dp.P * eb, (size_t)dp.P * eb,
+                            (size_t)dp.C, cudaMemcpyHostToDevice, h->s_in));
+    CK(h, cudaEventRecord(h->ev_in[slot], h->s_in));
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_in[slot], 0));
+    if (h->a_used[slot]) CK(h, cudaStreamWaitEvent(h->stream, h->ev_out[slot], 0));
+    int rc = launch_frame(h, h->af_buf[slot], dp.Pp, h->am_buf[slot], background_out ? h->ab_buf[slot] : nullptr,
+                          h->ast_dev + slot);
+    if (rc) return rc;
+    CK(h, cudaEventRecord(h->ev_done[slot], h->stream));
+    CK(h, cudaStreamWaitEvent(h->s_out, h->ev_done[slot], 0));
+    if (mask_out) CK(h, cudaMemcpyAsync(mask_out, h->am_buf[slot], (size_t)dp.P, cudaMemcpyDeviceToHost, h->s_out));
+    if (background_out)
+        CK(h, cudaMemcpyAsync(background_out, h->ab_buf[slot], (size_t)m * sizeof(float), cudaMemcpyDeviceToHost,
+                              h->s_out));
+    CK(h, cudaMemcpyAsync(h->ast_host + slot, h->ast_dev + slot, sizeof(int32_t), cudaMemcpyDeviceToHost, h->s_out));
+    CK(h, cudaEventRecord(h->ev_out[slot], h->s_out));
+    h->a_used[slot] = 1;
+    h->a_count += 1;
+    return PROST_OK;
+}
+
+int prost_wait(prost_handle *h)
+{
+    if (!h) return PROST_EINVAL;
+    if (h->a_count == 0) return fail(h, PROST_EINVAL, "no frame of prost_step_async in flight");
+    DeviceGuard dg(h->device);
+    const int slot = h->a_head;
+    CK(h, cudaEventSynchronize(h->ev_out[slot]));
+    h->a_head ^= 1;
+    h->a_count -= 1;
+    return h->ast_host[slot];
+}
+
 int prost_sync(prost_handle *h)
 {
     if (!h) return PROST_EINVAL;
     DeviceGuard dg(h->device);
+    if (h->s_out) CK(h, cudaStreamSynchronize(h->s_out)); // the copies out of pipelined frames
     CK(h, cudaMemcpyAsync(h->h_word, &h->ks->err_flags, sizeof(uint32_t), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaMemsetAsync(&h->ks->err_flags, 0, sizeof(uint32_t), h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -473,6 +589,7 @@ int prost_inject_barrier_skew(prost_handle *h, int64_t delta)
     if (!h) return PROST_EINVAL;
     // a forward skew below the grid size looks like CTAs that already arrived:
     // the launch cannot tell it from a healthy barrier
+    if (h->cluster_grid > 0) return fail(h, PROST_EINVAL, "the cluster form has no grid barrier");
     if (delta > 0 && delta < (int64_t)h->grid_frame)
         return fail(h, PROST_EINVAL, "a forward skew below the grid size is not detectable");
     DeviceGuard dg(h->device);
@@ -488,6 +605,7 @@ int prost_inject_wait_timeout(prost_handle *h, int32_t pass, int64_t cycles)
 {
     if (!h) return PROST_EINVAL;
     if (pass < 0 || pass > h->prm.n_cg) return fail(h, PROST_EINVAL, "pass must be in 0..n_cg");
+    if (h->cluster_grid > 0) return fail(h, PROST_EINVAL, "the cluster form has no software barrier to stall");
     if (cycles < 1 || cycles > 2000000000ll) return fail(h, PROST_EINVAL, "cycles must be in 1..2e9");
     h->stall_at = pass + 1;
     h->stall_limit = cycles;
@@ -606,6 +724,7 @@ int prost_get_stats(prost_handle *h, prost_stats *out)
     out->orth_err = ks.orth_err;
     out->eta_norm = ks.eta_norm;
     out->pi_explicit = ks.pi_explicit;
+    out->form = h->cluster_grid > 0 ? PROST_FORM_CLUSTER : PROST_FORM_GRID;
     return PROST_OK;
 }
 
@@ -708,6 +827,8 @@ void prost_destroy(prost_handle *h)
     {
         DeviceGuard dg(h->device);
         cudaStreamSynchronize(h->stream);
+        if (h->s_in) cudaStreamSynchronize(h->s_in);
+        if (h->s_out) cudaStreamSynchronize(h->s_out);
         free_state(h);
     }
     delete h;

@@ -127,7 +127,7 @@ struct FrameArgs {
     // giving up after stall_limit SM clock cycles
     int stall_at;
     long long stall_limit;
-    int prefetch;             // register form: bulk-prefetch the first pass's data into L2
+    int32_t *status_out;      // optional (device): the frame's status, as last_status
     DevParams prm;
 };
 
@@ -138,6 +138,9 @@ struct KernelOps {
     // several streams in one launch: CTA b works on stream map[b].x as its
     // CTA map[b].y of args[map[b].x].grid (device tables)
     cudaError_t (*frame_multi)(const FrameArgs *args, const int2 *map, int ctas, int frame_dtype, cudaStream_t);
+    // the cluster form: one cluster of `grid` CTAs; how many such clusters fit at once
+    cudaError_t (*frame_cluster)(const FrameArgs &, int frame_dtype, int grid, cudaStream_t);
+    int (*cluster_fit)(int frame_dtype, int grid);
     cudaError_t (*gram)(const GramArgs &, int grid, cudaStream_t);
     cudaError_t (*export_u)(const void *U, const KState *ks, float *out, DevParams prm,
                             cudaStream_t);

@@ -30,6 +30,8 @@
 // previous launch aborted) does nothing but raise the error.
 #pragma once
 
+#include <string.h>
+
 #include "prost_kernels.cuh"
 #include "prost_stage.cuh"
 
@@ -228,15 +230,23 @@ __device__ __noinline__ void reduce_cols(const float *cols, int nrows, int cstri
 #pragma unroll
         for (int i = 0; i < RED_ROWS / 4; ++i)
             v[i] = r0 + 4 * i < nrows ? __ldcg(p + i) : make_float4(0.f, 0.f, 0.f, 0.f);
-        float s = 0.f, k = 0.f;
+        // four compensated sums, one per lane of the 16-byte loads (shorter
+        // dependent chains), added in a fixed order
+        float s0 = 0.f, k0 = 0.f, s1 = 0.f, k1 = 0.f, s2 = 0.f, k2 = 0.f, s3 = 0.f, k3 = 0.f;
 #pragma unroll
         for (int i = 0; i < RED_ROWS / 4; ++i) {
             const int r = r0 + 4 * i;
-            kahan_add(s, k, r < nrows ? v[i].x : 0.f);
-            kahan_add(s, k, r + 1 < nrows ? v[i].y : 0.f);
-            kahan_add(s, k, r + 2 < nrows ? v[i].z : 0.f);
-            kahan_add(s, k, r + 3 < nrows ? v[i].w : 0.f);
+            kahan_add(s0, k0, r < nrows ? v[i].x : 0.f);
+            kahan_add(s1, k1, r + 1 < nrows ? v[i].y : 0.f);
+            kahan_add(s2, k2, r + 2 < nrows ? v[i].z : 0.f);
+            kahan_add(s3, k3, r + 3 < nrows ? v[i].w : 0.f);
         }
+        float s = 0.f, k = 0.f;
+        kahan_add(s, k, s0);
+        kahan_add(s, k, s1);
+        kahan_add(s, k, s2);
+        kahan_add(s, k, s3);
+        kahan_add(s, k, -((k0 + k1) + (k2 + k3)));
         scr[u] = s;
     }
     cons_sync<NCONS>();
@@ -320,7 +330,7 @@ __device__ __forceinline__ void mma_row(const unsigned char *base, int warp_byte
 // out: the abort flag, ERR_TIMEOUT and the frame's status PROST_ETIMEOUT.
 template <int NCONS>
 __device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target, int *s_err, KState *ks,
-                                          long long limit = WAIT_LIMIT)
+                                          int32_t *st_out, long long limit = WAIT_LIMIT)
 {
     cons_sync<NCONS>();
     if (threadIdx.x == 0) {
@@ -343,12 +353,38 @@ __device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target
             atomicExch(&gb->abort, 1);
             atomicOr(&ks->err_flags, ERR_TIMEOUT);
             ks->last_status = -5; // PROST_ETIMEOUT
+            if (st_out) *st_out = -5;
             *s_err = 1;
         }
         __threadfence();
     }
     cons_sync<NCONS>();
     return *(volatile int *)s_err == 0;
+}
+
+// Barrier of the cluster form: every thread of every CTA of the cluster
+// arrives (releasing its global-memory writes at cluster scope) and waits
+// (acquiring the others').  It is the hardware cluster barrier, reached by
+// all CTAs because the cluster form has no early return before the end of
+// the frame (every decision between barriers is taken on identical data).
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The synchronisation between a pass's partial values and their reduction:
+// the cluster barrier (cluster form) or the bounded grid barrier, whose
+// failure marks the frame timed out.
+template <bool CL, int NCONS>
+__device__ __forceinline__ bool pass_sync(GridBar *gb, unsigned long long target, int *s_err, KState *ks,
+                                          int32_t *st_out, long long limit = WAIT_LIMIT)
+{
+    if constexpr (CL) {
+        cluster_sync_all();
+        return true;
+    } else {
+        return grid_wait<NCONS>(gb, target, s_err, ks, st_out, limit);
+    }
 }
 
 // ---- k-space steps on the shared copy (one warp) ---------------------------------
@@ -739,7 +775,8 @@ __device__ bool cholesky_refined(ReorthScratch<K> &rs)
 // farther from I (bfloat16 stored rows, whose rounding moves the Gram away
 // from I) take an FP32 factorisation refined in FP64 (cholesky_refined).
 template <int K, int NT>
-__device__ void end_frame(const SKState<K> &sk, KState *ks, const float *G, float n_fg, ReorthScratch<K> &rs)
+__device__ void end_frame(const SKState<K> &sk, KState *ks, const float *G, float n_fg, ReorthScratch<K> &rs,
+                          int32_t *st_out)
 {
     const int t = threadIdx.x;
     const int i = t / K, l = t - (t / K) * K;
@@ -748,6 +785,7 @@ __device__ void end_frame(const SKState<K> &sk, KState *ks, const float *G, floa
         if (t == 0) {
             ks->err_flags |= ERR_BADFRAME;
             ks->last_status = -4; // PROST_EBADFRAME
+            if (st_out) *st_out = -4;
             ks->bad_frames += 1;
             ks->frames_since_rebase += 1;
         }
@@ -828,6 +866,7 @@ __device__ void end_frame(const SKState<K> &sk, KState *ks, const float *G, floa
         ks->frame_index = sk.frame_index + 1;
         ks->frames_since_rebase += 1;
         ks->last_status = ok ? 0 : -6; // PROST_ENOTSPD
+        if (st_out) *st_out = ok ? 0 : -6;
         ks->skip = 0;
     }
 }
@@ -968,44 +1007,12 @@ __device__ __forceinline__ void proj_pass(const FrameArgs &a, const FrameTiles &
     }
 }
 
-// Prefetch into L2 of what this CTA's first residual pass reads (register
-// form, when the host found the subspace small enough to stay in L2): its
-// tiles of the stored subspace, and the frame entries and labels of the same
-// tiles.  Every thread issues non-blocking line prefetches (one per 128-byte
-// line) before its first loads, so the whole range streams from HBM at once
-// and the pass's loads then find their lines in L2.  Every prefetched
-// address lies inside its buffer.
-__device__ __forceinline__ void prefetch_line(const void *p)
-{
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
-template <int K, typename FT, typename UT>
-__device__ __forceinline__ void prefetch_first_pass(const FrameArgs &a, const FrameTiles &tl, int nthreads)
-{
-    if (tl.nres <= 0) return;
-    const DevParams &prm = a.prm;
-    const char *ub = static_cast<const char *>(a.U) + (size_t)tl.r0 * K * TILE_P * sizeof(UT);
-    const int ulines = (int)(((size_t)tl.nres * K * TILE_P * sizeof(UT) + 127) / 128);
-    for (int q = threadIdx.x; q < ulines; q += nthreads) prefetch_line(ub + (size_t)q * 128);
-    // frame and label tiles, one channel plane at a time
-    const int ti1 = tl.r0 + tl.nres - 1;
-    const int c0 = tl.r0 / prm.npt, c1 = ti1 / prm.npt;
-    for (int c = c0; c <= c1; ++c) {
-        const int pa = c == c0 ? tl.r0 - c0 * prm.npt : 0;
-        const int pb = c == c1 ? ti1 - c1 * prm.npt : prm.npt - 1;
-        const char *fb = static_cast<const char *>(a.frame) + (size_t)c * a.frame_pitch * sizeof(FT);
-        const size_t f0 = (size_t)pa * TILE_P * sizeof(FT);
-        const size_t fend = min((size_t)(pb + 1) * TILE_P, (size_t)prm.P) * sizeof(FT);
-        for (size_t o = f0 + (size_t)threadIdx.x * 128; o < fend; o += (size_t)nthreads * 128) prefetch_line(fb + o);
-        const size_t l1 = (size_t)(pb + 1) * TILE_P;
-        for (size_t o = (size_t)pa * TILE_P + (size_t)threadIdx.x * 128; o < l1; o += (size_t)nthreads * 128)
-            prefetch_line(a.labels + o);
-    }
-}
-
 // The frame of one stream, by CTA b of the G CTAs working on it.
-template <int K, typename FT, typename UT>
+// CL: the cluster form (the whole grid is one thread-block cluster, its
+// barriers are the hardware cluster barrier, CTA 0 ends the frame); else the
+// grid form (cooperative launch, bounded grid barriers, the last CTA to
+// arrive ends the frame).
+template <int K, typename FT, typename UT, bool CL = false>
 __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, const int b)
 {
     using F = FCfg<K, UT>;
@@ -1023,8 +1030,15 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     const FrameTiles tl(prm, G, b);
 
     if (tid == 0) {
-        const unsigned long long c0 = ld_acquire_u64(&a.bar->count);
-        sk.err = (c0 < a.bar_base || c0 >= a.bar_base + (unsigned long long)G) ? 1 : 0;
+        // grid form: the barrier count must be where this launch expects it
+        // (a launch that gave up part-way leaves it elsewhere); the cluster
+        // form has no software barrier to check
+        if constexpr (CL) {
+            sk.err = 0;
+        } else {
+            const unsigned long long c0 = ld_acquire_u64(&a.bar->count);
+            sk.err = (c0 < a.bar_base || c0 >= a.bar_base + (unsigned long long)G) ? 1 : 0;
+        }
         sk.skip = 0;
         sk.last = 0;
         sk.proj = 0;
@@ -1044,11 +1058,9 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         if (tid == 0 && b == 0) {
             atomicOr(&a.ks->err_flags, ERR_TIMEOUT);
             a.ks->last_status = -5; // PROST_ETIMEOUT: the frame was refused
+            if (a.status_out) *a.status_out = -5;
         }
         return;
-    }
-    if constexpr (!F::STREAM) {
-        if (a.prefetch) prefetch_first_pass<K, FT, UT>(a, tl, NT);
     }
 
     const bool stats = b == 0;
@@ -1084,8 +1096,8 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 cons_partials<F::NPR, NW>(acc, F::NVR, col, sred, cs);
             }
             if (trace) a.ks->sub_ts[1] = global_ns();
-            if (!grid_wait<NT>(a.bar, target + (pass + 1 == a.stall_at ? 1ull : 0ull), &sk.err, a.ks,
-                               pass + 1 == a.stall_at ? a.stall_limit : WAIT_LIMIT))
+            if (!pass_sync<CL, NT>(a.bar, target + (pass + 1 == a.stall_at ? 1ull : 0ull), &sk.err, a.ks,
+                                   a.status_out, pass + 1 == a.stall_at ? a.stall_limit : WAIT_LIMIT))
                 return;
             if (trace) a.ks->sub_ts[2] = global_ns();
             reduce_cols<NT>(cols, G, cs, F::NVR, tot, rscr);
@@ -1104,8 +1116,8 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 cons_partials_tree<F::NVF, NW>(acc, F::NVF, col, sred, cs);
             else
                 cons_partials<F::NPF, NW>(acc, F::NVF, col, sred, cs);
-            if (!grid_wait<NT>(a.bar, target + (pass + 1 == a.stall_at ? 1ull : 0ull), &sk.err, a.ks,
-                               pass + 1 == a.stall_at ? a.stall_limit : WAIT_LIMIT))
+            if (!pass_sync<CL, NT>(a.bar, target + (pass + 1 == a.stall_at ? 1ull : 0ull), &sk.err, a.ks,
+                                   a.status_out, pass + 1 == a.stall_at ? a.stall_limit : WAIT_LIMIT))
                 return;
             reduce_cols<NT>(cols, G, cs, F::NVF, tot, rscr);
             if (warp == 0) kspace_cg<K, false>(sk, prm, tot, pass, a.ks, stats);
@@ -1126,7 +1138,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         else
             proj_pass<K, FT, UT>(a, tl, sk, acc1[0]);
         cons_partials_tree<1, NW, 1>(acc1, 1, const_cast<float *>(pcols) + b, sred, a.col_stride);
-        if (!grid_wait<NT>(a.bar, target, &sk.err, a.ks)) return;
+        if (!pass_sync<CL, NT>(a.bar, target, &sk.err, a.ks, a.status_out)) return;
         reduce_cols<NT>(pcols, G, a.col_stride, 1, tot, rscr);
         if (tid == 0) step_angle(sk, prm, sqrtf(fmaxf(tot[0], 0.f)), a.ks, stats);
         cons_sync<NT>();
@@ -1275,7 +1287,11 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     }
     cons_sync<NT>();
     if (tid == 0 && stats) a.ks->sub_ts[6] = global_ns();
-    if (tid == 0) {
+    if constexpr (CL) {
+        // cluster form: every CTA's partial values, then CTA 0 ends the frame
+        cluster_sync_all();
+        if (tid == 0) sk.last = b == 0;
+    } else if (tid == 0) {
         // every CTA arrives FRAME_ARRIVALS(n_cg) times per frame: once per
         // residual pass, once at the projection barrier (counted here when that
         // pass did not run) and once here; the last arrival of all is here
@@ -1290,7 +1306,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     if (!sk.last) return;
     reduce_cols<NT>(ucols, G, a.col_stride, F::NVU, tot, rscr);
     if (tid == 0) a.ks->sub_ts[8] = global_ns();
-    end_frame<K, NT>(sk, a.ks, tot, tot[NM], rs);
+    end_frame<K, NT>(sk, a.ks, tot, tot[NM], rs, a.status_out);
     if (tid == 0) a.ks->sub_ts[9] = global_ns();
     if (tid == 0) a.ks->phase_ts[prm.n_cg + 2] = global_ns();
 }
@@ -1300,6 +1316,13 @@ template <int K, typename FT, typename UT>
 __global__ void __launch_bounds__(FCfg<K, UT>::THREADS, 1) k_frame(const FrameArgs a)
 {
     frame_body<K, FT, UT>(a, (int)gridDim.x, (int)blockIdx.x);
+}
+
+// One stream: the whole grid as one thread-block cluster (small frames).
+template <int K, typename FT, typename UT>
+__global__ void __launch_bounds__(FCfg<K, UT>::THREADS, 1) k_frame_cluster(const FrameArgs a)
+{
+    frame_body<K, FT, UT, true>(a, (int)gridDim.x, (int)blockIdx.x);
 }
 
 // Several streams of one kernel family in one cooperative launch: each CTA
@@ -1333,6 +1356,58 @@ template <int K, typename UT> struct FrameOps {
     {
         return fdt == 0 ? launch_t<uint8_t>(a, grid, s) : launch_t<float>(a, grid, s);
     }
+    // the cluster form: one cluster of `grid` CTAs (up to 16, a non-portable size)
+    template <typename FT> static cudaError_t cluster_attrs()
+    {
+        static cudaError_t done = cudaErrorNotReady; // once per instantiation
+        if (done == cudaErrorNotReady) {
+            done = cudaFuncSetAttribute(k_frame_cluster<K, FT, UT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (done == cudaSuccess && dyn_smem<FT>() > 0)
+                done = cudaFuncSetAttribute(k_frame_cluster<K, FT, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            dyn_smem<FT>());
+        }
+        return done;
+    }
+    template <typename FT> static void cluster_cfg(cudaLaunchConfig_t &cfg, cudaLaunchAttribute *at, int grid,
+                                                   cudaStream_t s)
+    {
+        memset(&cfg, 0, sizeof(cfg));
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(F::THREADS);
+        cfg.dynamicSmemBytes = dyn_smem<FT>();
+        cfg.stream = s;
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = grid;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+    }
+    template <typename FT> static cudaError_t cluster_t(const FrameArgs &a, int grid, cudaStream_t s)
+    {
+        cudaError_t e = cluster_attrs<FT>();
+        if (e != cudaSuccess) return e;
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute at[1];
+        cluster_cfg<FT>(cfg, at, grid, s);
+        return cudaLaunchKernelEx(&cfg, k_frame_cluster<K, FT, UT>, a);
+    }
+    static cudaError_t cluster(const FrameArgs &a, int fdt, int grid, cudaStream_t s)
+    {
+        return fdt == 0 ? cluster_t<uint8_t>(a, grid, s) : cluster_t<float>(a, grid, s);
+    }
+    // clusters of `grid` CTAs that can be resident at once (0: the form cannot run)
+    template <typename FT> static int cluster_fit_t(int grid)
+    {
+        if (cluster_attrs<FT>() != cudaSuccess) return 0;
+        cudaLaunchConfig_t cfg;
+        cudaLaunchAttribute at[1];
+        cluster_cfg<FT>(cfg, at, grid, 0);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_frame_cluster<K, FT, UT>, &cfg) != cudaSuccess) return 0;
+        return n;
+    }
+    static int cluster_fit(int fdt, int grid) { return fdt == 0 ? cluster_fit_t<uint8_t>(grid) : cluster_fit_t<float>(grid); }
     template <typename FT>
     static cudaError_t multi_t(const FrameArgs *args, const int2 *map, int ctas, cudaStream_t s)
     {
@@ -1370,6 +1445,7 @@ template <int K, typename UT> struct FrameOps {
 template <int K, typename UT> const KernelOps *kernel_table()
 {
     static const KernelOps ops = {&FrameOps<K, UT>::launch, &FrameOps<K, UT>::prepare, &FrameOps<K, UT>::multi,
+                                  &FrameOps<K, UT>::cluster, &FrameOps<K, UT>::cluster_fit,
                                   &Ops<K, UT>::gram,
                                   &Ops<K, UT>::export_u, &Ops<K, UT>::gram_occupancy, &Ops<K, UT>::rebase,
                                   Cfg<K>::VW, FCfg<K, UT>::TP, FCfg<K, UT>::THREADS};

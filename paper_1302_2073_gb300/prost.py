@@ -22,6 +22,8 @@ PROST_EBADFRAME, PROST_ETIMEOUT, PROST_ENOTSPD = -4, -5, -6
 PROST_U8, PROST_F32, PROST_BF16 = 0, 1, 2
 PROST_MASK_POST_UPDATE, PROST_MASK_PRE_UPDATE = 0, 1
 PROST_MAX_K, PROST_MAX_CG = 16, 32
+PROST_FORM_AUTO, PROST_FORM_GRID, PROST_FORM_CLUSTER = 0, 1, 2
+PROST_CLUSTER_MAX_U_BYTES = 1 << 20
 
 HEADER = os.path.join(_build.INCLUDE, "prost.h")
 
@@ -38,7 +40,7 @@ class prost_params(C.Structure):
                 ("omega", C.c_double), ("t_init", C.c_double), ("t_min", C.c_double),
                 ("i_init", C.c_int32), ("n_cg", C.c_int32), ("in_scale", C.c_double),
                 ("in_offset", C.c_double), ("frame_dtype", C.c_int32), ("u_dtype", C.c_int32),
-                ("mask_from", C.c_int32), ("reserved", C.c_int32), ("seed", C.c_uint64)]
+                ("mask_from", C.c_int32), ("form", C.c_int32), ("seed", C.c_uint64)]
 
 
 class prost_stats(C.Structure):
@@ -49,7 +51,7 @@ class prost_stats(C.Structure):
                 ("y_norm", C.c_double), ("sigma", C.c_double), ("t", C.c_double),
                 ("theta", C.c_double), ("updated", C.c_int32), ("pad0", C.c_int32),
                 ("n_foreground", C.c_int64), ("orth_err", C.c_double),
-                ("eta_norm", C.c_double), ("pi_explicit", C.c_int32), ("pad1", C.c_int32)]
+                ("eta_norm", C.c_double), ("pi_explicit", C.c_int32), ("form", C.c_int32)]
 
 
 _lib = None
@@ -67,6 +69,8 @@ def lib():
         L.prost_init.argtypes = [P(prost_params), vp, P(vp)]
         L.prost_step.argtypes = [vp, vp, C.c_int, vp, vp]
         L.prost_sync.argtypes = [vp]
+        L.prost_step_async.argtypes = [vp, vp, vp, vp]
+        L.prost_wait.argtypes = [vp]
         L.prost_inject_barrier_skew.argtypes = [vp, C.c_int64]
         L.prost_inject_wait_timeout.argtypes = [vp, C.c_int32, C.c_int64]
         L.prost_get_subspace.argtypes = [vp, vp, vp, C.c_int]
@@ -171,12 +175,12 @@ _DTYPES = {"u8": PROST_U8, "uint8": PROST_U8, "f32": PROST_F32, "float32": PROST
 def make_params(width, height, channels=1, k=5, p=0.25, mu=0.0, delta=0.35, omega=5e-5,
                 t_init=5e-3, t_min=1e-4, i_init=100, n_cg=5, in_scale=1.0, in_offset=0.0,
                 frame_dtype="u8", u_dtype="f32", mask_from=PROST_MASK_POST_UPDATE, seed=0,
-                **_ignored) -> prost_params:
+                form=PROST_FORM_AUTO, **_ignored) -> prost_params:
     fd = _DTYPES[frame_dtype] if isinstance(frame_dtype, str) else int(frame_dtype)
     ud = _DTYPES[u_dtype] if isinstance(u_dtype, str) else int(u_dtype)
     return prost_params(int(width), int(height), int(channels), int(k), float(p), float(mu),
                         float(delta), float(omega), float(t_init), float(t_min), int(i_init),
-                        int(n_cg), float(in_scale), float(in_offset), fd, ud, int(mask_from), 0,
+                        int(n_cg), float(in_scale), float(in_offset), fd, ud, int(mask_from), int(form),
                         int(seed))
 
 
@@ -220,6 +224,22 @@ def prost_step(h, frame, mask_out=None, background_out=None):
     od = _where(frame, mask_out, background_out)
     return _check(lib().prost_step(h, _ptr(frame), od, _ptr(mask_out), _ptr(background_out)), h,
                   allow=(PROST_EBADFRAME,))
+
+
+def prost_step_async(h, frame, mask_out=None, background_out=None):
+    """Enqueue a host frame (numpy arrays or CPU tensors, page-locked for
+    overlap) and return at once; the buffers must stay alive until
+    prost_wait has returned this frame."""
+    for b in (frame, mask_out, background_out):
+        if b is not None and _is_torch(b) and b.is_cuda:
+            raise ProstError(PROST_EINVAL, "prost_step_async takes host buffers")
+    return _check(lib().prost_step_async(h, _ptr(frame), _ptr(mask_out), _ptr(background_out)), h)
+
+
+def prost_wait(h):
+    """Status of the oldest frame of prost_step_async (raises on errors other
+    than PROST_EBADFRAME)."""
+    return _check(lib().prost_wait(h), h, allow=(PROST_EBADFRAME,))
 
 
 def prost_sync(h):

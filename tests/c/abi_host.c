@@ -73,7 +73,7 @@ int main(void)
     FIELD(prost_params, frame_dtype);
     FIELD(prost_params, u_dtype);
     FIELD(prost_params, mask_from);
-    FIELD(prost_params, reserved);
+    FIELD(prost_params, form);
     FIELD(prost_params, seed);
     printf("sizeof prost_stats %zu\n", sizeof(prost_stats));
     FIELD(prost_stats, frames);
@@ -95,7 +95,7 @@ int main(void)
     FIELD(prost_stats, orth_err);
     FIELD(prost_stats, eta_norm);
     FIELD(prost_stats, pi_explicit);
-    FIELD(prost_stats, pad1);
+    FIELD(prost_stats, form);
 
     check(prost_version() == 101, "prost_version");
     check(prost_strerror(PROST_EINVAL) != NULL && strlen(prost_strerror(PROST_EINVAL)) > 0, "strerror");
@@ -106,14 +106,16 @@ int main(void)
     prm.k = 0;
     check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "k = 0 rejected");
     prm = valid_params();
-    prm.reserved = 1;
-    check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "reserved field must be 0");
+    prm.form = 3;
+    check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "form beyond the three forms");
     prm = valid_params();
     prm.p = 3.0;
     check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "p > 2 rejected");
     check(prost_init(NULL, NULL, NULL) == PROST_EINVAL, "prost_init without out");
     check(prost_inject_barrier_skew(NULL, 1) == PROST_EINVAL, "injection without a handle");
     check(prost_inject_wait_timeout(NULL, 0, 1000) == PROST_EINVAL, "wait injection without a handle");
+    check(prost_step_async(NULL, NULL, NULL, NULL) == PROST_EINVAL, "pipelined step without a handle");
+    check(prost_wait(NULL) == PROST_EINVAL, "wait without a handle");
     check(prost_window_inject_wait_timeout(NULL, 1, 1000) == PROST_EINVAL, "window wait injection without a window");
     check(prost_batch_split(10, 3, w, cap, ctas) == PROST_OK, "batch split");
     check(ctas[0] == 4 && ctas[1] == 3 && ctas[2] == 3, "batch split of 10 over thirds");

@@ -54,11 +54,15 @@ def test_parameter_validation(bad):
     assert ei.value.code == pg.PROST_EINVAL
 
 
-def test_reserved_field_must_be_zero():
-    p = pg.make_params(**_ok())
-    p.reserved = 1
-    with pytest.raises(pg.ProstError):
-        pg.prost_state_bytes(p)
+def test_form_field_takes_the_three_forms_only():
+    for form in (pg.PROST_FORM_AUTO, pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER):
+        p = pg.make_params(**_ok(), form=form)
+        assert pg.prost_state_bytes(p) > 0
+    for form in (-1, 3):
+        p = pg.make_params(**_ok())
+        p.form = form
+        with pytest.raises(pg.ProstError):
+            pg.prost_state_bytes(p)
 
 
 def test_null_arguments_are_rejected():
@@ -71,6 +75,8 @@ def test_null_arguments_are_rejected():
     assert L.prost_get_stats(None, None) == pg.PROST_EINVAL
     assert L.prost_inject_barrier_skew(None, 1) == pg.PROST_EINVAL
     assert L.prost_inject_wait_timeout(None, 0, 1000) == pg.PROST_EINVAL
+    assert L.prost_step_async(None, None, None, None) == pg.PROST_EINVAL
+    assert L.prost_wait(None) == pg.PROST_EINVAL
     assert L.prost_window_inject_wait_timeout(None, 1, 1000) == pg.PROST_EINVAL
     L.prost_destroy(None)
 

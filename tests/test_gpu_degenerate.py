@@ -58,7 +58,10 @@ def _start(m, k, seed):
     return rng, U32, U64
 
 
-def _run(wp, U32, U64, y, frame, labels=None):
+FORMS = [pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER]
+
+
+def _run(wp, U32, U64, y, frame, labels=None, form=pg.PROST_FORM_AUTO):
     """One frame from (U64, y) on both sides: the GPU is handed the float32
     rows with the coefficients that give the same U y, and re-orthonormalises
     them onto U64 itself."""
@@ -67,7 +70,7 @@ def _run(wp, U32, U64, y, frame, labels=None):
     y_raw = np.linalg.lstsq(U32.astype(np.float64), U64 @ y, rcond=None)[0]
     _, U64, y64 = matched_start(U32, y_raw)
     prm_o = oracle_params(wp)
-    h = pg.prost_init(gpu_params(wp))
+    h = pg.prost_init(gpu_params(wp, form=form))
     try:
         g = gpu_step_from(h, U32, y_raw, labels, 0, frame, device=True, torch=torch)
         assert g.status == pg.PROST_OK
@@ -93,8 +96,9 @@ def test_zero_frame_at_zero_coefficients_skips_the_step():
     assert not g.mask.any()
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("k", [10, 15])
-def test_zero_frame_keeps_eta_in_span(k):
+def test_zero_frame_keeps_eta_in_span(k, form):
     # r = -U y lies in span(U), so eta = -2 r does, and |U^T eta| = |eta|: the
     # norm identity would leave only rounding, which could take a step along noise
     wp = _wp(64, 48, 3, k)
@@ -102,7 +106,7 @@ def test_zero_frame_keeps_eta_in_span(k):
     rng, U32, U64 = _start(m, k, 2 + k)
     y = rng.standard_normal(k) * 3.0
     frame = _float_frame(np.zeros(m), wp)
-    g, err, tr, eta_n = _run(wp, U32, U64, y, frame)
+    g, err, tr, eta_n = _run(wp, U32, U64, y, frame, form=form)
     assert g.stats.pi_explicit == 1
     assert tr.pi_norm < 1e-12 * eta_n
     assert g.stats.pi_norm < 1e-5 * eta_n
@@ -121,8 +125,9 @@ def test_frame_in_span_up_to_its_float32_rounding(k):
     assert tr.pi_norm < PI_BAND * eta_n  # the band: rounding decides
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("k,ratio", [(10, 1e-3), (10, 1e-2), (15, 1e-3), (15, 1e-2), (7, 3e-2)])
-def test_eta_almost_in_span(k, ratio):
+def test_eta_almost_in_span(k, ratio, form):
     # x = U a + noise: eta = -2 (U (a - y) + noise), pi(eta) = -2 pi(noise)
     wp = _wp(96, 72, 3, k)
     m = 96 * 72 * 3
@@ -132,7 +137,7 @@ def test_eta_almost_in_span(k, ratio):
     d *= 4.0 / np.linalg.norm(d)
     noise = rng.standard_normal(m) * (4.0 * ratio / np.sqrt(m))
     frame = _float_frame(U64 @ (y0 + d) + noise, wp)
-    g, err, tr, eta_n = _run(wp, U32, U64, y0, frame)
+    g, err, tr, eta_n = _run(wp, U32, U64, y0, frame, form=form)
     got = tr.pi_norm / eta_n
     assert 0.3 * ratio < got < 3.0 * ratio, got
     assert g.stats.pi_explicit == 1

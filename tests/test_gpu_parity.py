@@ -51,19 +51,24 @@ def _run_case(wp, vid, frames, device=True, seed=11, **gover):
     return errs
 
 
-def test_gray_160x120_k5_float_frames():
+FORMS = [pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_gray_160x120_k5_float_frames(form):
     vid, wp = synth.make_workload("gray160x120_k5", n_frames=30)
-    errs = _run_case(wp, vid, [0, 1, 2, 25])
+    errs = _run_case(wp, vid, [0, 1, 2, 25], form=form)
     print(errs)
 
 
-def test_rgb_ragged_unaligned_planes_uint8():
+@pytest.mark.parametrize("form", FORMS)
+def test_rgb_ragged_unaligned_planes_uint8(form):
     # P = 37*29 = 1073: planes start off 4-byte boundaries, tails of every tile are ragged
     vid = synth.SyntheticVideo(37, 29, 3, 3, n_frames=8, fg_fraction=0.1, shape="ellipse",
                                jitter=1, seed=77, dtype="u8")
     wp = synth.video._params(vid.m, vid.k, "u8")
     wp.update(width=37, height=29, channels=3, frame_dtype="u8")
-    _run_case(wp, vid, [0, 1, 5])
+    _run_case(wp, vid, [0, 1, 5], form=form)
 
 
 def test_rgb_ragged_two_lanes_per_row_forms():
@@ -84,18 +89,20 @@ def test_rgb_64x48_k10_host_buffers_and_pre_update_labels():
     _run_case(wp, vid, [0, 3], mask_from=pg.PROST_MASK_PRE_UPDATE)
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("k", [1, 2, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16])
-def test_subspace_dimensions(k):
+def test_subspace_dimensions(k, form):
     vid = synth.SyntheticVideo(50, 40, 1, k, n_frames=4, fg_fraction=0.05, seed=100 + k, dtype="f32")
     wp = synth.video._params(vid.m, k, "f32")
     wp.update(width=50, height=40, channels=1, frame_dtype="f32")
-    _run_case(wp, vid, [0, 2])
+    _run_case(wp, vid, [0, 2], form=form)
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("n_cg", [0, 1, 12])
-def test_cg_iteration_counts(n_cg):
+def test_cg_iteration_counts(n_cg, form):
     vid, wp = synth.make_workload("gray160x120_k5", width=40, height=30, n_frames=4)
-    _run_case(dict(wp, n_cg=n_cg), vid, [0, 2])
+    _run_case(dict(wp, n_cg=n_cg), vid, [0, 2], form=form)
 
 
 @pytest.mark.parametrize("p,mu", [(2.0, 0.01), (1.0, 1e-3), (0.5, 0.05)])
@@ -118,6 +125,23 @@ def test_stats_report_the_step_size_rule():
             assert st.frames == i + 1
     finally:
         pg.prost_destroy(h)
+
+
+def test_the_automatic_form_follows_the_subspace_size():
+    # cluster form up to PROST_CLUSTER_MAX_U_BYTES of stored subspace, grid form above
+    for name, over, want in (("gray160x120_k5", {}, pg.PROST_FORM_CLUSTER),
+                             ("rgb640x480_k10", {"width": 160, "height": 120, "k": 15}, pg.PROST_FORM_GRID),
+                             ("rgb640x480_k10", {}, pg.PROST_FORM_GRID)):
+        vid, wp = synth.make_workload(name, n_frames=1, **over)
+        assert (vid.m * vid.k * 4 <= pg.PROST_CLUSTER_MAX_U_BYTES) == (want == pg.PROST_FORM_CLUSTER)
+        h = pg.prost_init(gpu_params(wp))
+        try:
+            f = torch.from_numpy(vid.frame(0)[0]).cuda()
+            pg.prost_step(h, f, torch.empty(vid.P, dtype=torch.uint8, device="cuda"))
+            assert pg.prost_sync(h) == pg.PROST_OK
+            assert pg.prost_get_stats(h).form == want
+        finally:
+            pg.prost_destroy(h)
 
 
 def test_full_size_640x480_rgb_k10_in_the_benchmark_configuration():

@@ -54,8 +54,9 @@ def _grid_size(h):
 
 
 def _pair(wp, frames, n_before):
-    a = pg.prost_init(gpu_params(wp, seed=3))
-    b = pg.prost_init(gpu_params(wp, seed=3))
+    # the grid form: the cluster form has no software barrier to disturb
+    a = pg.prost_init(gpu_params(wp, seed=3, form=pg.PROST_FORM_GRID))
+    b = pg.prost_init(gpu_params(wp, seed=3, form=pg.PROST_FORM_GRID))
     mask = torch.empty(frames[0].numel() // wp["channels"], dtype=torch.uint8, device="cuda")
     for h in (a, b):
         for t in range(n_before):
@@ -138,9 +139,22 @@ def test_host_frame_reports_the_fault_and_leaves_outputs_unwritten(kind):
         pg.prost_destroy(b)
 
 
+def test_the_cluster_form_takes_no_barrier_injection():
+    vid, wp = synth.make_workload("gray160x120_k5", n_frames=1)
+    h = pg.prost_init(gpu_params(wp, seed=3, form=pg.PROST_FORM_CLUSTER))
+    try:
+        for inject in (lambda: pg.prost_inject_barrier_skew(h, -1),
+                       lambda: pg.prost_inject_wait_timeout(h, 0, STALL_CYCLES)):
+            with pytest.raises(pg.ProstError) as ei:
+                inject()
+            assert ei.value.code == pg.PROST_EINVAL
+    finally:
+        pg.prost_destroy(h)
+
+
 def test_undetectable_forward_skew_is_rejected_by_the_injector():
     vid, wp = synth.make_workload("gray160x120_k5", n_frames=1)
-    h = pg.prost_init(gpu_params(wp, seed=3))
+    h = pg.prost_init(gpu_params(wp, seed=3, form=pg.PROST_FORM_GRID))
     try:
         with pytest.raises(pg.ProstError) as ei:
             pg.prost_inject_barrier_skew(h, 1)
