@@ -364,6 +364,140 @@ def precision_study(torch, pg, dev, stream, flush_l2, frames_timed=40, warm=3):
     return out
 
 
+def _angles_dev(torch, A, B):
+    """Largest principal angle between the column spans of two device
+    matrices (FP64 QR and SVD on the device)."""
+    qa, _ = torch.linalg.qr(A.double())
+    qb, _ = torch.linalg.qr(B.double())
+    s = torch.linalg.svdvals(qa.T @ qb)
+    return float(torch.arccos(torch.clamp(s.min(), -1.0, 1.0)))
+
+
+def bf16_error_study(torch, pg, dev, stream, n_1080=2000, n_batch=500, every=100):
+    """bfloat16 against float32 storage at the measured configurations' own
+    lengths: two trackers (or two batches) from the same float32 subspace see
+    the same frames; the largest principal angle between their subspaces, each
+    one's largest principal angle to the planted subspace of the synthetic
+    stream, the relative difference of their backgrounds and their mask
+    disagreement are recorded every `every` frames.  The float32 path follows the FP64 oracle
+    to about 4e-7 rad (config 1, 200 frames), so it stands in for the oracle
+    where the oracle would take hours; on one 160x120 stream of the batch the
+    oracle itself runs all n_batch frames beside both."""
+    import oracle
+    import synth
+    from synth.video_gpu import DeviceVideo
+    out = {}
+    # ---- 1920x1080 RGB, k = 15, n_1080 frames ------------------------------
+    vid, wp = synth.make_workload("rgb1920x1080_k15", n_frames=n_1080)
+    dvid = DeviceVideo(vid, dev)
+    hs = {ud: pg.prost_init(pg.make_params(**dict(wp, u_dtype=ud), seed=1), stream=stream) for ud in ("f32", "bf16")}
+    try:
+        U0 = torch.empty((vid.m, vid.k), dtype=torch.float32, device=dev)
+        pg.prost_get_subspace(hs["f32"], U0)
+        pg.prost_set_subspace(hs["bf16"], U0)
+        masks = {ud: torch.empty(vid.P, dtype=torch.uint8, device=dev) for ud in hs}
+        bgs = {ud: torch.empty(vid.m, dtype=torch.float32, device=dev) for ud in hs}
+        dis = torch.zeros((), dtype=torch.float64, device=dev)
+        curve = {}
+        frame = torch.empty((vid.channels, vid.height, vid.width), dtype=torch.uint8, device=dev)
+        Ua = torch.empty_like(U0)
+        Ub = torch.empty_like(U0)
+        with torch.cuda.stream(stream):
+            for t in range(n_1080):
+                dvid.frame(t, out=frame)
+                for ud, h in hs.items():
+                    pg.prost_step(h, frame, masks[ud], bgs[ud])
+                dis += (masks["f32"] != masks["bf16"]).double().mean()
+                if (t + 1) % every == 0:
+                    pg.prost_get_subspace(hs["f32"], Ua)
+                    pg.prost_get_subspace(hs["bf16"], Ub)
+                    curve[t + 1] = {"principal_angle_rad": _angles_dev(torch, Ua, Ub),
+                                    "fp32_to_planted_rad": _angles_dev(torch, Ua, dvid.U0),
+                                    "bf16_to_planted_rad": _angles_dev(torch, Ub, dvid.U0),
+                                    "background_rel": float((bgs["bf16"] - bgs["f32"]).norm() /
+                                                            (bgs["f32"] - wp["in_offset"]).norm())}
+        torch.cuda.synchronize()
+        for h in hs.values():
+            assert pg.prost_sync(h) == pg.PROST_OK
+        out["rgb1920x1080_k15"] = {"frames": n_1080, "curve": curve,
+                                   "final_principal_angle_rad": curve[max(curve)]["principal_angle_rad"],
+                                   "mask_disagreement_mean": float(dis) / n_1080,
+                                   "frames_source": "synth.video_gpu (same recipe, torch draws)"}
+    finally:
+        for h in hs.values():
+            pg.prost_destroy(h)
+    del dvid
+    # ---- 64 streams, n_batch ticks ----------------------------------------
+    streams = synth.batched_workload(n_frames=n_batch)
+    dvs = [DeviceVideo(v, dev) for v, _ in streams]
+    n = len(streams)
+    bs = {ud: pg.prost_batch_init([pg.make_params(**dict(w, u_dtype=ud), seed=i + 1)
+                                   for i, (_, w) in enumerate(streams)], stream=stream) for ud in ("f32", "bf16")}
+    try:
+        hb = {ud: [pg.prost_batch_stream(b, i) for i in range(n)] for ud, b in bs.items()}
+        for i, (v, _) in enumerate(streams):
+            U = torch.empty((v.m, v.k), dtype=torch.float32, device=dev)
+            pg.prost_get_subspace(hb["f32"][i], U)
+            pg.prost_set_subspace(hb["bf16"][i], U)
+        # the oracle on stream 0 (160x120), from the same start, on the numpy frames
+        v0, w0 = streams[0]
+        U0h = np.empty((v0.m, v0.k), np.float32)
+        pg.prost_get_subspace(hb["f32"][0], U0h)
+        U64, y64 = oracle.reorthonormalize(U0h.astype(np.float64), np.zeros(v0.k))
+        ost = oracle.OracleState(U64, y64, np.zeros(v0.P, np.uint8), 0)
+        prm0 = oracle.params(**w0)
+        host0 = v0.frames(0, n_batch)
+        masks = {ud: [torch.empty(v.P, dtype=torch.uint8, device=dev) for v, _ in streams] for ud in bs}
+        dis = torch.zeros(n, dtype=torch.float64, device=dev)
+        curve = {}
+        frames = [torch.empty((1, v.height, v.width), dtype=torch.uint8, device=dev) for v, _ in streams]
+        for t in range(n_batch):
+            with torch.cuda.stream(stream):
+                frames[0].copy_(torch.from_numpy(host0[t]))
+                for i in range(1, n):
+                    dvs[i].frame(t, out=frames[i])
+                for ud, b in bs.items():
+                    pg.prost_batch_step(b, frames, masks[ud])
+                dis += torch.stack([(a != c).double().mean() for a, c in zip(masks["f32"], masks["bf16"])])
+            oracle.frame_step(prm0, ost, host0[t], want_residual=False)
+            if (t + 1) % every == 0:
+                torch.cuda.synchronize()
+                angs, pf, pb = [], [], []
+                for i, (v, _) in enumerate(streams):
+                    Ua = torch.empty((v.m, v.k), dtype=torch.float32, device=dev)
+                    Ub = torch.empty_like(Ua)
+                    pg.prost_get_subspace(hb["f32"][i], Ua)
+                    pg.prost_get_subspace(hb["bf16"][i], Ub)
+                    angs.append(_angles_dev(torch, Ua, Ub))
+                    pf.append(_angles_dev(torch, Ua, dvs[i].U0))
+                    pb.append(_angles_dev(torch, Ub, dvs[i].U0))
+                Uo = torch.from_numpy(ost.U).to(dev)
+                U0f = torch.empty((v0.m, v0.k), dtype=torch.float32, device=dev)
+                U0b = torch.empty_like(U0f)
+                pg.prost_get_subspace(hb["f32"][0], U0f)
+                pg.prost_get_subspace(hb["bf16"][0], U0b)
+                curve[t + 1] = {"max_principal_angle_rad": max(angs), "median_principal_angle_rad": float(np.median(angs)),
+                                "to_planted_rad": {"fp32_median": float(np.median(pf)), "fp32_max": max(pf),
+                                                   "bf16_median": float(np.median(pb)), "bf16_max": max(pb)},
+                                "stream0_fp32_vs_oracle_rad": _angles_dev(torch, U0f, Uo),
+                                "stream0_bf16_vs_oracle_rad": _angles_dev(torch, U0b, Uo)}
+        torch.cuda.synchronize()
+        for b in bs.values():
+            assert pg.prost_batch_sync(b) == pg.PROST_OK
+        last = curve[max(curve)]
+        d = (dis / n_batch).cpu().numpy()
+        out["batched_64_streams"] = {"ticks": n_batch, "curve": curve,
+                                     "final_max_principal_angle_rad": last["max_principal_angle_rad"],
+                                     "mask_disagreement_mean": float(d.mean()), "mask_disagreement_max": float(d.max()),
+                                     "oracle_stream": f"stream 0 ({v0.width}x{v0.height}, k = {v0.k}), numpy frames",
+                                     "frames_source": "stream 0: synth.video (the oracle's frames); the others "
+                                                      "synth.video_gpu"}
+    finally:
+        for b in bs.values():
+            pg.prost_batch_destroy(b)
+    return out
+
+
 def pipeline_study(torch, pg, dev, stream, flush_l2, frames_timed=200, warm=10):
     """The paper's whole per-frame pipeline (Section 3.4) on the GPU: a
     640x480 RGB uint8 frame resampled to 160x120 and normalised, one tracker
@@ -722,6 +856,23 @@ def run_ours(args, dist):
         out["bf16_vs_fp32"] = precision_study(torch, pg, dev, stream, flush_l2)
         out["pipeline_160x120_k15"] = pipeline_study(torch, pg, dev, stream, flush_l2)
         out["batched_64_streams"] = batched_study(torch, pg, dev, stream)
+        err = bf16_error_study(torch, pg, dev, stream)
+        out["bf16_vs_fp32"]["error_at_length"] = err
+        bt = out["batched_64_streams"]
+        eb = err["batched_64_streams"]
+        tp = eb["curve"][eb["ticks"]]["to_planted_rad"]
+        e5 = err["rgb1920x1080_k15"]["curve"][err["rgb1920x1080_k15"]["frames"]]
+        out["bf16_vs_fp32"]["statement"] = (
+            f"BF16 batched / FP32 batched = {bt['bf16_over_f32']:.3f} aggregate frames/s at a largest principal "
+            f"angle of {err['batched_64_streams']['final_max_principal_angle_rad']:.3g} rad between the BF16 and "
+            f"FP32 subspaces over {err['batched_64_streams']['ticks']} frames per stream (64 streams; the FP32 "
+            f"path is {err['batched_64_streams']['curve'][err['batched_64_streams']['ticks']]['stream0_fp32_vs_oracle_rad']:.2g} "
+            f"rad from the FP64 oracle on stream 0; largest angle to the planted subspace, median over streams: "
+            f"FP32 {tp['fp32_median']:.3g}, BF16 {tp['bf16_median']:.3g} rad; mask disagreement "
+            f"{eb['mask_disagreement_mean']:.2g}); 1080p k = 15: {out['bf16_vs_fp32']['bf16_over_fp32']:.3f}x at "
+            f"{err['rgb1920x1080_k15']['final_principal_angle_rad']:.3g} rad over {err['rgb1920x1080_k15']['frames']} "
+            f"frames (to the planted subspace: FP32 {e5['fp32_to_planted_rad']:.3g}, BF16 "
+            f"{e5['bf16_to_planted_rad']:.3g} rad)")
         out["window_320x240_n64_k10"] = window_study(torch, pg, dev)
     if dist.rank == 0 and n == 1 and not args.no_cpu_baseline:
         fps, nf, secs = oracle_sample(args.workload, args.cpu_seconds)

@@ -1,6 +1,7 @@
 """The seeded synthetic video: determinism and the stated recipe."""
 
 import numpy as np
+import pytest
 
 import synth
 
@@ -42,3 +43,21 @@ def test_jitter_shifts_whole_frame_with_edge_replication():
             if np.allclose(np.clip(b[:, rows][:, :, cols], 0, 1), f, atol=1e-6):
                 hits += 1
     assert hits >= 1
+
+
+def test_device_video_follows_the_host_recipe():
+    """The torch generator (run here on the CPU) shares the host stream's
+    planted subspace, walk and shapes: its noiseless pieces match the numpy
+    ones, its frames are reproducible, and its draws stay in range."""
+    torch = pytest.importorskip("torch")
+    from synth.video_gpu import DeviceVideo
+    vid, _ = synth.make_workload("rgb640x480_k10", width=64, height=48, n_frames=5)
+    dv = DeviceVideo(vid, "cpu")
+    for t in (0, 3):
+        assert np.array_equal(dv.shape_mask(t).numpy(), vid.shape_mask(t))
+        b = (vid.offset + vid.scale * (dv.U0 @ dv.Y0[t])).numpy().reshape(vid.channels, vid.height, vid.width)
+        np.testing.assert_allclose(b, vid.background(t), atol=1e-5)
+        f1, f2 = dv.frame(t), dv.frame(t)
+        assert f1.dtype == torch.uint8 and tuple(f1.shape) == (vid.channels, vid.height, vid.width)
+        assert torch.equal(f1, f2)
+    assert not torch.equal(dv.frame(0), dv.frame(1))
