@@ -373,13 +373,23 @@ def _angles_dev(torch, A, B):
     return float(torch.arccos(torch.clamp(s.min(), -1.0, 1.0)))
 
 
+def _outside(torch, U, B):
+    """Fraction of the energy of the columns of B outside span(U) (device)."""
+    q, _ = torch.linalg.qr(U.double())
+    B = B.double().reshape(U.shape[0], -1)
+    return float((B - q @ (q.T @ B)).norm() / B.norm())
+
+
 def bf16_error_study(torch, pg, dev, stream, n_1080=2000, n_batch=500, every=100):
     """bfloat16 against float32 storage at the measured configurations' own
     lengths: two trackers (or two batches) from the same float32 subspace see
-    the same frames; the largest principal angle between their subspaces, each
-    one's largest principal angle to the planted subspace of the synthetic
-    stream, the relative difference of their backgrounds and their mask
-    disagreement are recorded every `every` frames.  The float32 path follows the FP64 oracle
+    the same frames; the largest principal angle between their subspaces, the
+    fraction of the planted background's energy (the noiseless background
+    minus its offset) that each subspace misses, the relative difference of
+    their backgrounds and their mask disagreement are recorded every `every`
+    frames.  (The largest angle to the planted subspace itself is near 90
+    degrees for both: the slow coefficient walk excites few of its k
+    directions.)  The float32 path follows the FP64 oracle
     to about 4e-7 rad (config 1, 200 frames), so it stands in for the oracle
     where the oracle would take hours; on one 160x120 stream of the batch the
     oracle itself runs all n_batch frames beside both."""
@@ -412,8 +422,8 @@ def bf16_error_study(torch, pg, dev, stream, n_1080=2000, n_batch=500, every=100
                     pg.prost_get_subspace(hs["f32"], Ua)
                     pg.prost_get_subspace(hs["bf16"], Ub)
                     curve[t + 1] = {"principal_angle_rad": _angles_dev(torch, Ua, Ub),
-                                    "fp32_to_planted_rad": _angles_dev(torch, Ua, dvid.U0),
-                                    "bf16_to_planted_rad": _angles_dev(torch, Ub, dvid.U0),
+                                    "fp32_background_outside": _outside(torch, Ua, dvid.U0 @ dvid.Y0[t]),
+                                    "bf16_background_outside": _outside(torch, Ub, dvid.U0 @ dvid.Y0[t]),
                                     "background_rel": float((bgs["bf16"] - bgs["f32"]).norm() /
                                                             (bgs["f32"] - wp["in_offset"]).norm())}
         torch.cuda.synchronize()
@@ -469,16 +479,16 @@ def bf16_error_study(torch, pg, dev, stream, n_1080=2000, n_batch=500, every=100
                     pg.prost_get_subspace(hb["f32"][i], Ua)
                     pg.prost_get_subspace(hb["bf16"][i], Ub)
                     angs.append(_angles_dev(torch, Ua, Ub))
-                    pf.append(_angles_dev(torch, Ua, dvs[i].U0))
-                    pb.append(_angles_dev(torch, Ub, dvs[i].U0))
+                    pf.append(_outside(torch, Ua, dvs[i].U0 @ dvs[i].Y0[t]))
+                    pb.append(_outside(torch, Ub, dvs[i].U0 @ dvs[i].Y0[t]))
                 Uo = torch.from_numpy(ost.U).to(dev)
                 U0f = torch.empty((v0.m, v0.k), dtype=torch.float32, device=dev)
                 U0b = torch.empty_like(U0f)
                 pg.prost_get_subspace(hb["f32"][0], U0f)
                 pg.prost_get_subspace(hb["bf16"][0], U0b)
                 curve[t + 1] = {"max_principal_angle_rad": max(angs), "median_principal_angle_rad": float(np.median(angs)),
-                                "to_planted_rad": {"fp32_median": float(np.median(pf)), "fp32_max": max(pf),
-                                                   "bf16_median": float(np.median(pb)), "bf16_max": max(pb)},
+                                "background_outside": {"fp32_median": float(np.median(pf)), "fp32_max": max(pf),
+                                                       "bf16_median": float(np.median(pb)), "bf16_max": max(pb)},
                                 "stream0_fp32_vs_oracle_rad": _angles_dev(torch, U0f, Uo),
                                 "stream0_bf16_vs_oracle_rad": _angles_dev(torch, U0b, Uo)}
         torch.cuda.synchronize()
@@ -496,6 +506,58 @@ def bf16_error_study(torch, pg, dev, stream, n_1080=2000, n_batch=500, every=100
         for b in bs.values():
             pg.prost_batch_destroy(b)
     return out
+
+
+def config1_study(torch, pg, dev, stream):
+    """The 160x120 grayscale stream, k = 5, all 200 frames (the first measured
+    configuration): GPU frames/s over the 200 frames run back to back as one
+    stream (per-frame CUDA events; the 0.38 MB subspace stays in L2, as it
+    would for this stream), its roofline against measured HBM, and the FP64
+    oracle timed on the same 200 frames on one host core."""
+    import oracle
+    import synth
+    vid, wp = synth.make_workload("gray160x120_k5")
+    host = vid.frames(0, vid.n_frames)
+    frames = torch.from_numpy(host).to(dev)
+    mask = torch.empty(vid.P, dtype=torch.uint8, device=dev)
+    h = pg.prost_init(pg.make_params(**wp, seed=1), stream=stream)
+    try:
+        with torch.cuda.stream(stream):
+            for t in range(5):
+                pg.prost_step(h, frames[t], mask)  # untimed warm-up (then the stream restarts)
+        torch.cuda.synchronize()
+        pg.prost_set_frame_index(h, 0)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(vid.n_frames)]
+        with torch.cuda.stream(stream):
+            for t, (a, b) in enumerate(ev):
+                a.record(stream)
+                pg.prost_step(h, frames[t], mask)
+                b.record(stream)
+        torch.cuda.synchronize()
+        assert pg.prost_sync(h) == pg.PROST_OK
+        form = pg.prost_get_stats(h).form
+    finally:
+        pg.prost_destroy(h)
+    span_ms = ev[0][0].elapsed_time(ev[-1][1])
+    launch_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    bytes_f = algorithmic_bytes(vid.m, vid.P, vid.k, wp["n_cg"], 4, 4)
+    peak, src = measured_peak_hbm()
+    prm = oracle.params(**wp)
+    st = oracle.initial_state(synth.random_orthonormal(vid.m, vid.k, 1), vid.P)
+    t0 = time.perf_counter()
+    for t in range(vid.n_frames):
+        oracle.frame_step(prm, st, host[t], want_residual=False)
+    orc_s = time.perf_counter() - t0
+    return {"workload": "gray160x120_k5", "frames": vid.n_frames,
+            "kernel_form": "cluster" if form == pg.PROST_FORM_CLUSTER else "grid",
+            "frames_per_s": vid.n_frames / (span_ms / 1e3), "pixels_per_s": vid.n_frames * vid.P / (span_ms / 1e3),
+            "launch_ms": launch_ms, "bytes_per_frame": bytes_f,
+            "roofline": {"bound": "hbm", "achieved": bytes_f / (launch_ms * 1e-3) / 1e9, "peak": peak,
+                         "frac": bytes_f / (launch_ms * 1e-3) / 1e9 / peak, "unit": "GB/s",
+                         "peak_source": f"{src} hbm_gbs", "note": "latency-bound: 7 reductions per frame over 0.38 MB"},
+            "oracle": {"frames_per_s": vid.n_frames / orc_s, "cores": 1, "seconds": orc_s,
+                       "sample": "all 200 frames, single-threaded FP64 C oracle"}}
 
 
 def pipeline_study(torch, pg, dev, stream, flush_l2, frames_timed=200, warm=10):
@@ -855,24 +917,25 @@ def run_ours(args, dist):
     if dist.rank == 0 and n == 1 and not args.no_precision:
         out["bf16_vs_fp32"] = precision_study(torch, pg, dev, stream, flush_l2)
         out["pipeline_160x120_k15"] = pipeline_study(torch, pg, dev, stream, flush_l2)
+        out["config1_gray160x120_k5"] = config1_study(torch, pg, dev, stream)
         out["batched_64_streams"] = batched_study(torch, pg, dev, stream)
         err = bf16_error_study(torch, pg, dev, stream)
         out["bf16_vs_fp32"]["error_at_length"] = err
         bt = out["batched_64_streams"]
         eb = err["batched_64_streams"]
-        tp = eb["curve"][eb["ticks"]]["to_planted_rad"]
+        tp = eb["curve"][eb["ticks"]]["background_outside"]
         e5 = err["rgb1920x1080_k15"]["curve"][err["rgb1920x1080_k15"]["frames"]]
         out["bf16_vs_fp32"]["statement"] = (
             f"BF16 batched / FP32 batched = {bt['bf16_over_f32']:.3f} aggregate frames/s at a largest principal "
             f"angle of {err['batched_64_streams']['final_max_principal_angle_rad']:.3g} rad between the BF16 and "
             f"FP32 subspaces over {err['batched_64_streams']['ticks']} frames per stream (64 streams; the FP32 "
             f"path is {err['batched_64_streams']['curve'][err['batched_64_streams']['ticks']]['stream0_fp32_vs_oracle_rad']:.2g} "
-            f"rad from the FP64 oracle on stream 0; largest angle to the planted subspace, median over streams: "
-            f"FP32 {tp['fp32_median']:.3g}, BF16 {tp['bf16_median']:.3g} rad; mask disagreement "
+            f"rad from the FP64 oracle on stream 0; planted background energy outside the subspace, median over "
+            f"streams: FP32 {tp['fp32_median']:.3g}, BF16 {tp['bf16_median']:.3g}; mask disagreement "
             f"{eb['mask_disagreement_mean']:.2g}); 1080p k = 15: {out['bf16_vs_fp32']['bf16_over_fp32']:.3f}x at "
             f"{err['rgb1920x1080_k15']['final_principal_angle_rad']:.3g} rad over {err['rgb1920x1080_k15']['frames']} "
-            f"frames (to the planted subspace: FP32 {e5['fp32_to_planted_rad']:.3g}, BF16 "
-            f"{e5['bf16_to_planted_rad']:.3g} rad)")
+            f"frames (planted background energy outside: FP32 {e5['fp32_background_outside']:.3g}, BF16 "
+            f"{e5['bf16_background_outside']:.3g})")
         out["window_320x240_n64_k10"] = window_study(torch, pg, dev)
     if dist.rank == 0 and n == 1 and not args.no_cpu_baseline:
         fps, nf, secs = oracle_sample(args.workload, args.cpu_seconds)

@@ -442,6 +442,18 @@ int prost_pre_apply(prost_pre *p, const void *frame, int on_device, float *out);
 /* The running statistics (synchronises): mean_out (host, channels*h_out*w_out
  * floats, or NULL), the standard deviation, the frames counted so far. */
 int prost_pre_get_stats(prost_pre *p, float *mean_out, double *sigma_out, int32_t *frames_out);
+/* Checkpoint of the running statistics (Section 3.4's initialisation phase).
+ * prost_pre_get_state() with buf = NULL stores the needed size in *len;
+ * otherwise writes the frames counted, the FP64 running sums of the entries
+ * and of their squares, the deviation and the per-entry mean plane, behind a
+ * header with the geometry, frame type and i_init, into buf (host, *len bytes
+ * available) and sets *len to the bytes written.  prost_pre_set_state()
+ * restores them into a pre-processor made with the same sizes, frame type and
+ * i_init, which then continues bit-identically, inside the initialisation
+ * phase or after it.  Both synchronise the stream.  PROST_EINVAL for NULL, a
+ * short or malformed buffer, or one made with other parameters. */
+int prost_pre_get_state(prost_pre *p, void *buf, size_t *len);
+int prost_pre_set_state(prost_pre *p, const void *buf, size_t len);
 const char *prost_pre_last_error(const prost_pre *p);
 void prost_pre_destroy(prost_pre *p);
 

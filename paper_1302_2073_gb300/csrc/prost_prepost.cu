@@ -337,6 +337,81 @@ extern "C" int prost_pre_get_stats(prost_pre *p, float *mean_out, double *sigma_
     return PROST_OK;
 }
 
+namespace {
+
+// Checkpoint layout: this header, then the mean plane (n_out floats).
+struct PreStateHeader {
+    char magic[8];
+    uint32_t version, header_bytes;
+    int32_t w_in, h_in, C, w_out, h_out, fdt, i_init, n;
+    double sums[2]; // FP64 running sums of v and v^2 over the frames counted
+    float sigma;
+    uint32_t pad;
+    uint64_t mean_bytes;
+};
+
+} // namespace
+
+extern "C" int prost_pre_get_state(prost_pre *p, void *buf, size_t *len)
+{
+    if (!p || !len) return PROST_EINVAL;
+    const size_t mean_bytes = (size_t)p->g.n_out * sizeof(float);
+    const size_t need = sizeof(PreStateHeader) + mean_bytes;
+    if (!buf) {
+        *len = need;
+        return PROST_OK;
+    }
+    if (*len < need) { p->err = "buffer too small"; return PROST_EINVAL; }
+    PreStateHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "PROSTPR1", 8);
+    hd.version = 1;
+    hd.header_bytes = sizeof(hd);
+    hd.w_in = p->g.w_in;
+    hd.h_in = p->g.h_in;
+    hd.C = p->g.C;
+    hd.w_out = p->g.w_out;
+    hd.h_out = p->g.h_out;
+    hd.fdt = p->fdt;
+    hd.i_init = p->i_init;
+    hd.n = p->n;
+    hd.mean_bytes = mean_bytes;
+    PRE_CK(cudaStreamSynchronize(p->stream));
+    PRE_CK(cudaMemcpy(hd.sums, p->sums, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    PRE_CK(cudaMemcpy(&hd.sigma, p->sigma, sizeof(float), cudaMemcpyDeviceToHost));
+    char *b = static_cast<char *>(buf);
+    memcpy(b, &hd, sizeof(hd));
+    PRE_CK(cudaMemcpy(b + sizeof(hd), p->mean, mean_bytes, cudaMemcpyDeviceToHost));
+    *len = need;
+    return PROST_OK;
+}
+
+extern "C" int prost_pre_set_state(prost_pre *p, const void *buf, size_t len)
+{
+    if (!p || !buf) return PROST_EINVAL;
+    PreStateHeader hd;
+    if (len < sizeof(hd)) { p->err = "buffer too small"; return PROST_EINVAL; }
+    memcpy(&hd, buf, sizeof(hd));
+    const size_t mean_bytes = (size_t)p->g.n_out * sizeof(float);
+    if (memcmp(hd.magic, "PROSTPR1", 8) != 0 || hd.version != 1 || hd.header_bytes != sizeof(hd) ||
+        hd.mean_bytes != mean_bytes || len < sizeof(hd) + mean_bytes) {
+        p->err = "not a pre-processor state buffer of this version";
+        return PROST_EINVAL;
+    }
+    if (hd.w_in != p->g.w_in || hd.h_in != p->g.h_in || hd.C != p->g.C || hd.w_out != p->g.w_out ||
+        hd.h_out != p->g.h_out || hd.fdt != p->fdt || hd.i_init != p->i_init || hd.n < 0 || hd.n > p->i_init ||
+        !(hd.sigma > 0.f)) {
+        p->err = "the state was made with other sizes, frame type or i_init";
+        return PROST_EINVAL;
+    }
+    PRE_CK(cudaStreamSynchronize(p->stream));
+    PRE_CK(cudaMemcpy(p->sums, hd.sums, 2 * sizeof(double), cudaMemcpyHostToDevice));
+    PRE_CK(cudaMemcpy(p->sigma, &hd.sigma, sizeof(float), cudaMemcpyHostToDevice));
+    PRE_CK(cudaMemcpy(p->mean, static_cast<const char *>(buf) + sizeof(hd), mean_bytes, cudaMemcpyHostToDevice));
+    p->n = hd.n;
+    return PROST_OK;
+}
+
 extern "C" const char *prost_pre_last_error(const prost_pre *p)
 {
     return p ? p->err.c_str() : g_pre_err.c_str();

@@ -95,6 +95,8 @@ def lib():
         L.prost_pre_init.argtypes = [C.c_int32] * 7 + [vp, P(vp)]
         L.prost_pre_apply.argtypes = [vp, vp, C.c_int, vp]
         L.prost_pre_get_stats.argtypes = [vp, vp, P(C.c_double), P(C.c_int32)]
+        L.prost_pre_get_state.argtypes = [vp, vp, P(sz)]
+        L.prost_pre_set_state.argtypes = [vp, vp, sz]
         L.prost_pre_last_error.argtypes = [vp]
         L.prost_pre_last_error.restype = C.c_char_p
         L.prost_pre_destroy.argtypes = [vp]
@@ -494,6 +496,20 @@ def prost_pre_get_stats(p, mean_out=None):
     n = C.c_int32(0)
     _check_pre(lib().prost_pre_get_stats(p, _ptr(mean_out), C.byref(sd), C.byref(n)), p)
     return sd.value, n.value
+
+
+def prost_pre_get_state(p):
+    """The pre-processor's running statistics as bytes (checkpoint)."""
+    n = C.c_size_t(0)
+    _check_pre(lib().prost_pre_get_state(p, None, C.byref(n)), p)
+    buf = C.create_string_buffer(n.value)
+    _check_pre(lib().prost_pre_get_state(p, buf, C.byref(n)), p)
+    return buf.raw[:n.value]
+
+
+def prost_pre_set_state(p, state: bytes):
+    buf = C.create_string_buffer(state, len(state))
+    return _check_pre(lib().prost_pre_set_state(p, buf, len(state)), p)
 
 
 def prost_pre_last_error(p=None):

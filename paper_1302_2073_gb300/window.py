@@ -1,9 +1,10 @@
 """The windowed cost as a torch.autograd.Function.
 
-Forward and backward are the C ABI's window kernels (prost_window_eval): the
-forward writes the cost, the backward runs the pass again and writes dF/dU,
-dF/dY and dF/dmu multiplied by the upstream gradient inside the kernel, so no
-arithmetic of the method runs in PyTorch, which only supplies device memory.
+The forward is the C ABI's window kernel (prost_window_eval).  When an input
+needs a gradient, that one pass also writes dF/dU, dF/dY and dF/dmu (the
+hand-written adjoint), which the backward only scales by the upstream
+gradient; otherwise the pass writes the cost alone.  No arithmetic of the
+method runs in PyTorch, which supplies device memory and the scaling.
 """
 
 from __future__ import annotations
@@ -26,22 +27,19 @@ def _autograd_fn():
                 if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
                     raise ValueError("U, Y, mu and X must be contiguous float32 CUDA tensors")
             cost = torch.empty((), dtype=torch.float32, device=U.device)
-            _p.prost_window_eval(win.handle, U, Y, X, labels, mu, cost)
-            ctx.win = win
-            ctx.labels = labels
-            ctx.save_for_backward(U, Y, mu, X)
+            if any(ctx.needs_input_grad[:3]):
+                dU, dY, dmu = torch.empty_like(U), torch.empty_like(Y), torch.empty_like(mu)
+                _p.prost_window_eval(win.handle, U, Y, X, labels, mu, cost, dU, dY, dmu)
+                ctx.save_for_backward(dU, dY, dmu)
+            else:
+                _p.prost_window_eval(win.handle, U, Y, X, labels, mu, cost)
             return cost
 
         @staticmethod
         def backward(ctx, g):
-            U, Y, mu, X = ctx.saved_tensors
-            g = g.contiguous()
-            dU = torch.empty_like(U)
-            dY = torch.empty_like(Y)
-            dmu = torch.empty_like(mu)
-            cost = torch.empty((), dtype=torch.float32, device=U.device)
-            _p.prost_window_eval(ctx.win.handle, U, Y, X, ctx.labels, mu, cost, dU, dY, dmu, gscale=g)
-            return dU, dY, dmu, None, None, None
+            dU, dY, dmu = ctx.saved_tensors
+            return (dU * g if ctx.needs_input_grad[0] else None, dY * g if ctx.needs_input_grad[1] else None,
+                    dmu * g if ctx.needs_input_grad[2] else None, None, None, None)
 
     _FN = WindowFn
     return _FN

@@ -116,6 +116,8 @@ int main(void)
     check(prost_inject_wait_timeout(NULL, 0, 1000) == PROST_EINVAL, "wait injection without a handle");
     check(prost_step_async(NULL, NULL, NULL, NULL) == PROST_EINVAL, "pipelined step without a handle");
     check(prost_wait(NULL) == PROST_EINVAL, "wait without a handle");
+    check(prost_pre_get_state(NULL, NULL, NULL) == PROST_EINVAL, "pre-processor checkpoint without a handle");
+    check(prost_pre_set_state(NULL, NULL, 0) == PROST_EINVAL, "pre-processor restore without a handle");
     check(prost_window_inject_wait_timeout(NULL, 1, 1000) == PROST_EINVAL, "window wait injection without a window");
     check(prost_batch_split(10, 3, w, cap, ctas) == PROST_OK, "batch split");
     check(ctas[0] == 4 && ctas[1] == 3 && ctas[2] == 3, "batch split of 10 over thirds");

@@ -77,6 +77,8 @@ def test_null_arguments_are_rejected():
     assert L.prost_inject_wait_timeout(None, 0, 1000) == pg.PROST_EINVAL
     assert L.prost_step_async(None, None, None, None) == pg.PROST_EINVAL
     assert L.prost_wait(None) == pg.PROST_EINVAL
+    assert L.prost_pre_get_state(None, None, None) == pg.PROST_EINVAL
+    assert L.prost_pre_set_state(None, None, 0) == pg.PROST_EINVAL
     assert L.prost_window_inject_wait_timeout(None, 1, 1000) == pg.PROST_EINVAL
     L.prost_destroy(None)
 

@@ -147,3 +147,51 @@ def test_pipeline_pre_tracker_median_against_the_oracle():
     finally:
         pg.prost_destroy(hdl)
         pg.prost_pre_destroy(p)
+
+
+@pytest.mark.parametrize("cut", [0, 3, 6, 9])
+def test_pre_processing_resumes_bit_identically_from_a_checkpoint(cut):
+    """A pre-processor restored from a checkpoint taken after `cut` frames
+    (before, inside and after its 6-frame initialisation phase) gives the same
+    output bits as the one that never stopped."""
+    rng = np.random.default_rng(17)
+    frames = [rng.integers(0, 256, size=(3, 96, 128)).astype(np.uint8) for _ in range(11)]
+    a = pg.prost_pre_init(128, 96, 3, 40, 30, "u8", 6)
+    b = pg.prost_pre_init(128, 96, 3, 40, 30, "u8", 6)
+    try:
+        out_a = []
+        ck = None
+        for t, f in enumerate(frames):
+            if t == cut:
+                ck = pg.prost_pre_get_state(a)
+            o = np.empty(3 * 30 * 40, np.float32)
+            pg.prost_pre_apply(a, f, o)
+            out_a.append(o)
+        if ck is None:
+            ck = pg.prost_pre_get_state(a)
+        pg.prost_pre_set_state(b, ck)
+        for t in range(cut, len(frames)):
+            o = np.empty(3 * 30 * 40, np.float32)
+            pg.prost_pre_apply(b, frames[t], o)
+            assert np.array_equal(o, out_a[t]), t
+        ma, mb = np.empty(3 * 30 * 40, np.float32), np.empty(3 * 30 * 40, np.float32)
+        sa, sb = pg.prost_pre_get_stats(a, ma), pg.prost_pre_get_stats(b, mb)
+        assert np.array_equal(ma, mb) and sa == sb
+    finally:
+        pg.prost_pre_destroy(a)
+        pg.prost_pre_destroy(b)
+
+
+def test_pre_processing_checkpoint_refuses_other_parameters():
+    a = pg.prost_pre_init(128, 96, 3, 40, 30, "u8", 6)
+    b = pg.prost_pre_init(128, 96, 3, 40, 30, "u8", 5)
+    try:
+        ck = pg.prost_pre_get_state(a)
+        with pytest.raises(pg.ProstError) as ei:
+            pg.prost_pre_set_state(b, ck)
+        assert ei.value.code == pg.PROST_EINVAL
+        with pytest.raises(pg.ProstError):
+            pg.prost_pre_set_state(a, ck[:-4])
+    finally:
+        pg.prost_pre_destroy(a)
+        pg.prost_pre_destroy(b)

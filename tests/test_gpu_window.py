@@ -17,6 +17,9 @@ pytestmark = pytest.mark.gpu
 # norm-relative errors stay near 1e-6
 COST_RTOL = 1e-5
 GRAD_RTOL = 1e-5
+# per entry: an FP32 sum of n frame terms (dU) or of a tile's rows then FP64
+# across tiles (dY), against the largest entry of the gradient
+ELEM_RTOL = 1e-5
 
 
 @pytest.fixture(autouse=True)
@@ -70,6 +73,10 @@ def test_cost_and_gradients_match_the_oracle(m, C, k, n, labels_on):
     assert _rel(gU, 3 * dU) <= GRAD_RTOL
     assert _rel(gY, 3 * dY) <= GRAD_RTOL
     assert abs(gmu - 3 * dmu) <= GRAD_RTOL * 3 * dmu
+    # element by element, scaled by the largest entry: an error confined to a
+    # few rows would pass the norms above but not this
+    assert np.max(np.abs(gU - 3 * dU)) <= ELEM_RTOL * np.max(np.abs(3 * dU))
+    assert np.max(np.abs(gY - 3 * dY)) <= ELEM_RTOL * np.max(np.abs(3 * dY))
 
 
 def test_gradients_against_central_differences_of_the_gpu_cost():
@@ -141,3 +148,29 @@ def test_argument_checks():
         pg.prost_window_init(100, 1, 17, 8)    # k > 16
     with pytest.raises(pg.ProstError):
         pg.prost_window_init(100, 1, 4, 129)   # n > 128
+
+
+def test_gradient_scale_in_the_kernel():
+    """prost_window_eval's gscale multiplies the three gradients inside the
+    pass (the C ABI's form of an upstream gradient)."""
+    m, C, k, n = 3000, 1, 5, 6
+    U, Y, X, labels = _case(m, C, k, n, seed=9)
+    w = pg.prost_window_init(m, C, k, n, 0.25, 5e-5)
+    try:
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        Ut, Yt, Xt, Lt = dev(U), dev(Y), dev(X), dev(labels)
+        mu = torch.tensor(0.05, dtype=torch.float32, device="cuda")
+        g = torch.tensor(-2.5, dtype=torch.float32, device="cuda")
+        outs = []
+        for gs in (None, g):
+            c = torch.empty((), dtype=torch.float32, device="cuda")
+            dU, dY, dmu = torch.empty_like(Ut), torch.empty_like(Yt), torch.empty_like(mu)
+            pg.prost_window_eval(w, Ut, Yt, Xt, Lt, mu, c, dU, dY, dmu, gscale=gs)
+            outs.append((float(c), dU.cpu().numpy(), dY.cpu().numpy(), float(dmu)))
+    finally:
+        pg.prost_window_destroy(w)
+    (c1, u1, y1, m1), (c2, u2, y2, m2) = outs
+    assert c1 == c2
+    np.testing.assert_allclose(u2, -2.5 * u1, rtol=1e-6, atol=1e-30)
+    np.testing.assert_allclose(y2, -2.5 * y1, rtol=1e-6, atol=1e-30)
+    assert m2 == pytest.approx(-2.5 * m1, rel=1e-6)
