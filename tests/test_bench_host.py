@@ -66,7 +66,7 @@ def test_l2_roofline_arithmetic():
     assert r["bound"] == "l2" and r["unit"] == "GB/s"
     assert r["frac"] == pytest.approx(2746.0 / r["peak"])
     # slices x sectors/cycle x bytes/sector x L2 clock, from the capture
-    assert r["peak"] == pytest.approx(188 * 3 * 32 * 2.002765, rel=1e-4)
+    assert r["peak"] == pytest.approx(188 * 3 * 32 * 2.001746, rel=1e-4)
     assert bench.l2_roofline(2746.0, False) is None
 
 
