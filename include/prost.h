@@ -86,13 +86,21 @@ extern "C" {
  * hardware cluster barrier, for small subspaces where the grid barriers of
  * many CTAs would cost more than the streaming.  AUTO picks CLUSTER when the
  * stored subspace takes at most PROST_CLUSTER_MAX_U_BYTES and a cluster fits
- * the device, else GRID.  Failure injection (prost_inject_*) needs GRID. */
+ * the device, else GRID.  PASSES: the frame as a sequence of ordinary
+ * launches, one per pass over the rows (two per CG iteration: the gradient,
+ * then the curvature sum_e c_e (u_e^T d)^2 of the line step), with k chosen at
+ * run time; float32 storage only.  GRID and CLUSTER exist for
+ * k <= PROST_MAX_K_SINGLE; PASSES for every k and the only form above it, which
+ * AUTO then picks.  Failure injection (prost_inject_*) needs GRID. */
 #define PROST_FORM_AUTO 0
 #define PROST_FORM_GRID 1
 #define PROST_FORM_CLUSTER 2
+#define PROST_FORM_PASSES 3
 #define PROST_CLUSTER_MAX_U_BYTES (1u << 20)
 
-#define PROST_MAX_K 16
+#define PROST_MAX_K 32        /* largest subspace dimension (PASSES form above PROST_MAX_K_SINGLE) */
+#define PROST_MAX_K_SINGLE 16 /* largest k of the single-launch forms (GRID, CLUSTER) */
+#define PROST_STATIC_MAX_K 16 /* largest k of prost_cost_grad_static() */
 #define PROST_MAX_CG 32
 
 typedef struct prost_handle prost_handle;
@@ -111,7 +119,8 @@ typedef struct prost_params {
     int32_t frame_dtype;             /* PROST_U8 or PROST_F32 */
     int32_t u_dtype;                 /* PROST_F32 or PROST_BF16 (subspace storage) */
     int32_t mask_from;               /* PROST_MASK_POST_UPDATE or PROST_MASK_PRE_UPDATE */
-    int32_t form;                    /* kernel form: PROST_FORM_AUTO (0), PROST_FORM_GRID or PROST_FORM_CLUSTER */
+    int32_t form;                    /* kernel form: PROST_FORM_AUTO (0), PROST_FORM_GRID, PROST_FORM_CLUSTER
+                                        or PROST_FORM_PASSES */
     uint64_t seed;                   /* seed of the random initial subspace (Section 3.4) */
 } prost_params;
 
@@ -139,7 +148,7 @@ typedef struct prost_stats {
                                         by an extra pass over U: the identity
                                         |pi(eta)|^2 = |eta|^2 - |U^T eta|^2 (Eq. gproject)
                                         loses its digits when |pi(eta)|^2 < |eta|^2 / 4 */
-    int32_t form;                    /* PROST_FORM_GRID or PROST_FORM_CLUSTER: the handle's frame kernel */
+    int32_t form;                    /* PROST_FORM_GRID, PROST_FORM_CLUSTER or PROST_FORM_PASSES: the handle's form */
 } prost_stats;
 
 /* Sizes of the device state of a handle with these parameters (bytes, device
@@ -197,8 +206,8 @@ int prost_sync(prost_handle *h);
  * that gave up part-way leaves it.  The next frame launch finds the count
  * outside the range it expects and returns at once, leaving the state
  * untouched; on the host path prost_step() returns PROST_ETIMEOUT and leaves
- * its outputs unwritten.  Grid form only (PROST_EINVAL for the cluster form,
- * which has no software barrier).  The following prost_sync() reports PROST_ETIMEOUT
+ * its outputs unwritten.  Grid form only (PROST_EINVAL for the cluster and
+ * passes forms, which have no software grid barrier).  The following prost_sync() reports PROST_ETIMEOUT
  * and resets the barrier, and later frames run normally (the refused frame
  * does not count towards the periodic rebase).  A launch can only detect a
  * backward skew (delta < 0) or a forward one of at least the frame kernel's
@@ -216,7 +225,7 @@ int prost_inject_barrier_skew(prost_handle *h, int64_t delta);
  * host path prost_step() returns PROST_ETIMEOUT, and prost_sync() reports
  * PROST_ETIMEOUT and resets the barrier.  Applies to one launch.  Grid form
  * only.  Errors: PROST_EINVAL (NULL handle, pass or cycles out of range, the
- * cluster form). */
+ * cluster or passes form). */
 int prost_inject_wait_timeout(prost_handle *h, int32_t pass, int64_t cycles);
 
 /* Copy out the current subspace (the re-orthonormalised representative,
@@ -300,7 +309,8 @@ int prost_get_timing(prost_handle *h, float *ms, int *n);
  *              float32 frame has a non-finite entry (out is then not finite)
  *   stream     cudaStream_t as void* (NULL = default stream)
  * The call only enqueues work on the stream; read out after synchronising it.
- * Limits: k <= PROST_MAX_K (the width of the static partial rows), m <= 2^30.
+ * Limits: k <= PROST_STATIC_MAX_K (the width of the static partial rows),
+ * m <= 2^30.
  * Larger k, bad parameters or NULL pointers return PROST_EINVAL; a failed CUDA
  * call returns PROST_ECUDA.  No detail string is recorded.
  * The first call on each device looks up the array's device address
@@ -338,7 +348,9 @@ void prost_destroy(prost_handle *h);
  * CTAs are split between its streams, and with the CUDA graph on (the
  * default) a whole tick is one graph launch.  Each stream computes exactly what
  * a prost_handle with its parameters computes (Steps 1-3 of Section 3.3), up to
- * the summation order of its reductions.
+ * the summation order of its reductions.  Every stream must run a
+ * single-launch form: k <= PROST_MAX_K_SINGLE and form AUTO, GRID or CLUSTER
+ * (PROST_EINVAL otherwise).
  * The batch owns its handles; prost_batch_stream() lends one (for
  * prost_get_subspace, prost_get_stats, checkpoints...; frames must go through
  * prost_batch_step while the batch lives).  Work is ordered on the given stream.

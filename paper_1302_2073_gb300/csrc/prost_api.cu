@@ -25,6 +25,7 @@ struct prost_handle {
     int num_sms;
     int grid_frame, grid_gram;
     int cluster_grid;      // > 0: the frame kernel runs as one cluster of this many CTAs
+    int wide;              // the passes form (a sequence of ordinary launches per frame)
     void *U;               // stored subspace (C x npt tile blocks of k x TILE_P float32 or bfloat16)
     uint8_t *labels;       // previous labels (Pp bytes)
     KState *ks;
@@ -121,7 +122,7 @@ int check_params(const prost_params *prm, DevParams *dp, std::string *why)
     if (p.channels < 1 || p.channels > 4) { *why = "channels must be 1..4"; return PROST_EINVAL; }
     const int64_t P = (int64_t)p.width * p.height, m = m_of(p);
     if (m > (int64_t)1 << 30) { *why = "frame too large (m > 2^30)"; return PROST_EINVAL; }
-    if (p.k < 1 || p.k > KMAX || (int64_t)p.k > m) { *why = "k must be in 1..min(m, 16)"; return PROST_EINVAL; }
+    if (p.k < 1 || p.k > KMAX || (int64_t)p.k > m) { *why = "k must be in 1..min(m, 32)"; return PROST_EINVAL; }
     if (!(p.p > 0.0 && p.p <= 2.0)) { *why = "p must be in (0, 2]"; return PROST_EINVAL; }
     if (!(p.delta > 0.0) || !isfinite(p.delta)) { *why = "delta must be positive"; return PROST_EINVAL; }
     double mu = p.mu;
@@ -135,7 +136,10 @@ int check_params(const prost_params *prm, DevParams *dp, std::string *why)
     if (p.frame_dtype != PROST_U8 && p.frame_dtype != PROST_F32) { *why = "frame_dtype must be PROST_U8 or PROST_F32"; return PROST_EINVAL; }
     if (p.u_dtype != PROST_F32 && p.u_dtype != PROST_BF16) { *why = "u_dtype must be PROST_F32 or PROST_BF16"; return PROST_EINVAL; }
     if (p.mask_from != PROST_MASK_POST_UPDATE && p.mask_from != PROST_MASK_PRE_UPDATE) { *why = "mask_from must be 0 or 1"; return PROST_EINVAL; }
-    if (p.form != PROST_FORM_AUTO && p.form != PROST_FORM_GRID && p.form != PROST_FORM_CLUSTER) { *why = "form must be PROST_FORM_AUTO, PROST_FORM_GRID or PROST_FORM_CLUSTER"; return PROST_EINVAL; }
+    if (p.form != PROST_FORM_AUTO && p.form != PROST_FORM_GRID && p.form != PROST_FORM_CLUSTER && p.form != PROST_FORM_PASSES) { *why = "form must be PROST_FORM_AUTO, PROST_FORM_GRID, PROST_FORM_CLUSTER or PROST_FORM_PASSES"; return PROST_EINVAL; }
+    const bool passes = p.form == PROST_FORM_PASSES || p.k > KFRAME;
+    if (p.k > KFRAME && p.form != PROST_FORM_AUTO && p.form != PROST_FORM_PASSES) { *why = "k > 16 runs in the passes form only (form AUTO or PROST_FORM_PASSES)"; return PROST_EINVAL; }
+    if (passes && p.u_dtype != PROST_F32) { *why = "the passes form (every k > 16) stores the subspace in float32 only"; return PROST_EINVAL; }
     if (dp) {
         memset(dp, 0, sizeof(*dp));
         dp->P = P;
@@ -258,7 +262,7 @@ struct StateHeader {
 
 extern "C" {
 
-int prost_version(void) { return 101; }
+int prost_version(void) { return 102; }
 
 const char *prost_strerror(int code)
 {
@@ -299,7 +303,8 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     int rc = check_params(prm, &dp, &why);
     if (rc) { g_init_err = why; return rc; }
     load_ops();
-    const KernelOps *ops = g_ops[prm->u_dtype == PROST_BF16 ? 1 : 0][prm->k];
+    const bool wide = prm->form == PROST_FORM_PASSES || prm->k > KFRAME;
+    const KernelOps *ops = wide ? wide_ops() : g_ops[prm->u_dtype == PROST_BF16 ? 1 : 0][prm->k];
     if (!ops) { g_init_err = "no kernel set for this k"; return PROST_EINVAL; }
 
     prost_handle *h = new (std::nothrow) prost_handle();
@@ -307,6 +312,7 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     h->prm = *prm;
     h->dp = dp;
     h->ops = ops;
+    h->wide = wide ? 1 : 0;
     h->stream = (cudaStream_t)stream;
     h->U = nullptr; h->labels = nullptr; h->ks = nullptr; h->partials = nullptr;
     h->counter = nullptr; h->frame_buf = nullptr; h->bg_buf = nullptr; h->u_buf = nullptr;
@@ -340,6 +346,7 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     if (occ < 1) { h->err = "the frame kernel does not fit on this device"; return bail(PROST_ECUDA); }
     if (ops->tile != TILE_P) { h->err = "tile size mismatch"; return bail(PROST_ECUDA); }
     int64_t gf = (int64_t)occ * h->num_sms;
+    if (wide) gf = 1;              // the passes form sizes its own launches
     if (gf > dp.npt) gf = dp.npt;  // every CTA gets at least one pixel tile
     // the cross-CTA reduction's unit sums fit its shared scratch
     if (gf > max_frame_grid((int)partial_row(prm->k))) gf = max_frame_grid((int)partial_row(prm->k));
@@ -350,7 +357,7 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     h->cluster_grid = 0;
     {
         const size_t ub = (size_t)prm->k * dp.C * dp.Pp * u_elem_bytes(dp);
-        if (prm->form == PROST_FORM_CLUSTER || (prm->form == PROST_FORM_AUTO && ub <= PROST_CLUSTER_MAX_U_BYTES)) {
+        if (!wide && (prm->form == PROST_FORM_CLUSTER || (prm->form == PROST_FORM_AUTO && ub <= PROST_CLUSTER_MAX_U_BYTES))) {
             int g = 16;
             while (g > 1 && (g > dp.npt || g > h->grid_frame)) g /= 2;
             while (g >= 1 && ops->cluster_fit(fdt, g) < 1) g /= 2;
@@ -365,6 +372,7 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     // the Gram kernel's rows, or the frame kernel's two value-major buffers
     h->partial_floats = std::max((size_t)h->grid_gram * partial_row(prm->k),
                                  (size_t)2 * col_stride(h->grid_frame) * partial_row(prm->k));
+    if (wide) h->partial_floats = wide_partial_floats(dp, h->num_sms);
 
     CKI(cudaMalloc(&h->U, (size_t)prm->k * dp.C * dp.Pp * u_elem_bytes(dp)));
     CKI(cudaMalloc(&h->labels, (size_t)dp.Pp));
@@ -421,6 +429,7 @@ int launch_frame(prost_handle *h, const void *fptr, int64_t pitch, uint8_t *mask
     fa.stall_at = h->stall_at;
     fa.stall_limit = h->stall_limit;
     fa.status_out = status_dev;
+    fa.counter = h->counter;
     h->stall_at = 0; // one launch only
     fa.prm = h->dp;
     if (h->timing) CK(h, cudaEventRecord(h->ev[0], h->stream));
@@ -433,7 +442,7 @@ int launch_frame(prost_handle *h, const void *fptr, int64_t pitch, uint8_t *mask
         h->timed_frames += 1;
     }
     // the grid barrier's arrivals (the cluster form does not use it)
-    if (!cl) h->bar_base += (unsigned long long)grid * (unsigned long long)frame_arrivals(h->prm.n_cg);
+    if (!cl && !h->wide) h->bar_base += (unsigned long long)grid * (unsigned long long)frame_arrivals(h->prm.n_cg);
     // The frame kernel updates the stored rows in the stored basis (U = U_st T);
     // every REBASE_EVERY frames the stored rows are moved onto the orthonormal
     // representative so that the conditioning of U_st cannot drift.  The
@@ -590,6 +599,7 @@ int prost_inject_barrier_skew(prost_handle *h, int64_t delta)
     // a forward skew below the grid size looks like CTAs that already arrived:
     // the launch cannot tell it from a healthy barrier
     if (h->cluster_grid > 0) return fail(h, PROST_EINVAL, "the cluster form has no grid barrier");
+    if (h->wide) return fail(h, PROST_EINVAL, "the passes form has no grid barrier");
     if (delta > 0 && delta < (int64_t)h->grid_frame)
         return fail(h, PROST_EINVAL, "a forward skew below the grid size is not detectable");
     DeviceGuard dg(h->device);
@@ -606,6 +616,7 @@ int prost_inject_wait_timeout(prost_handle *h, int32_t pass, int64_t cycles)
     if (!h) return PROST_EINVAL;
     if (pass < 0 || pass > h->prm.n_cg) return fail(h, PROST_EINVAL, "pass must be in 0..n_cg");
     if (h->cluster_grid > 0) return fail(h, PROST_EINVAL, "the cluster form has no software barrier to stall");
+    if (h->wide) return fail(h, PROST_EINVAL, "the passes form has no grid barrier to stall");
     if (cycles < 1 || cycles > 2000000000ll) return fail(h, PROST_EINVAL, "cycles must be in 1..2e9");
     h->stall_at = pass + 1;
     h->stall_limit = cycles;
@@ -724,7 +735,7 @@ int prost_get_stats(prost_handle *h, prost_stats *out)
     out->orth_err = ks.orth_err;
     out->eta_norm = ks.eta_norm;
     out->pi_explicit = ks.pi_explicit;
-    out->form = h->cluster_grid > 0 ? PROST_FORM_CLUSTER : PROST_FORM_GRID;
+    out->form = h->wide ? PROST_FORM_PASSES : (h->cluster_grid > 0 ? PROST_FORM_CLUSTER : PROST_FORM_GRID);
     return PROST_OK;
 }
 
@@ -740,7 +751,7 @@ int prost_get_state(prost_handle *h, void *buf, size_t *len)
     StateHeader hd;
     memset(&hd, 0, sizeof(hd));
     memcpy(hd.magic, "PROSTST1", 8);
-    hd.version = 3; // 3: the k-space state with |eta| and the projection-pass flag
+    hd.version = 4; // 4: the k-space state 32 wide, with the passes form's vectors
     hd.header_bytes = sizeof(StateHeader);
     hd.prm = h->prm;
     hd.u_bytes = u_bytes;
@@ -768,7 +779,7 @@ int prost_set_state(prost_handle *h, const void *buf, size_t len)
     if (len < sizeof(StateHeader)) return fail(h, PROST_EINVAL, "state buffer too short");
     StateHeader hd;
     memcpy(&hd, buf, sizeof(hd));
-    if (memcmp(hd.magic, "PROSTST1", 8) != 0 || hd.version != 3 || hd.header_bytes != sizeof(StateHeader))
+    if (memcmp(hd.magic, "PROSTST1", 8) != 0 || hd.version != 4 || hd.header_bytes != sizeof(StateHeader))
         return fail(h, PROST_EINVAL, "not a prost state buffer of this version");
     prost_params a = hd.prm, b = h->prm;
     a.seed = b.seed = 0;
@@ -1042,6 +1053,11 @@ extern "C" int prost_batch_init(const prost_params *prms, int32_t n, void *strea
         return code;
     };
     g_init_err.clear();
+    for (int i = 0; i < n; ++i)
+        if (prms[i].k > KFRAME || prms[i].form == PROST_FORM_PASSES) {
+            g_init_err = "stream " + std::to_string(i) + ": a batch runs the single-launch forms only (k <= 16, form not PASSES)";
+            return bail(PROST_EINVAL);
+        }
     for (int i = 0; i < n; ++i) {
         prost_handle *h = nullptr;
         const int rc = prost_init(&prms[i], stream, &h);

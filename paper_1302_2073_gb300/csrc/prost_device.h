@@ -7,7 +7,8 @@
 
 namespace prost {
 
-constexpr int KMAX = 16;     // largest subspace dimension with a compiled kernel set
+constexpr int KMAX = 32;     // largest subspace dimension (k-space state arrays are this wide)
+constexpr int KFRAME = 16;   // largest k with a compiled single-launch frame kernel set
 constexpr int CGMAX = 32;    // largest number of CG iterations per frame
 constexpr int THREADS = 256; // threads per CTA of the Gram and layout kernels
 constexpr int TILE_P = 224;  // pixels per tile of the stored subspace (16-byte multiple for uint8)
@@ -62,6 +63,13 @@ struct KState {
     // barrier passed, all rows reduced, CG step done; update-pass rows done,
     // partial row written, arrived; last CTA: rows reduced, factors done
     uint64_t sub_ts[10];
+    // k-space vectors of the pass-sequence form (one launch per pass), kept
+    // here between its launches: d, the previous g, s = T d, T v, T g,
+    // w = R^T v; d^T g, |y|, cos(theta) - 1, sin(theta) / |pi(eta)|
+    float wd[KMAX], wgp[KMAX], ws[KMAX], wtv[KMAX], wtg[KMAX], ww[KMAX];
+    float wdg, wyn, wcm1, wsnp;
+    int32_t wskip;             // the frame was rejected (non-finite entry)
+    int32_t wproj;             // the final step asked for the explicit projection pass
 };
 
 constexpr uint32_t ERR_BADFRAME = 1u, ERR_NOTSPD = 2u, ERR_TIMEOUT = 4u;
@@ -128,6 +136,7 @@ struct FrameArgs {
     int stall_at;
     long long stall_limit;
     int32_t *status_out;      // optional (device): the frame's status, as last_status
+    unsigned int *counter;    // arrival counter of the pass-sequence form's reductions (zero between launches)
     DevParams prm;
 };
 
@@ -170,5 +179,9 @@ void register_ops_k09_10(const KernelOps **f32, const KernelOps **bf16);
 void register_ops_k11_12(const KernelOps **f32, const KernelOps **bf16);
 void register_ops_k13_14(const KernelOps **f32, const KernelOps **bf16);
 void register_ops_k15_16(const KernelOps **f32, const KernelOps **bf16);
+// the pass-sequence form (k at run time, 1..KMAX, float32 stored rows) and the
+// floats of partial sums it needs (prost_wide.cu)
+const KernelOps *wide_ops();
+size_t wide_partial_floats(const DevParams &prm, int sms);
 
 } // namespace prost

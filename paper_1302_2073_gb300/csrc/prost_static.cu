@@ -14,7 +14,8 @@
 namespace prost {
 
 constexpr int STATIC_MAX_CTAS = 1024;      // partial rows the array holds
-constexpr int STATIC_ROW = KMAX + 2;       // gradient (k), cost, non-finite count
+constexpr int STATIC_KMAX = PROST_STATIC_MAX_K; // widest k (the kernel set below)
+constexpr int STATIC_ROW = STATIC_KMAX + 2;      // gradient (k), cost, non-finite count
 
 struct StaticScratch {
     float partials[STATIC_MAX_CTAS * STATIC_ROW];
@@ -32,7 +33,7 @@ struct StaticArgs {
     double *out;             // k + 1 doubles (device): cost, then gradient
     int32_t *status;         // device or NULL
     int64_t m, P;
-    float y[KMAX];
+    float y[STATIC_KMAX];
     float p, mu, omega, in_scale, in_offset, e;
 };
 
@@ -94,7 +95,7 @@ static cudaError_t launch_static(const StaticArgs &a, StaticScratch *s, int fdt,
 
 typedef cudaError_t (*StaticLaunch)(const StaticArgs &, StaticScratch *, int, int, cudaStream_t);
 
-static const StaticLaunch g_static_launch[KMAX + 1] = {
+static const StaticLaunch g_static_launch[STATIC_KMAX + 1] = {
     nullptr, launch_static<1>, launch_static<2>, launch_static<3>, launch_static<4>,
     launch_static<5>, launch_static<6>, launch_static<7>, launch_static<8>, launch_static<9>,
     launch_static<10>, launch_static<11>, launch_static<12>, launch_static<13>,
@@ -143,8 +144,8 @@ extern "C" int prost_cost_grad_static(const prost_params *prm, const float *U, c
     if (p.width <= 0 || p.height <= 0 || p.channels < 1 || p.channels > 4) return PROST_EINVAL;
     const int64_t P = (int64_t)p.width * p.height, m = P * p.channels;
     if (m > ((int64_t)1 << 30)) return PROST_EINVAL;
-    // the static partial rows hold at most PROST_MAX_K gradient entries
-    if (p.k < 1 || p.k > KMAX || (int64_t)p.k > m) return PROST_EINVAL;
+    // the static partial rows hold at most PROST_STATIC_MAX_K gradient entries
+    if (p.k < 1 || p.k > STATIC_KMAX || (int64_t)p.k > m) return PROST_EINVAL;
     if (!(p.p > 0.0 && p.p <= 2.0) || !(p.delta > 0.0)) return PROST_EINVAL;
     const double mu = p.mu == 0.0 ? p.delta * p.delta * (1.0 - p.p) : p.mu;
     if (!(mu > 0.0) || !(p.omega >= 0.0 && p.omega <= 1.0)) return PROST_EINVAL;
@@ -163,7 +164,7 @@ extern "C" int prost_cost_grad_static(const prost_params *prm, const float *U, c
     a.status = status_out;
     a.m = m;
     a.P = P;
-    for (int j = 0; j < KMAX; ++j) a.y[j] = j < p.k ? (float)y[j] : 0.f;
+    for (int j = 0; j < STATIC_KMAX; ++j) a.y[j] = j < p.k ? (float)y[j] : 0.f;
     a.p = (float)p.p;
     a.mu = (float)mu;
     a.omega = (float)p.omega;

@@ -97,7 +97,7 @@ int main(void)
     FIELD(prost_stats, pi_explicit);
     FIELD(prost_stats, form);
 
-    check(prost_version() == 101, "prost_version");
+    check(prost_version() == 102, "prost_version");
     check(prost_strerror(PROST_EINVAL) != NULL && strlen(prost_strerror(PROST_EINVAL)) > 0, "strerror");
     check(prost_state_bytes(&prm, &bytes) == PROST_OK, "state bytes of valid parameters");
     check(bytes > (size_t)64 * 48 * 3 * 10 * 4, "state holds at least the subspace");
@@ -106,8 +106,16 @@ int main(void)
     prm.k = 0;
     check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "k = 0 rejected");
     prm = valid_params();
-    prm.form = 3;
-    check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "form beyond the three forms");
+    prm.form = 4;
+    check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "form beyond the four forms");
+    prm = valid_params();
+    prm.k = PROST_MAX_K;
+    check(prost_state_bytes(&prm, &bytes) == PROST_OK, "k = 32 in the passes form");
+    prm.k = PROST_MAX_K + 1;
+    check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "k = 33 rejected");
+    prm.k = PROST_MAX_K_SINGLE + 1;
+    prm.form = PROST_FORM_GRID;
+    check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "k = 17 has no grid form");
     prm = valid_params();
     prm.p = 3.0;
     check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "p > 2 rejected");

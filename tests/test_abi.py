@@ -23,7 +23,7 @@ def test_binding_covers_every_declared_symbol():
 
 
 def test_version_and_error_strings():
-    assert pg.prost_version() == 101
+    assert pg.prost_version() == 102
     assert pg.prost_strerror(pg.PROST_EBADFRAME) == "frame has a non-finite entry"
     assert pg.prost_strerror(12345) == "unknown error"
 
@@ -40,11 +40,14 @@ def test_state_bytes_of_valid_parameters():
 
 
 @pytest.mark.parametrize("bad", [
-    dict(width=0), dict(channels=5), dict(k=0), dict(k=17), dict(p=0.0), dict(p=2.5),
+    dict(width=0), dict(channels=5), dict(k=0), dict(k=33), dict(p=0.0), dict(p=2.5),
     dict(delta=0.0), dict(p=1.0, mu=0.0), dict(mu=-1.0), dict(omega=1.5), dict(t_init=0.0),
     dict(t_min=-1.0), dict(i_init=0), dict(n_cg=-1), dict(n_cg=33), dict(frame_dtype=7),
     dict(u_dtype=7), dict(mask_from=2), dict(width=2, height=2, channels=1, k=5),
     dict(in_scale=float("nan")),
+    # k above the single-launch forms: the passes form only, float32 storage only
+    dict(k=17, form=1), dict(k=20, form=2), dict(k=32, u_dtype="bf16"),
+    dict(k=10, form=3, u_dtype="bf16"),
 ])
 def test_parameter_validation(bad):
     prm = dict(_ok())
@@ -54,11 +57,14 @@ def test_parameter_validation(bad):
     assert ei.value.code == pg.PROST_EINVAL
 
 
-def test_form_field_takes_the_three_forms_only():
-    for form in (pg.PROST_FORM_AUTO, pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER):
+def test_form_field_takes_the_four_forms_only():
+    for form in (pg.PROST_FORM_AUTO, pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER, pg.PROST_FORM_PASSES):
         p = pg.make_params(**_ok(), form=form)
         assert pg.prost_state_bytes(p) > 0
-    for form in (-1, 3):
+    for k in (17, 32):
+        for form in (pg.PROST_FORM_AUTO, pg.PROST_FORM_PASSES):
+            assert pg.prost_state_bytes(pg.make_params(**dict(_ok(), k=k), form=form)) > 0
+    for form in (-1, 4):
         p = pg.make_params(**_ok())
         p.form = form
         with pytest.raises(pg.ProstError):
@@ -120,6 +126,11 @@ def test_pre_processing_arguments_are_checked_on_the_host(args):
 def test_batch_and_median_arguments_are_checked_on_the_host():
     with pytest.raises(pg.ProstError):
         pg.prost_batch_init([])
+    # a batch runs the single-launch forms only: refused before any device call
+    for bad in (dict(k=17), dict(k=32), dict(form=pg.PROST_FORM_PASSES)):
+        with pytest.raises(pg.ProstError) as ei:
+            pg.prost_batch_init([pg.make_params(**_ok()), pg.make_params(**dict(_ok(), **bad))])
+        assert ei.value.code == pg.PROST_EINVAL
     L = pg.lib()
     m = np.zeros(16, np.uint8)
     ptr = m.ctypes.data_as(C.c_void_p)

@@ -58,7 +58,7 @@ def _start(m, k, seed):
     return rng, U32, U64
 
 
-FORMS = [pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER]
+FORMS = [pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER, pg.PROST_FORM_PASSES]
 
 
 def _run(wp, U32, U64, y, frame, labels=None, form=pg.PROST_FORM_AUTO):

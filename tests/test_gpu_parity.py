@@ -51,7 +51,7 @@ def _run_case(wp, vid, frames, device=True, seed=11, **gover):
     return errs
 
 
-FORMS = [pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER]
+FORMS = [pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER, pg.PROST_FORM_PASSES]
 
 
 @pytest.mark.parametrize("form", FORMS)

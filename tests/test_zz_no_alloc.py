@@ -80,10 +80,10 @@ def test_static_scratch_entry_rejects_sizes_beyond_its_limit():
     if not torch.cuda.is_available():
         pytest.fail("needs a CUDA GPU")
     vid, wp = synth.make_workload("gray160x120_k5", width=32, height=24, n_frames=1)
-    bad = pg.make_params(**dict(wp, k=pg.PROST_MAX_K + 1))
-    U = torch.zeros((vid.m, pg.PROST_MAX_K + 1), dtype=torch.float32, device="cuda")
-    out = torch.empty(pg.PROST_MAX_K + 2, dtype=torch.float64, device="cuda")
+    bad = pg.make_params(**dict(wp, k=pg.PROST_STATIC_MAX_K + 1))
+    U = torch.zeros((vid.m, pg.PROST_STATIC_MAX_K + 1), dtype=torch.float32, device="cuda")
+    out = torch.empty(pg.PROST_STATIC_MAX_K + 2, dtype=torch.float64, device="cuda")
     f = torch.zeros(vid.m, dtype=torch.float32, device="cuda")
     with pytest.raises(pg.ProstError) as ei:
-        pg.prost_cost_grad_static(bad, U, [0.0] * (pg.PROST_MAX_K + 1), f, None, out)
+        pg.prost_cost_grad_static(bad, U, [0.0] * (pg.PROST_STATIC_MAX_K + 1), f, None, out)
     assert ei.value.code == pg.PROST_EINVAL
