@@ -560,6 +560,46 @@ def config1_study(torch, pg, dev, stream):
                        "sample": "all 200 frames, single-threaded FP64 C oracle"}}
 
 
+def passes_bytes(m, P, k, n_cg, sx, su):
+    """Bytes one frame of the passes form streams: the subspace in a gradient
+    and a curvature pass per CG iteration, the final gradient pass, the update
+    pass (read and write) and the Gram pass; the frame and the weight byte in
+    every pass that reads them; the labels and the mask written."""
+    reads = 2 * n_cg + 3
+    rows = 2 * n_cg + 2
+    return reads * m * k * su + m * k * su + rows * (m * sx + P) + 2 * P
+
+
+def passes_form_study(torch, pg, dev, stream, flush_l2, frames_timed=30, warm=5):
+    """The passes form (every k above 16; any k on request) on 640x480 RGB
+    uint8 frames: frames/s with L2 flushed before every frame, at k = 16
+    beside the single-launch grid form, and at k = 24 and 32."""
+    import synth
+    peak, src = measured_peak_hbm()
+    out = {"workload": "rgb640x480 uint8, float32 subspace, L2 flushed before every frame", "cases": []}
+    for k, form in ((16, pg.PROST_FORM_GRID), (16, pg.PROST_FORM_PASSES), (24, pg.PROST_FORM_PASSES),
+                    (32, pg.PROST_FORM_PASSES)):
+        vid, wp = synth.make_workload("rgb640x480_k10", k=k, n_frames=warm + frames_timed)
+        frames = torch.from_numpy(vid.frames(0, warm + frames_timed)).to(dev)
+        masks = [torch.empty(vid.P, dtype=torch.uint8, device=dev) for _ in range(2)]
+        h = pg.prost_init(pg.make_params(**wp, seed=1, form=form), stream=stream)
+        try:
+            fps = _timed_fps(torch, pg, h, frames, masks, stream, warm, flush_l2)
+        finally:
+            pg.prost_destroy(h)
+        del frames
+        n_cg = wp["n_cg"]
+        own = passes_bytes(vid.m, vid.P, k, n_cg, 1, 4) if form == pg.PROST_FORM_PASSES else \
+            algorithmic_bytes(vid.m, vid.P, k, n_cg, 1, 4)
+        gbs = own * fps / 1e9
+        out["cases"].append({"k": k, "form": "passes" if form == pg.PROST_FORM_PASSES else "grid",
+                             "frames_per_s": fps, "ms_per_frame": 1e3 / fps,
+                             "method_bytes_per_frame": algorithmic_bytes(vid.m, vid.P, k, n_cg, 1, 4),
+                             "form_bytes_per_frame": own, "form_GBps": gbs, "frac_of_hbm_peak": gbs / peak})
+    out["peak_source"] = f"{src} hbm_gbs"
+    return out
+
+
 def pipeline_study(torch, pg, dev, stream, flush_l2, frames_timed=200, warm=10):
     """The paper's whole per-frame pipeline (Section 3.4) on the GPU: a
     640x480 RGB uint8 frame resampled to 160x120 and normalised, one tracker
@@ -923,6 +963,7 @@ def run_ours(args, dist):
         out["bf16_vs_fp32"] = precision_study(torch, pg, dev, stream, flush_l2)
         out["pipeline_160x120_k15"] = pipeline_study(torch, pg, dev, stream, flush_l2)
         out["config1_gray160x120_k5"] = config1_study(torch, pg, dev, stream)
+        out["passes_form_rgb640x480"] = passes_form_study(torch, pg, dev, stream, flush_l2)
         out["batched_64_streams"] = batched_study(torch, pg, dev, stream)
         err = bf16_error_study(torch, pg, dev, stream)
         out["bf16_vs_fp32"]["error_at_length"] = err

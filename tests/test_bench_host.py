@@ -74,3 +74,11 @@ def test_algorithmic_bytes_of_the_default_workload():
     # (n_cg + 2) reads of U, one write, a frame and a label byte per pass, the mask
     m, P, k, n_cg = 921600, 307200, 10, 5
     assert bench.algorithmic_bytes(m, P, k, n_cg, 1, 4) == 303820800
+
+
+def test_bytes_of_the_passes_form():
+    # 2 n_cg + 3 reads of U and one write; frame and weight byte in 2 n_cg + 2
+    # passes; labels and mask written
+    m, P, k, n_cg = 921600, 307200, 32, 5
+    U = m * k * 4
+    assert bench.passes_bytes(m, P, k, n_cg, 1, 4) == 14 * U + 12 * (m + P) + 2 * P == 1666867200
