@@ -671,9 +671,11 @@ def batched_study(torch, pg, dev, stream, ticks=30, n_distinct=4):
             masks = [torch.empty(v.P, dtype=torch.uint8, device=dev) for v, _ in streams]
             tuned_ms = pg.prost_batch_tune(b, frames[0], ticks=3)
             ctas, ngroups, alpha, graph = pg.prost_batch_plan(b, n)
+            conc = pg.prost_batch_get_concurrent(b)
             res = {}
-            for use_graph in (graph, not graph):
+            for use_graph, use_conc in ((graph, conc), (not graph, conc), (graph, not conc)):
                 pg.prost_batch_set_graph(b, use_graph)
+                pg.prost_batch_set_concurrent(b, use_conc)
                 for t in range(3):
                     pg.prost_batch_step(b, frames[t % n_distinct], masks)
                 torch.cuda.synchronize()
@@ -684,13 +686,14 @@ def batched_study(torch, pg, dev, stream, ticks=30, n_distinct=4):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1) / ticks
-                res["graph" if use_graph else "direct"] = {"ms_per_tick": ms, "frames_per_s": n / (ms / 1e3)}
+                key = ("graph" if use_graph else "direct") + ("_concurrent" if use_conc else "_serial")
+                res[key] = {"ms_per_tick": ms, "frames_per_s": n / (ms / 1e3)}
             pg.prost_batch_sync(b)
             last[ud] = [m.cpu().numpy() for m in masks]
             best = min(res.values(), key=lambda r: r["ms_per_tick"])
             out[ud] = {"frames_per_s": best["frames_per_s"], "ms_per_tick": best["ms_per_tick"],
-                       "plan": {"alpha": alpha, "graph": bool(graph), "kernel_groups": ngroups,
-                                "tuner_ms_per_tick": tuned_ms},
+                       "plan": {"alpha": alpha, "graph": bool(graph), "concurrent_groups": bool(conc),
+                                "kernel_groups": ngroups, "tuner_ms_per_tick": tuned_ms},
                        "launch": res}
         finally:
             pg.prost_batch_destroy(b)

@@ -368,9 +368,20 @@ int prost_batch_sync(prost_batch *b);
 int prost_batch_stream(prost_batch *b, int32_t i, prost_handle **h);
 /* Capture ticks in a CUDA graph (1, the default) or launch them directly (0). */
 int prost_batch_set_graph(prost_batch *b, int enable);
+/* Run the kernel groups of a tick one after another (0, the default) or
+ * concurrently (1): each group's launch on its own stream, forked from and
+ * joined back into the batch stream (inside the graph too), on a share of
+ * the SMs proportional to the bytes its streams move per tick, at least one
+ * SM per stream.  The shares sum to at most the SM count, so every CTA of
+ * every group is resident at once.  Synchronises the batch stream and
+ * re-plans the CTA split.  PROST_EINVAL (the plan unchanged) when the groups'
+ * streams outnumber the SMs. */
+int prost_batch_set_concurrent(prost_batch *b, int enable);
+int prost_batch_get_concurrent(prost_batch *b, int32_t *enabled);
 /* Autotuner: times `ticks` ticks of each candidate plan (the split of each
  * group's CTAs between its streams in proportion to rows^alpha, alpha in
- * {0.5, 0.75, 1}; graph on or off) on the given frames and keeps the fastest.
+ * {0.5, 0.75, 1}; the groups in turn or concurrent, where they fit; graph on
+ * or off) on the given frames and keeps the fastest.
  * The trackers' states are saved and restored around the trials.  best_ms:
  * the chosen plan's time per tick. */
 int prost_batch_tune(prost_batch *b, const void *const *frames, int32_t ticks, float *best_ms);

@@ -936,6 +936,12 @@ struct prost_batch {
     int graph_ok;               // the capture worked (cooperative kernel nodes)
     cudaGraphExec_t gexec[2];
     float alpha;                // CTAs of a stream proportional to (its rows)^alpha
+    // concurrent groups: each group's launch on its own stream, forked from
+    // and joined back into the batch stream, on its own share of the SMs
+    int concurrent;
+    std::vector<cudaStream_t> gstream;
+    std::vector<cudaEvent_t> gjoin;
+    cudaEvent_t fork;
     uint32_t ticks_since_rebase;
     void *save;                 // device scratch of the tuner (states saved around trial ticks)
     size_t save_bytes;
@@ -958,13 +964,69 @@ int bfail(prost_batch *b, int code, const std::string &why)
                          std::string(#call) + ": " + cudaGetErrorString(e_));                 \
     } while (0)
 
+// SMs of each group when the groups run concurrently: shares of the device in
+// proportion to the bytes the group's streams move per tick (at least one SM
+// per stream), summing to at most the SM count, so that every CTA of every
+// group is resident at once and no group's grid barrier waits on SMs another
+// group holds.  Empty when the groups cannot all be resident together.
+std::vector<int> concurrent_sms(prost_batch *b)
+{
+    const int sms = b->h[0]->num_sms;
+    const int ng = (int)b->groups.size();
+    std::vector<double> w(ng, 0.0);
+    std::vector<int> lo(ng), s(ng);
+    double wsum = 0.0;
+    int need = 0;
+    for (int gi = 0; gi < ng; ++gi) {
+        const BatchGroup &g = b->groups[gi];
+        const int occ = g.ops->frame_prepare(g.fdt);
+        if (occ < 1) return {};
+        for (int i = 0; i < g.count; ++i) {
+            const prost_handle *h = b->h[b->order[g.first + i]];
+            w[gi] += (double)h->dp.C * (double)h->dp.Pp * (double)h->dp.k * (double)u_elem_bytes(h->dp) *
+                     (double)(h->prm.n_cg + 3);
+        }
+        lo[gi] = (g.count + occ - 1) / occ;
+        need += lo[gi];
+        wsum += w[gi];
+    }
+    if (need > sms || !(wsum > 0.0)) return {};
+    int used = 0;
+    for (int gi = 0; gi < ng; ++gi) {
+        s[gi] = std::max(lo[gi], (int)floor(sms * w[gi] / wsum));
+        used += s[gi];
+    }
+    while (used > sms) { // take from the group with the most SMs per byte
+        int big = -1;
+        for (int gi = 0; gi < ng; ++gi)
+            if (s[gi] > lo[gi] && (big < 0 || s[gi] / w[gi] > s[big] / w[big])) big = gi;
+        s[big] -= 1;
+        used -= 1;
+    }
+    while (used < sms) { // give to the group with the most bytes per SM
+        int best = 0;
+        for (int gi = 1; gi < ng; ++gi)
+            if (w[gi] / s[gi] > w[best] / s[best]) best = gi;
+        s[best] += 1;
+        used += 1;
+    }
+    return s;
+}
+
 // Split each group's CTA budget between its streams (prost_batch_split), in
 // proportion to rows^alpha, and upload the CTA -> stream map of its launch.
+// Serial groups each take the whole device; concurrent groups their share.
 int plan_ctas(prost_batch *b)
 {
-    for (BatchGroup &g : b->groups) {
+    std::vector<int> share;
+    if (b->concurrent) {
+        share = concurrent_sms(b);
+        if (share.empty()) return bfail(b, PROST_EINVAL, "the groups cannot all be resident at once");
+    }
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        BatchGroup &g = b->groups[gi];
         prost_handle *h0 = b->h[b->order[g.first]];
-        const int budget = occupancy_ctas(h0, g.ops, g.fdt);
+        const int budget = b->concurrent ? share[gi] * g.ops->frame_prepare(g.fdt) : occupancy_ctas(h0, g.ops, g.fdt);
         if (budget < g.count) return bfail(b, PROST_EINVAL, "more streams in a group than resident CTAs");
         std::vector<double> w(g.count);
         std::vector<int32_t> cap(g.count), n(g.count);
@@ -1006,14 +1068,27 @@ void drop_graphs(prost_batch *b)
         }
 }
 
-// the tick's operations on the batch stream: table copy, one launch per group
+// the tick's operations on the batch stream: table copy, one launch per
+// group, in turn or (concurrent) each on its group stream between a fork and
+// a join
 int enqueue_tick(prost_batch *b, int t)
 {
     BCK(cudaMemcpyAsync(b->d_args, b->h_args[t], b->h.size() * sizeof(FrameArgs), cudaMemcpyHostToDevice,
                         b->stream));
     // the CTA maps hold table slots of the whole batch
-    for (const BatchGroup &g : b->groups)
-        BCK(g.ops->frame_multi(b->d_args, g.d_map, g.ctas, g.fdt, b->stream));
+    if (!b->concurrent) {
+        for (const BatchGroup &g : b->groups)
+            BCK(g.ops->frame_multi(b->d_args, g.d_map, g.ctas, g.fdt, b->stream));
+        return PROST_OK;
+    }
+    BCK(cudaEventRecord(b->fork, b->stream));
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        const BatchGroup &g = b->groups[gi];
+        BCK(cudaStreamWaitEvent(b->gstream[gi], b->fork, 0));
+        BCK(g.ops->frame_multi(b->d_args, g.d_map, g.ctas, g.fdt, b->gstream[gi]));
+        BCK(cudaEventRecord(b->gjoin[gi], b->gstream[gi]));
+        BCK(cudaStreamWaitEvent(b->stream, b->gjoin[gi], 0));
+    }
     return PROST_OK;
 }
 
@@ -1097,6 +1172,15 @@ extern "C" int prost_batch_init(const prost_params *prms, int32_t n, void *strea
     }
     int rc = plan_ctas(b);
     if (rc) return bail(rc);
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) return bail(PROST_ECUDA);
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(PROST_ECUDA);
+        b->gstream.push_back(s);
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(PROST_ECUDA);
+        b->gjoin.push_back(e);
+    }
     if (cudaMalloc(&b->d_args, (size_t)n * sizeof(FrameArgs)) != cudaSuccess) return bail(PROST_ENOMEM);
     for (int t = 0; t < 2; ++t) {
         if (cudaMallocHost(&b->h_args[t], (size_t)n * sizeof(FrameArgs)) != cudaSuccess) return bail(PROST_ENOMEM);
@@ -1195,6 +1279,32 @@ extern "C" int prost_batch_set_graph(prost_batch *b, int enable)
     return PROST_OK;
 }
 
+extern "C" int prost_batch_set_concurrent(prost_batch *b, int enable)
+{
+    if (!b) return PROST_EINVAL;
+    DeviceGuard dg(b->device);
+    BCK(cudaStreamSynchronize(b->stream));
+    const int old = b->concurrent;
+    b->concurrent = enable ? 1 : 0;
+    drop_graphs(b);
+    const int rc = plan_ctas(b);
+    if (rc) {
+        const std::string why = b->err;
+        b->concurrent = old;
+        plan_ctas(b);
+        b->err = why;
+        return rc;
+    }
+    return PROST_OK;
+}
+
+extern "C" int prost_batch_get_concurrent(prost_batch *b, int32_t *enabled)
+{
+    if (!b || !enabled) return PROST_EINVAL;
+    *enabled = b->concurrent;
+    return PROST_OK;
+}
+
 extern "C" int prost_batch_plan(prost_batch *b, int32_t *ctas_per_stream, int32_t *n_groups, float *alpha,
                                 int32_t *graph)
 {
@@ -1240,7 +1350,8 @@ int save_states(prost_batch *b, bool restore)
 } // namespace
 
 // Pick the batch plan by measurement: the CTA split exponent alpha in
-// {0.5, 0.75, 1} and the graph on or off, each timed over `ticks` ticks on the
+// {0.5, 0.75, 1}, the groups in turn or concurrent (when they can all be
+// resident at once) and the graph on or off, each timed over `ticks` ticks on the
 // given frames; the states are saved before and restored after every trial,
 // so tuning leaves the trackers where they were (the frame counters included).
 extern "C" int prost_batch_tune(prost_batch *b, const void *const *frames, int32_t ticks, float *best_ms)
@@ -1251,12 +1362,15 @@ extern "C" int prost_batch_tune(prost_batch *b, const void *const *frames, int32
     if (rc) return rc;
     const float alphas[3] = {0.5f, 0.75f, 1.0f};
     float best = 1e30f, best_alpha = b->alpha;
-    int best_graph = b->use_graph;
+    int best_graph = b->use_graph, best_conc = b->concurrent;
     const uint32_t ticks0 = b->ticks_since_rebase;
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
-    for (float al : alphas) {
+    for (int trial = 0; trial < 6 && !rc; ++trial) {
+        const float al = alphas[trial % 3];
+        b->concurrent = trial / 3;
+        if (b->concurrent && concurrent_sms(b).empty()) break; // the groups cannot all be resident at once
         b->alpha = al;
         drop_graphs(b);
         rc = plan_ctas(b);
@@ -1277,18 +1391,19 @@ extern "C" int prost_batch_tune(prost_batch *b, const void *const *frames, int32
                 best = ms;
                 best_alpha = al;
                 best_graph = gr;
+                best_conc = b->concurrent;
             }
             const int rs = save_states(b, true);
             if (!rc) rc = rs;
             if (rc) break;
         }
-        if (rc) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->ticks_since_rebase = ticks0;
     b->alpha = best_alpha;
     b->use_graph = best_graph;
+    b->concurrent = best_conc;
     drop_graphs(b);
     const int rp = plan_ctas(b);
     if (!rc) rc = rp;
@@ -1315,6 +1430,11 @@ extern "C" void prost_batch_destroy(prost_batch *b)
         if (b->used[t]) cudaEventDestroy(b->used[t]);
     }
     if (b->save) cudaFree(b->save);
+    for (cudaStream_t s : b->gstream)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->gjoin)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
     for (prost_handle *h : b->h) prost_destroy(h);
     delete b;
 }

@@ -107,6 +107,8 @@ def lib():
         L.prost_batch_sync.argtypes = [vp]
         L.prost_batch_stream.argtypes = [vp, C.c_int32, P(vp)]
         L.prost_batch_set_graph.argtypes = [vp, C.c_int]
+        L.prost_batch_set_concurrent.argtypes = [vp, C.c_int]
+        L.prost_batch_get_concurrent.argtypes = [vp, P(C.c_int32)]
         L.prost_batch_tune.argtypes = [vp, P(vp), C.c_int32, P(C.c_float)]
         L.prost_batch_plan.argtypes = [vp, P(C.c_int32), P(C.c_int32), P(C.c_float), P(C.c_int32)]
         L.prost_batch_split.argtypes = [C.c_int32, C.c_int32, P(C.c_double), P(C.c_int32), P(C.c_int32)]
@@ -382,6 +384,16 @@ def prost_batch_stream(b, i):
 
 def prost_batch_set_graph(b, enable=True):
     return _check_batch(lib().prost_batch_set_graph(b, 1 if enable else 0), b)
+
+
+def prost_batch_set_concurrent(b, enable=True):
+    return _check_batch(lib().prost_batch_set_concurrent(b, 1 if enable else 0), b)
+
+
+def prost_batch_get_concurrent(b):
+    v = C.c_int32()
+    _check_batch(lib().prost_batch_get_concurrent(b, C.byref(v)), b)
+    return bool(v.value)
 
 
 def prost_batch_tune(b, frames, ticks=5):

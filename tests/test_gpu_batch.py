@@ -1,7 +1,8 @@
 """Many streams per tick (prost_batch) through the C ABI: per-stream parity
 with the FP64 oracle for streams of mixed k, channels and frame types in one
 tick, graph and direct launches bit-identical, the autotuner leaving the
-trackers untouched, a long run across the rebase, and argument checks."""
+trackers untouched, the kernel groups in turn or concurrent, a long run
+across the rebase, and argument checks."""
 
 import numpy as np
 import pytest
@@ -42,10 +43,13 @@ def _export(h, vid):
     return U, y
 
 
-def test_one_tick_matches_the_oracle_for_every_stream():
+@pytest.mark.parametrize("concurrent", [False, True])
+def test_one_tick_matches_the_oracle_for_every_stream(concurrent):
     streams = _streams()
     b = pg.prost_batch_init([gpu_params(wp) for _, wp in streams])
     try:
+        pg.prost_batch_set_concurrent(b, concurrent)
+        assert pg.prost_batch_get_concurrent(b) == concurrent
         starts, frames, masks = [], [], []
         for i, (vid, wp) in enumerate(streams):
             st = oracle.initial_state(synth.random_orthonormal(vid.m, vid.k, 30 + i), vid.P)
@@ -64,6 +68,9 @@ def test_one_tick_matches_the_oracle_for_every_stream():
         pg.prost_batch_sync(b)
         ctas, ngroups, alpha, graph = pg.prost_batch_plan(b, len(streams))
         assert ngroups == 4 and all(c >= 1 for c in ctas)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        if concurrent:  # every CTA of every group resident at once
+            assert sum(ctas) <= sms
         for i, (vid, wp) in enumerate(streams):
             h = pg.prost_batch_stream(b, i)
             res = oracle.frame_step(oracle_params(wp), starts[i], vid.frame(2)[0])
@@ -82,10 +89,11 @@ def test_one_tick_matches_the_oracle_for_every_stream():
         pg.prost_batch_destroy(b)
 
 
-def _run(streams, graph, ticks):
+def _run(streams, graph, ticks, concurrent=False):
     b = pg.prost_batch_init([gpu_params(wp, seed=7) for _, wp in streams])
     try:
         pg.prost_batch_set_graph(b, graph)
+        pg.prost_batch_set_concurrent(b, concurrent)
         fr = [[torch.from_numpy(v.frame(t % v.n_frames)[0]).cuda() for v, _ in streams] for t in range(ticks)]
         ms = [torch.empty(v.P, dtype=torch.uint8, device="cuda") for v, _ in streams]
         for t in range(ticks):
@@ -97,14 +105,28 @@ def _run(streams, graph, ticks):
         pg.prost_batch_destroy(b)
 
 
-def test_graph_and_direct_launches_are_bit_identical():
+@pytest.mark.parametrize("concurrent", [False, True])
+def test_graph_and_direct_launches_are_bit_identical(concurrent):
     streams = _streams()
-    a, ma = _run(streams, True, 5)
-    d, md = _run(streams, False, 5)
+    a, ma = _run(streams, True, 5, concurrent)
+    d, md = _run(streams, False, 5, concurrent)
     for (Ua, ya), (Ud, yd) in zip(a, d):
         assert np.array_equal(Ua, Ud) and np.array_equal(ya, yd)
     for x, y in zip(ma, md):
         assert np.array_equal(x, y)
+
+
+def test_concurrent_groups_track_the_serial_ones():
+    # the CTA splits differ, so do the summation orders: the same subspaces to
+    # FP32 rounding after five ticks
+    streams = _streams()
+    a, ma = _run(streams, True, 5, False)
+    c, mc = _run(streams, True, 5, True)
+    for (Ua, ya), (Uc, yc) in zip(a, c):
+        assert np.linalg.norm(Ua - Uc) <= 1e-5 * np.linalg.norm(Ua)
+        assert np.linalg.norm(ya - yc) <= 1e-5 * np.linalg.norm(ya)
+    for x, y in zip(ma, mc):
+        assert (x != y).mean() < 1e-3
 
 
 def test_tuner_leaves_the_trackers_where_they_were():
