@@ -29,12 +29,17 @@ constexpr int KW = KMAX;                  // widest subspace of this form
 constexpr int WT = 256;                   // threads per CTA of the row passes
 constexpr int NWG = KW * (KW + 1) / 2;    // packed upper triangle of a KW x KW matrix
 constexpr int TOTF = 544;                 // floats of reduced sums ahead of the per-CTA rows
-constexpr int GT = 288;                   // threads of the Gram kernel (272 work, 16 idle)
-constexpr int NB2 = (KW / 2) * (KW / 2 + 1) / 2; // 2 x 2 blocks of the upper triangle
-constexpr int TSTR = TILE_P + 1;          // shared row stride of a staged tile (no bank conflicts)
+constexpr int NB4 = (KW / 4) * (KW / 4 + 1) / 2; // 4 x 4 blocks of the upper triangle (36)
+constexpr int GT = NB4 * 8;               // threads of the Gram kernel: 8 row groups per block
+constexpr int RS = KW + 4;                // shared row stride of a staged tile (16-byte rows)
+constexpr int GPER = (KW * TILE_P + GT - 1) / GT; // a Gram thread's loads of one tile block
+constexpr int MAX_CTAS = 320;             // CTAs of a pass at most (the sums' scratch)
+constexpr int RCH = 16;                   // rows per unit of a pass's cross-CTA sum
+constexpr int GCH = 40;                   // rows per unit of the Gram's cross-CTA sum
+static_assert(NWG * ((MAX_CTAS + GCH - 1) / GCH) <= TILE_P * RS, "the Gram's chunk sums fit the tile");
 static_assert(KW == 32, "the pass-sequence form is written for up to 32 columns");
 static_assert(TOTF >= NWG + 1 && TOTF % 4 == 0, "reduced sums: the Gram, then the foreground count");
-static_assert(2 * NB2 <= GT, "two row halves of every 2 x 2 block");
+static_assert(TILE_P % 8 == 0 && RS % 4 == 0, "row groups and 16-byte rows");
 
 struct WideArgs {
     float *U;                 // stored subspace, tile-blocked (float32)
@@ -50,11 +55,42 @@ struct WideArgs {
     DevParams prm;
 };
 
+// Fixed-order sum over nrows partial rows of nv values (part[b * nv + i]) by
+// the nt threads of one CTA: the rows are cut into chunks of CH, a unit
+// (value, chunk) has all its CH loads in flight at once and sums them with
+// Kahan compensation, and the chunk sums of each value are then added in
+// chunk order, so the result depends only on nrows and CH.  scr holds
+// nv * ceil(nrows / CH) floats.
+template <int CH>
+__device__ __forceinline__ void chunked_sum(const float *part, int nrows, int nv, float *tot, float *scr, int nt)
+{
+    const int nch = (nrows + CH - 1) / CH;
+    for (int u = threadIdx.x; u < nv * nch; u += nt) {
+        const int c = u / nv, i = u - (u / nv) * nv;
+        float v[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int b = c * CH + q;
+            v[q] = b < nrows ? __ldcg(part + (size_t)b * nv + i) : 0.f;
+        }
+        float sum = 0.f, comp = 0.f;
+#pragma unroll
+        for (int q = 0; q < CH; ++q) kahan_add(sum, comp, v[q]);
+        scr[c * nv + i] = sum;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nv; i += nt) {
+        float sum = 0.f, comp = 0.f;
+        for (int c = 0; c < nch; ++c) kahan_add(sum, comp, scr[c * nv + i]);
+        tot[i] = sum;
+    }
+}
+
 // CTA sums of NV per-thread values (shuffle tree per value, then the warps in
-// order) into the CTA's row of part, then the fixed-order, Kahan-compensated
-// sum over the CTAs by the last CTA to arrive into tot.
+// order) into the CTA's row of part, then the fixed-order sum over the CTAs
+// (chunked_sum) by the last CTA to arrive into tot.
 template <int NV>
-__device__ __forceinline__ void wide_reduce(const float (&acc)[NV], float *part, float *tot, unsigned int *counter)
+__device__ __forceinline__ bool wide_reduce(const float (&acc)[NV], float *part, float *tot, unsigned int *counter)
 {
     __shared__ float sw[WT / 32][NV];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -72,13 +108,150 @@ __device__ __forceinline__ void wide_reduce(const float (&acc)[NV], float *part,
         for (int ww = 0; ww < WT / 32; ++ww) a += sw[ww][i];
         part[(size_t)blockIdx.x * NV + i] = a;
     }
-    if (!arrive_last(counter)) return;
-    for (int i = threadIdx.x; i < NV; i += WT) {
-        float s = 0.f, c = 0.f;
-        for (int b = 0; b < (int)gridDim.x; ++b) kahan_add(s, c, __ldcg(part + (size_t)b * NV + i));
-        tot[i] = s;
-    }
+    if (!arrive_last(counter)) return false;
+    __shared__ float scr[NV * ((MAX_CTAS + RCH - 1) / RCH)];
+    chunked_sum<RCH>(part, (int)gridDim.x, NV, tot, scr, WT);
     if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads(); // tot is complete for the CTA
+    return true;
+}
+
+// Step 2's angle from |pi(eta)| (one thread): sigma = |pi(eta)| |y| (Eq. svd),
+// theta = sigma t (Eq. geodesic), skipped when |y| = 0 or |pi(eta)| = 0.
+__device__ void wide_angle(KState *ks, const DevParams &prm, float pin)
+{
+    const float yn = ks->wyn;
+    const bool upd = yn > 0.f && pin > 0.f;
+    const float t = step_size(prm, ks->frame_index);
+    const float sigma = pin * yn;
+    const float theta = sigma * t;
+    const float sh = sinf(0.5f * theta);
+    ks->wcm1 = upd ? -2.f * sh * sh : 0.f;
+    ks->wsnp = upd ? sinf(theta) / pin : 0.f;
+    ks->pi_norm = pin;
+    ks->y_norm = yn;
+    ks->sigma = sigma;
+    ks->t = t;
+    ks->theta = upd ? theta : 0.f;
+    ks->updated = upd ? 1 : 0;
+}
+
+// The k-space steps, run by the last CTA of the pass before, once it has
+// reduced the pass's sums into tot: its threads stage T (and R) in shared
+// memory, then one warp (lane l < k holds entry l) takes the step:
+//   STAGE 0, after gradient pass `pass` < n_cg: g = T^T g_st, the PR+ beta,
+//            d = -g + beta d, s = T d (the direction in the stored basis), d^T g;
+//   STAGE 1, after its curvature pass: alpha, y += alpha d, T y += alpha s;
+//   STAGE 2, after the final gradient pass: |pi(eta)| from the norm identity
+//            or the request for the projection pass; v = y/|y|, T v, T g,
+//            w = R^T v and (without the projection pass) the angle;
+//   STAGE 3, after the projection pass: the angle from the explicit |pi(eta)|.
+struct StepSmem {
+    float T[KW * KW]; // T = R^{-1}, row-major, zero outside k x k
+    float R[KW * KW]; // R, row-major, zero outside k x k (STAGE 2)
+};
+
+template <int STAGE>
+__device__ void wide_step(const WideArgs &a, int pass, StepSmem &sm)
+{
+    KState *ks = a.ks;
+    const DevParams &prm = a.prm;
+    const int k = prm.k, l = threadIdx.x;
+    if constexpr (STAGE == 0 || STAGE == 2) {
+        for (int i = threadIdx.x; i < KW * KW; i += WT) {
+            const int r = i / KW, c = i - (i / KW) * KW;
+            const bool in = r < k && c < k;
+            sm.T[i] = in ? ks->Tf[r * k + c] : 0.f;
+            if (STAGE == 2) sm.R[i] = in ? (float)ks->R[r * KMAX + c] : 0.f;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x >= 32) return;
+    const bool act = l < k;
+    const float *tot = a.tot;
+    if constexpr (STAGE == 1) {
+        const float den = prm.p * tot[0];
+        const float alpha = den > 0.f ? -ks->wdg / den : 0.f;
+        if (act) {
+            ks->y[l] = fma((double)alpha, (double)ks->wd[l], ks->y[l]);
+            ks->yf[l] = fmaf(alpha, ks->ws[l], ks->yf[l]);
+        }
+        if (l == 0) ks->alpha[pass] = alpha;
+    } else if constexpr (STAGE == 3) {
+        if (l == 0) wide_angle(ks, prm, sqrtf(fmaxf(tot[0], 0.f)));
+    } else {
+        const float f = tot[KW], ee = tot[KW + 1], nbad = tot[KW + 2];
+        // g = T^T g_st (T upper triangular; zero outside k x k)
+        float gl = 0.f;
+#pragma unroll
+        for (int i = 0; i < KW; ++i) gl = fmaf(sm.T[i * KW + l], tot[i], gl);
+        if (!act) gl = 0.f;
+        const float gsq = wsumf(gl * gl);
+        float beta = 0.f, dl;
+        if (pass == 0) {
+            dl = -gl;
+        } else {
+            const float gp = act ? ks->wgp[l] : 0.f;
+            const float ggp = wsumf(gp * gp);
+            const float num = wsumf(gl * (gl - gp));
+            beta = ggp > 0.f ? fmaxf(0.f, num / ggp) : 0.f;
+            dl = act ? fmaf(beta, ks->wd[l], -gl) : 0.f;
+        }
+        if (l == 0) {
+            ks->cost[pass] = f;
+            ks->gnorm[pass] = sqrtf(gsq);
+            ks->beta[pass] = beta;
+        }
+        if (pass == 0 && nbad > 0.f) {
+            if (l == 0) ks->wskip = 1; // the later launches of this frame return at once
+            return;
+        }
+        if constexpr (STAGE == 0) {
+            const float dg = wsumf(dl * gl);
+            float sl = 0.f;
+#pragma unroll
+            for (int i = 0; i < KW; ++i) sl = fmaf(sm.T[l * KW + i], __shfl_sync(FULL, dl, i), sl);
+            if (act) {
+                ks->wd[l] = dl;
+                ks->wgp[l] = gl;
+                ks->ws[l] = sl;
+            }
+            if (l == 0) ks->wdg = dg;
+        } else {
+            const float yl = act ? (float)ks->y[l] : 0.f;
+            const float yn = sqrtf(wsumf(yl * yl));
+            // |pi(eta)|^2 = |eta|^2 - |U^T eta|^2 (Eq. gproject, U orthonormal)
+            // cancels when most of eta lies in span(U); below PROJ_RATIO |eta|^2
+            // the projection pass forms the norm explicitly instead
+            const float pin2 = ee - gsq;
+            const bool proj = yn > 0.f && ee > 0.f && !(pin2 > PROJ_RATIO * ee);
+            const float pin = (!proj && pin2 > 0.f) ? sqrtf(pin2) : 0.f;
+            const bool upd = yn > 0.f && (proj || pin > 0.f);
+            const float vl = (act && upd) ? yl / yn : 0.f;
+            float tv = 0.f, tg = 0.f, wl = 0.f;
+#pragma unroll
+            for (int i = 0; i < KW; ++i) {
+                const float vi = __shfl_sync(FULL, vl, i);
+                const float gi = __shfl_sync(FULL, gl, i);
+                tv = fmaf(sm.T[l * KW + i], vi, tv);
+                tg = fmaf(sm.T[l * KW + i], gi, tg);
+                wl = fmaf(sm.R[i * KW + l], vi, wl);
+            }
+            if (act) {
+                ks->wtv[l] = tv;
+                ks->wtg[l] = tg;
+                ks->ww[l] = wl;
+            }
+            if (l == 0) {
+                ks->wyn = yn;
+                ks->wproj = proj ? 1 : 0;
+                ks->eta_norm = sqrtf(fmaxf(ee, 0.f));
+                ks->pi_explicit = proj ? 1 : 0;
+                ks->n_cg_done = prm.n_cg;
+                if (!proj) wide_angle(ks, prm, pin);
+            }
+        }
+    }
 }
 
 // One pass over the stored rows at the current y (float(T y) in yf):
@@ -87,7 +260,7 @@ __device__ __forceinline__ void wide_reduce(const float (&acc)[NV], float *part,
 // MODE 2, the projection pass (only when the final step asked for it):
 //         sum_e (eta_e - u_st,e^T tg)^2 with tg = T g (Eq. gproject).
 template <typename FT, int MODE>
-__global__ void __launch_bounds__(WT) k_wide_res(const WideArgs a)
+__global__ void __launch_bounds__(WT) k_wide_res(const WideArgs a, int pass)
 {
     constexpr int NV = MODE == 0 ? KW + 3 : 1;
     const DevParams &prm = a.prm;
@@ -144,133 +317,17 @@ __global__ void __launch_bounds__(WT) k_wide_res(const WideArgs a)
             acc[0] = fmaf(pe, pe, acc[0]);
         }
     }
-    wide_reduce<NV>(acc, a.part, a.tot, a.counter);
-}
-
-// Step 2's angle from |pi(eta)| (one thread): sigma = |pi(eta)| |y| (Eq. svd),
-// theta = sigma t (Eq. geodesic), skipped when |y| = 0 or |pi(eta)| = 0.
-__device__ void wide_angle(KState *ks, const DevParams &prm, float pin)
-{
-    const float yn = ks->wyn;
-    const bool upd = yn > 0.f && pin > 0.f;
-    const float t = step_size(prm, ks->frame_index);
-    const float sigma = pin * yn;
-    const float theta = sigma * t;
-    const float sh = sinf(0.5f * theta);
-    ks->wcm1 = upd ? -2.f * sh * sh : 0.f;
-    ks->wsnp = upd ? sinf(theta) / pin : 0.f;
-    ks->pi_norm = pin;
-    ks->y_norm = yn;
-    ks->sigma = sigma;
-    ks->t = t;
-    ks->theta = upd ? theta : 0.f;
-    ks->updated = upd ? 1 : 0;
-}
-
-// The k-space steps, one warp (lane l < k holds entry l), from the reduced
-// sums of the pass before:
-//   STAGE 0, after gradient pass `pass` < n_cg: g = T^T g_st, the PR+ beta,
-//            d = -g + beta d, s = T d (the direction in the stored basis), d^T g;
-//   STAGE 1, after its curvature pass: alpha, y += alpha d, T y += alpha s;
-//   STAGE 2, after the final gradient pass: |pi(eta)| from the norm identity
-//            or the request for the projection pass; v = y/|y|, T v, T g,
-//            w = R^T v and (without the projection pass) the angle;
-//   STAGE 3, after the projection pass: the angle from the explicit |pi(eta)|.
-template <int STAGE>
-__global__ void __launch_bounds__(32) k_wide_step(const WideArgs a, int pass)
-{
-    KState *ks = a.ks;
-    const DevParams &prm = a.prm;
-    const int k = prm.k, l = threadIdx.x;
-    const bool act = l < k;
-    const float *tot = a.tot;
-    if (ks->wskip) return;
-    if constexpr (STAGE == 1) {
-        const float den = prm.p * tot[0];
-        const float alpha = den > 0.f ? -ks->wdg / den : 0.f;
-        if (act) {
-            ks->y[l] = fma((double)alpha, (double)ks->wd[l], ks->y[l]);
-            ks->yf[l] = fmaf(alpha, ks->ws[l], ks->yf[l]);
-        }
-        if (l == 0) ks->alpha[pass] = alpha;
-    } else if constexpr (STAGE == 3) {
-        if (ks->wproj && l == 0) wide_angle(ks, prm, sqrtf(fmaxf(tot[0], 0.f)));
+    if (!wide_reduce<NV>(acc, a.part, a.tot, a.counter)) return;
+    __shared__ StepSmem sm;
+    if constexpr (MODE == 0) {
+        if (pass < prm.n_cg)
+            wide_step<0>(a, pass, sm);
+        else
+            wide_step<2>(a, pass, sm);
+    } else if constexpr (MODE == 1) {
+        wide_step<1>(a, pass, sm);
     } else {
-        const float f = tot[KW], ee = tot[KW + 1], nbad = tot[KW + 2];
-        // g = T^T g_st (T upper triangular)
-        float gl = 0.f;
-        for (int i = 0; i < KW; ++i)
-            if (act && i <= l) gl = fmaf(ks->Tf[i * k + l], tot[i], gl);
-        const float gsq = wsumf(act ? gl * gl : 0.f);
-        float beta = 0.f, dl;
-        if (pass == 0) {
-            dl = act ? -gl : 0.f;
-        } else {
-            const float gp = act ? ks->wgp[l] : 0.f;
-            const float ggp = wsumf(gp * gp);
-            const float num = wsumf(act ? gl * (gl - gp) : 0.f);
-            beta = ggp > 0.f ? fmaxf(0.f, num / ggp) : 0.f;
-            dl = act ? fmaf(beta, ks->wd[l], -gl) : 0.f;
-        }
-        if (l == 0) {
-            ks->cost[pass] = f;
-            ks->gnorm[pass] = sqrtf(gsq);
-            ks->beta[pass] = beta;
-        }
-        if (pass == 0 && nbad > 0.f) {
-            if (l == 0) ks->wskip = 1; // the later launches of this frame return at once
-            return;
-        }
-        if constexpr (STAGE == 0) {
-            const float dg = wsumf(act ? dl * gl : 0.f);
-            float sl = 0.f;
-            for (int i = 0; i < KW; ++i) {
-                const float di = __shfl_sync(FULL, dl, i);
-                if (act && i >= l && i < k) sl = fmaf(ks->Tf[l * k + i], di, sl);
-            }
-            if (act) {
-                ks->wd[l] = dl;
-                ks->wgp[l] = gl;
-                ks->ws[l] = sl;
-            }
-            if (l == 0) ks->wdg = dg;
-        } else {
-            const float yl = act ? (float)ks->y[l] : 0.f;
-            const float yn = sqrtf(wsumf(yl * yl));
-            // |pi(eta)|^2 = |eta|^2 - |U^T eta|^2 (Eq. gproject, U orthonormal)
-            // cancels when most of eta lies in span(U); below PROJ_RATIO |eta|^2
-            // the projection pass forms the norm explicitly instead
-            const float pin2 = ee - gsq;
-            const bool proj = yn > 0.f && ee > 0.f && !(pin2 > PROJ_RATIO * ee);
-            const float pin = (!proj && pin2 > 0.f) ? sqrtf(pin2) : 0.f;
-            const bool upd = yn > 0.f && (proj || pin > 0.f);
-            const float vl = (act && upd) ? yl / yn : 0.f;
-            float tv = 0.f, tg = 0.f, wl = 0.f;
-            for (int i = 0; i < KW; ++i) {
-                const float vi = __shfl_sync(FULL, vl, i);
-                const float gi = __shfl_sync(FULL, gl, i);
-                if (act && i < k) {
-                    if (i >= l) {
-                        tv = fmaf(ks->Tf[l * k + i], vi, tv);
-                        tg = fmaf(ks->Tf[l * k + i], gi, tg);
-                    }
-                    if (i <= l) wl = fmaf((float)ks->R[i * KMAX + l], vi, wl);
-                }
-            }
-            if (act) {
-                ks->wtv[l] = tv;
-                ks->wtg[l] = tg;
-                ks->ww[l] = wl;
-            }
-            if (l == 0) {
-                ks->wyn = yn;
-                ks->wproj = proj ? 1 : 0;
-                ks->eta_norm = sqrtf(fmaxf(ee, 0.f));
-                ks->pi_explicit = proj ? 1 : 0;
-                ks->n_cg_done = prm.n_cg;
-                if (!proj) wide_angle(ks, prm, pin);
-            }
-        }
+        wide_step<3>(a, pass, sm);
     }
 }
 
@@ -342,85 +399,97 @@ __global__ void __launch_bounds__(WT) k_wide_update(const WideArgs a)
         a.labels[q] = nl;
         if (a.mask_out && valid) a.mask_out[q] = nl;
     }
-    wide_reduce<1>(acc, a.part, a.tot + NWG, a.counter);
+    (void)wide_reduce<1>(acc, a.part, a.tot + NWG, a.counter);
 }
 
-__device__ __forceinline__ int packed_kw(int i, int j) { return i * KW - i * (i - 1) / 2 + (j - i); }
-
 // Gram of the stored rows, packed upper (k-wide rows), into tot.  Each CTA
-// stages one tile block (k columns of TILE_P rows) at a time in shared memory;
-// each of 272 threads sums one 2 x 2 block of the Gram over one half of the
-// rows (even or odd), in FP32 within a tile and Kahan-compensated across
-// tiles.
-__global__ void __launch_bounds__(GT) k_wide_gram(const float *U, const KState *ks, DevParams prm, float *part,
-                                                 float *tot, unsigned int *counter, int after_rebase)
+// (two per SM, so that one loads while the other sums) stages one tile block
+// (k columns of TILE_P rows) at a time in shared memory, transposed to rows of
+// RS floats.  Thread t sums the 4 x 4 block t / 8 of the upper triangle (36
+// blocks) over the rows r = t % 8 (mod 8), with one 16-byte load of each
+// row's 4 + 4 entries per 16 multiply-adds, in FP32 within a tile and
+// Kahan-compensated across tiles; the 8 row groups of a block (8 consecutive
+// lanes) are added by a fixed shuffle tree.
+__global__ void __launch_bounds__(GT, 2) k_wide_gram(const float *U, const KState *ks, DevParams prm, float *part,
+                                                    float *tot, unsigned int *counter, int after_rebase)
 {
     if (after_rebase && !ks->rebased) return; // the periodic rebase was not due
-    __shared__ float tile[KW * TSTR];
-    __shared__ float sg[2][NWG];
+    __shared__ __align__(16) float tile[TILE_P * RS];
     const int k = prm.k;
     const int t = threadIdx.x;
-    const int blk = t % NB2, half = t / NB2; // half 2: idle in the sums
+    const int blk = t >> 3, g = t & 7;
     int bi = 0, rem = blk;
-    while (rem >= KW / 2 - bi) {
-        rem -= KW / 2 - bi;
+    while (rem >= KW / 4 - bi) {
+        rem -= KW / 4 - bi;
         ++bi;
     }
     const int bj = bi + rem; // block (bi, bj), bi <= bj
-    const int i0 = 2 * bi, j0 = 2 * bj;
-    const bool work = half < 2 && j0 < k;
-    for (int i = t; i < KW * TSTR; i += GT) tile[i] = 0.f; // columns >= k stay zero
-    float s[4] = {0.f, 0.f, 0.f, 0.f}, cs[4] = {0.f, 0.f, 0.f, 0.f};
+    const int i0 = 4 * bi, j0 = 4 * bj;
+    const bool work = j0 < k;
+    for (int i = t; i < TILE_P * RS; i += GT) tile[i] = 0.f; // columns >= k stay zero
+    float s[16], cs[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) s[q] = cs[q] = 0.f;
+    const int n = k * TILE_P; // floats of one tile block
     const int ntiles = prm.C * prm.npt;
     for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-        __syncthreads(); // the previous tile's reads (and the zero fill) are done
-        const float *src = U + (int64_t)ti * k * TILE_P;
-        for (int i = t; i < k * TILE_P; i += GT) {
-            const int j = i / TILE_P, r = i - j * TILE_P;
-            tile[j * TSTR + r] = __ldcg(src + i);
+        __syncthreads(); // the previous block's sums (and the zero fill) are done
+        const float *src = U + (int64_t)ti * n;
+        float v[GPER]; // every load of the block in flight before the stores
+#pragma unroll
+        for (int q = 0; q < GPER; ++q) {
+            const int i = t + GT * q;
+            v[q] = i < n ? __ldcg(src + i) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < GPER; ++q) {
+            const int i = t + GT * q;
+            if (i < n) {
+                const int j = i / TILE_P, r = i - j * TILE_P;
+                tile[r * RS + j] = v[q];
+            }
         }
         __syncthreads();
         if (work) {
-            const float *x0 = tile + i0 * TSTR, *x1 = x0 + TSTR, *z0 = tile + j0 * TSTR, *z1 = z0 + TSTR;
-            float a00 = 0.f, a01 = 0.f, a10 = 0.f, a11 = 0.f;
-            for (int r = half; r < TILE_P; r += 2) {
-                const float u0 = x0[r], u1 = x1[r], v0 = z0[r], v1 = z1[r];
-                a00 = fmaf(u0, v0, a00);
-                a01 = fmaf(u0, v1, a01);
-                a10 = fmaf(u1, v0, a10);
-                a11 = fmaf(u1, v1, a11);
+            float a[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) a[q] = 0.f;
+            for (int r = g; r < TILE_P; r += 8) {
+                const float4 x = *reinterpret_cast<const float4 *>(tile + r * RS + i0);
+                const float4 z = *reinterpret_cast<const float4 *>(tile + r * RS + j0);
+                const float xv[4] = {x.x, x.y, x.z, x.w}, zv[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) a[p * 4 + q] = fmaf(xv[p], zv[q], a[p * 4 + q]);
             }
-            kahan_add(s[0], cs[0], a00);
-            kahan_add(s[1], cs[1], a01);
-            kahan_add(s[2], cs[2], a10);
-            kahan_add(s[3], cs[3], a11);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) kahan_add(s[q], cs[q], a[q]);
         }
     }
-    // each upper entry (i, j < k) is written once per half; in a diagonal
-    // block the (i0 + 1, i0) sum mirrors (i0, i0 + 1)
-    if (work) {
-        sg[half][packed_kw(i0, j0)] = s[0];
-        if (j0 + 1 < k) sg[half][packed_kw(i0, j0 + 1)] = s[1];
-        if (bi != bj && i0 + 1 < k) sg[half][packed_kw(i0 + 1, j0)] = s[2];
-        if (j0 + 1 < k) sg[half][packed_kw(i0 + 1, j0 + 1)] = s[3];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        float v = s[q];
+        v += __shfl_xor_sync(FULL, v, 1);
+        v += __shfl_xor_sync(FULL, v, 2);
+        v += __shfl_xor_sync(FULL, v, 4);
+        s[q] = v;
     }
-    __syncthreads();
+    // each upper entry (i <= j < k) lies in exactly one block, written once
+    if (work && g == 0) {
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + p, j = j0 + q;
+                if (i <= j && j < k)
+                    part[(size_t)blockIdx.x * (k * (k + 1) / 2) + (i * k - i * (i - 1) / 2 + (j - i))] = s[p * 4 + q];
+            }
+    }
     const int nm = k * (k + 1) / 2;
-    for (int p = t; p < nm; p += GT) {
-        int i = 0, r = p;
-        while (r >= k - i) {
-            r -= k - i;
-            ++i;
-        }
-        const int w = packed_kw(i, i + r);
-        part[(size_t)blockIdx.x * NWG + p] = sg[0][w] + sg[1][w];
-    }
     if (!arrive_last(counter)) return;
-    for (int p = t; p < nm; p += GT) {
-        float sum = 0.f, c = 0.f;
-        for (int b = 0; b < (int)gridDim.x; ++b) kahan_add(sum, c, __ldcg(part + (size_t)b * NWG + p));
-        tot[p] = sum;
-    }
+    // the tile's shared memory is free now: the chunk sums of the reduction
+    chunked_sum<GCH>(part, (int)gridDim.x, nm, tot, tile, GT); // rows nm apart (packed k-wide)
     if (t == 0) *counter = 0u;
 }
 
@@ -475,6 +544,7 @@ __device__ bool wide_cholesky(int k, double *R, double *T, double *W, double *in
 __global__ void __launch_bounds__(1024) k_wide_factor(const WideArgs a, int frame_end, int after_rebase)
 {
     __shared__ double R[KW * KW], T[KW * KW], W[KW * KW], inv[KW], ty[KW];
+    __shared__ float Xh[KW * KW], Xl[KW * KW], X2[KW * KW];
     __shared__ float emax;
     KState *ks = a.ks;
     const int k = a.prm.k;
@@ -501,7 +571,44 @@ __global__ void __launch_bounds__(1024) k_wide_factor(const WideArgs a, int fram
         if (e > 0.f) atomicMax(reinterpret_cast<int *>(&emax), __float_as_int(e));
     }
     __syncthreads();
-    const bool ok = wide_cholesky(k, R, T, W, inv);
+    bool ok = true;
+    if (emax <= 1e-5f) {
+        // G = I + E close to I (float32 rows re-orthonormalised every frame):
+        // R = I + X with X upper triangular, X = upper_half(E - X^T X) by two
+        // sweeps from X = upper_half(E) (upper_half halves the diagonal), split
+        // as Xh + Xl in FP32; T = R^{-1} = I - X + X^2 - X^3 (the next terms are
+        // below 1e-20); both summed in FP64
+        const float e = el ? (float)W[t] - (i == l ? 1.f : 0.f) : 0.f; // exact
+        Xh[t] = l > i ? e : (l == i ? 0.5f * e : 0.f);
+        Xl[t] = 0.f;
+        __syncthreads();
+        for (int sweep = 0; sweep < 2; ++sweep) {
+            float pv = 0.f;
+            if (el && l >= i)
+                for (int r = 0; r <= i; ++r) {
+                    pv = fmaf(Xh[r * KW + i], Xh[r * KW + l], pv);
+                    pv = fmaf(Xh[r * KW + i], Xl[r * KW + l], pv);
+                    pv = fmaf(Xl[r * KW + i], Xh[r * KW + l], pv);
+                }
+            __syncthreads();
+            if (el) Xl[t] = l > i ? -pv : (l == i ? -0.5f * pv : 0.f);
+            __syncthreads();
+        }
+        float x2 = 0.f;
+        if (el && l >= i)
+            for (int r = i; r <= l; ++r) x2 = fmaf(Xh[i * KW + r] + Xl[i * KW + r], Xh[r * KW + l] + Xl[r * KW + l], x2);
+        X2[t] = x2;
+        __syncthreads();
+        float x3 = 0.f;
+        if (el && l >= i)
+            for (int r = i; r <= l; ++r) x3 = fmaf(X2[i * KW + r], Xh[r * KW + l], x3);
+        const double xh = (double)Xh[t], xl = (double)Xl[t], id = i == l ? 1.0 : 0.0;
+        R[t] = el ? (id + xh) + xl : 0.0;
+        T[t] = el ? ((id - xh) - xl) + ((double)x2 - (double)x3) : 0.0;
+        __syncthreads();
+    } else {
+        ok = wide_cholesky(k, R, T, W, inv); // also NaN
+    }
     if (t < k) {
         double v = 0.0;
         if (frame_end)
@@ -607,17 +714,19 @@ int sms_now()
 }
 
 // CTAs of the row passes (two per SM, at most one per WT rows) and of the
-// Gram pass (two per SM, at most one per tile block)
+// Gram pass (two per SM, at most one per tile block), at most MAX_CTAS
 int row_grid(const DevParams &prm, int sms)
 {
     const int64_t need = ((int64_t)prm.C * prm.Pp + WT - 1) / WT;
-    return (int)(need < 2 * sms ? need : 2 * sms);
+    const int64_t g = need < 2 * sms ? need : 2 * sms;
+    return (int)(g < MAX_CTAS ? g : MAX_CTAS);
 }
 
 int gram_grid(const DevParams &prm, int sms)
 {
     const int64_t nt = (int64_t)prm.C * prm.npt;
-    return (int)(nt < 2 * sms ? nt : 2 * sms);
+    const int64_t g = nt < 2 * sms ? nt : 2 * sms;
+    return (int)(g < MAX_CTAS ? g : MAX_CTAS);
 }
 
 WideArgs wide_args(const FrameArgs &fa)
@@ -653,17 +762,14 @@ template <typename FT> cudaError_t frame_t(const WideArgs &w, cudaStream_t s)
     const int n_cg = w.prm.n_cg;
     static_assert(offsetof(KState, wproj) == offsetof(KState, wskip) + sizeof(int32_t), "flags side by side");
     WCK(cudaMemsetAsync(&w.ks->wskip, 0, 2 * sizeof(int32_t), s)); // wskip, wproj
+    // each pass's last CTA takes the k-space step that follows it
     for (int pass = 0; pass < n_cg; ++pass) {
-        WCK((k_wide_res<FT, 0><<<grid, WT, 0, s>>>(w)));
-        WCK((k_wide_step<0><<<1, 32, 0, s>>>(w, pass)));
-        WCK((k_wide_res<FT, 1><<<grid, WT, 0, s>>>(w)));
-        WCK((k_wide_step<1><<<1, 32, 0, s>>>(w, pass)));
+        WCK((k_wide_res<FT, 0><<<grid, WT, 0, s>>>(w, pass)));
+        WCK((k_wide_res<FT, 1><<<grid, WT, 0, s>>>(w, pass)));
     }
-    WCK((k_wide_res<FT, 0><<<grid, WT, 0, s>>>(w)));
-    WCK((k_wide_step<2><<<1, 32, 0, s>>>(w, n_cg)));
-    // the projection pass and its angle return at once unless the final step asked for them
-    WCK((k_wide_res<FT, 2><<<grid, WT, 0, s>>>(w)));
-    WCK((k_wide_step<3><<<1, 32, 0, s>>>(w, n_cg)));
+    WCK((k_wide_res<FT, 0><<<grid, WT, 0, s>>>(w, n_cg)));
+    // the projection pass returns at once unless the final step asked for it
+    WCK((k_wide_res<FT, 2><<<grid, WT, 0, s>>>(w, n_cg)));
     WCK((k_wide_update<FT><<<grid, WT, 0, s>>>(w)));
     WCK((k_wide_gram<<<gram_grid(w.prm, sms), GT, 0, s>>>(w.U, w.ks, w.prm, w.part, w.tot, w.counter, 0)));
     WCK((k_wide_factor<<<1, 1024, 0, s>>>(w, 1, 0)));

@@ -432,3 +432,99 @@ def test_window_shared_memory_carve_up_fits_the_launch(k):
         us_end = hs_end + WT * k
         assert us_end * 4 <= smem_grad <= 227 * 1024
     assert (k4 * 4) % 16 == 0   # row t of Ys starts 16-byte aligned for its float4 loads
+
+
+# ---- the passes form (prost_wide.cu) -------------------------------------------
+
+WIDE_CU = _src("prost_wide.cu")
+KW = _const(DEVICE_H, r"constexpr int KMAX = (\d+);")
+TOTF = _const(WIDE_CU, r"constexpr int TOTF = (\d+);")
+assert "constexpr int NB4 = (KW / 4) * (KW / 4 + 1) / 2;" in WIDE_CU
+assert "constexpr int GT = NB4 * 8;" in WIDE_CU
+assert "constexpr int RS = KW + 4;" in WIDE_CU
+assert "const int blk = t >> 3, g = t & 7;" in WIDE_CU
+assert "for (int r = g; r < TILE_P; r += 8) {" in WIDE_CU
+assert "part[(size_t)blockIdx.x * (k * (k + 1) / 2) + (i * k - i * (i - 1) / 2 + (j - i))] = s[p * 4 + q];" in WIDE_CU
+MAX_CTAS = _const(WIDE_CU, r"constexpr int MAX_CTAS = (\d+);")
+RCH = _const(WIDE_CU, r"constexpr int RCH = (\d+);")
+GCH = _const(WIDE_CU, r"constexpr int GCH = (\d+);")
+assert "const int c = u / nv, i = u - (u / nv) * nv;" in WIDE_CU
+NB4 = (KW // 4) * (KW // 4 + 1) // 2
+GT = NB4 * 8
+RS = KW + 4
+
+
+def _gram_block(blk):
+    bi, rem = 0, blk
+    while rem >= KW // 4 - bi:
+        rem -= KW // 4 - bi
+        bi += 1
+    return bi, bi + rem
+
+
+@pytest.mark.parametrize("k", range(1, KW + 1))
+def test_wide_gram_writes_every_packed_entry_once(k):
+    """Thread t of the Gram kernel sums the 4 x 4 block t / 8 over the rows
+    r = t % 8 (mod 8); the lanes with t % 8 = 0 write the block's entries
+    i <= j < k at the packed index of a k-wide upper triangle: every entry of
+    that triangle exactly once, inside the NWG-float row."""
+    nwg = KW * (KW + 1) // 2
+    nm = k * (k + 1) // 2
+    written = np.zeros(nm, np.int64)
+    rows = np.zeros((NB4, TILE_P), np.int64)
+    for t in range(GT):
+        blk, g = t >> 3, t & 7
+        bi, bj = _gram_block(blk)
+        assert 0 <= bi <= bj < KW // 4
+        i0, j0 = 4 * bi, 4 * bj
+        # the 16-byte loads of a staged row stay inside it and aligned
+        assert (i0 * 4) % 16 == 0 and (j0 * 4) % 16 == 0 and j0 + 4 <= RS
+        if j0 >= k:
+            continue
+        rows[blk, g::8] += 1
+        if g != 0:
+            continue
+        for p in range(4):
+            for q in range(4):
+                i, j = i0 + p, j0 + q
+                if i <= j < k:
+                    idx = i * k - i * (i - 1) // 2 + (j - i)
+                    assert 0 <= idx < nm <= nwg
+                    written[idx] += 1
+    assert np.all(written == 1)
+    used = sorted({_gram_block(t >> 3) for t in range(GT) if 4 * _gram_block(t >> 3)[1] < k})
+    for blk in range(NB4):
+        if _gram_block(blk) in used:
+            assert np.all(rows[blk] == 1)  # each working block sums every row once
+    assert TOTF >= nwg + 1
+
+
+def test_wide_staged_tile_fits_and_rows_are_16_byte_aligned():
+    # tile[r * RS + j] for r < TILE_P, j < k <= KW; each row starts on 16 bytes
+    assert (RS * 4) % 16 == 0
+    assert (TILE_P - 1) * RS + KW - 1 < TILE_P * RS
+    # an 8-lane phase of 16-byte loads (one block, rows g + 8 it) touches 8
+    # distinct 4-bank groups: bank of float (r * RS + i0) = (4 r + i0) mod 32
+    for i0 in range(0, KW, 4):
+        banks = {((g * RS + i0) % 32) // 4 for g in range(8)}
+        assert len(banks) == 8
+
+
+@pytest.mark.parametrize("ch,nv", [(RCH, KW + 3), (RCH, 1), (GCH, KW * (KW + 1) // 2), (GCH, 1)])
+def test_wide_chunked_sum_reads_every_row_once(ch, nv):
+    """chunked_sum: unit u = (chunk u / nv, value u % nv) loads rows
+    chunk * CH + q < nrows of its value; every (row, value) exactly once,
+    inside the nrows * nv partial floats, and the chunk sums fit the scratch
+    sized for MAX_CTAS rows."""
+    for nrows in (1, 2, 15, 16, 17, 39, 40, 41, 152, 303, 304, MAX_CTAS):
+        nch = (nrows + ch - 1) // ch
+        seen = np.zeros((nrows, nv), np.int64)
+        for u in range(nv * nch):
+            c, i = u // nv, u % nv
+            assert c * nv + i < nv * ((MAX_CTAS + ch - 1) // ch)
+            for q in range(ch):
+                b = c * ch + q
+                if b < nrows:
+                    assert b * nv + i < nrows * nv
+                    seen[b, i] += 1
+        assert np.all(seen == 1)
