@@ -449,6 +449,9 @@ MAX_CTAS = _const(WIDE_CU, r"constexpr int MAX_CTAS = (\d+);")
 RCH = _const(WIDE_CU, r"constexpr int RCH = (\d+);")
 GCH = _const(WIDE_CU, r"constexpr int GCH = (\d+);")
 assert "const int c = u / nv, i = u - (u / nv) * nv;" in WIDE_CU
+assert "constexpr int GPER = (KW * TILE_P + GT - 1) / GT;" in WIDE_CU
+assert "v[q] = i < n ? __ldcg(src + i) : 0.f;" in WIDE_CU
+assert "const int j = i / TILE_P, r = i - j * TILE_P;" in WIDE_CU and "tile[r * RS + j] = v[q];" in WIDE_CU
 NB4 = (KW // 4) * (KW // 4 + 1) // 2
 GT = NB4 * 8
 RS = KW + 4
@@ -528,3 +531,21 @@ def test_wide_chunked_sum_reads_every_row_once(ch, nv):
                     assert b * nv + i < nrows * nv
                     seen[b, i] += 1
         assert np.all(seen == 1)
+
+
+@pytest.mark.parametrize("k", [1, 4, 5, 17, 31, 32])
+def test_wide_gram_tile_copy_covers_the_block(k):
+    """The Gram kernel's copy of one tile block: thread t's load q is entry
+    i = t + GT q < k TILE_P of the block (column i / TILE_P, row i % TILE_P),
+    stored transposed at r * RS + j: every entry once, inside the tile."""
+    gper = (KW * TILE_P + GT - 1) // GT
+    seen = np.zeros((KW, TILE_P), np.int64)
+    n = k * TILE_P
+    for t in range(GT):
+        for q in range(gper):
+            i = t + GT * q
+            if i < n:
+                j, r = i // TILE_P, i % TILE_P
+                assert r * RS + j < TILE_P * RS
+                seen[j, r] += 1
+    assert np.all(seen[:k] == 1) and np.all(seen[k:] == 0)
