@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--window-only", action="store_true",
                     help="run only the windowed cost study (320x240, n = 64, k = 10) and print its JSON")
+    ap.add_argument("--passes-only", action="store_true",
+                    help="run only the passes-form study (640x480 RGB, k = 16, 24, 32) and print its JSON")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the bfloat16 against float32 storage study")
     return ap.parse_args()
@@ -1006,10 +1008,29 @@ def run_window_only():
     return 0
 
 
+def run_passes_only():
+    import torch
+    import paper_1302_2073_gb300 as pg
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush_rd = torch.ones((256 << 20) // 4, dtype=torch.float32, device=dev)
+    sink = torch.empty(1, dtype=torch.float32, device=dev)
+
+    def flush_l2(t):
+        flush.fill_(t & 0xFF)
+        torch.sum(flush_rd, dim=0, keepdim=True, out=sink)
+
+    print(json.dumps({"passes_form_rgb640x480": passes_form_study(torch, pg, dev, stream, flush_l2)}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.window_only:
         return run_window_only()
+    if args.passes_only:
+        return run_passes_only()
     dist = Dist()
     if args.impl == "reference":
         return run_reference(args, dist)
