@@ -332,7 +332,9 @@ int prost_cost_grad_static(const prost_params *prm, const float *U, const double
  *                        update pass: rows streamed, partial row written,
  *                        arrival; (last CTA) partial rows reduced, Cholesky-QR
  *                        factors and state written.
- * Stamps of phases that did not run are stale.  Synchronises the stream. */
+ * Stamps of phases that did not run are stale.  The passes form writes no
+ * stamps (its launches are timed by prost_set_timing's events).  Synchronises
+ * the stream. */
 #define PROST_TRACE_LEN (PROST_MAX_CG + 13)
 int prost_get_trace(prost_handle *h, uint64_t *ts);
 

@@ -701,16 +701,20 @@ __global__ void __launch_bounds__(WT) k_wide_rebase(float *U, const KState *ks, 
 
 // ---- host side -----------------------------------------------------------------
 
-int g_sms = 0;
+// SMs of the current device (the handle's: its calls run under a device
+// guard), looked up once per device; the partial-sum buffers were sized
+// from the same count
+constexpr int MAX_DEV = 64;
+int g_sms[MAX_DEV];
 
 int sms_now()
 {
-    if (g_sms > 0) return g_sms;
     int dev = 0, n = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return 1;
-    g_sms = n > 0 ? n : 1;
-    return g_sms;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < MAX_DEV && g_sms[dev] > 0) return g_sms[dev];
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+    if (dev >= 0 && dev < MAX_DEV) g_sms[dev] = n;
+    return n;
 }
 
 // CTAs of the row passes (two per SM, at most one per WT rows) and of the
