@@ -11,7 +11,9 @@
 // residuals with Y held in shared memory, accumulates the cost, dF/dmu and its
 // row of dF/dU, and stages its eta_te in shared memory; the block then forms
 // its share of dF/dY = U^T H from the staged tile (k x n outputs, each a sum
-// over the tile's rows).  Per-block partial sums are added in a fixed order
+// over the tile's rows), each thread a 2 x 4 block of outputs over a subset of
+// the rows (one 8-byte load of u and four of eta per 8 multiply-adds).
+// Per-block partial sums are added in a fixed order
 // (FP64 for the scalars), so results are deterministic.  At the window of the
 // measured configuration (m = 76,800, n = 64, k = 10) the three products are
 // about 3 x 98 MFLOP against 20 MB of frames: a few microseconds of CUDA-core
@@ -33,6 +35,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 
@@ -58,7 +61,7 @@ struct WinArgs {
 };
 
 template <int K, bool GRAD>
-__global__ void __launch_bounds__(WT) k_window(WinArgs a)
+__global__ void __launch_bounds__(WT, 2) k_window(WinArgs a)
 {
     // Y transposed, frame t's k values contiguous and padded to a multiple of
     // 4: a thread takes y_t with K4 / 4 vector loads and keeps it for both
@@ -68,7 +71,10 @@ __global__ void __launch_bounds__(WT) k_window(WinArgs a)
     float *sm = reinterpret_cast<float *>(sm4);
     float *Ys = sm;                          // n x K4
     float *Hs = Ys + K4 * a.n;               // WT x (n + 1)
-    float *Us = Hs + (GRAD ? WT * (a.n + 1) : 0); // WT x K
+    // the tile's rows, US floats apart (K rounded up to even: pairs of
+    // columns as one 8-byte load)
+    constexpr int US = (K + 1) / 2 * 2, JP = US / 2;
+    float *Us = Hs + (GRAD ? WT * (a.n + 1) : 0); // WT x US
     const int n = a.n, tid = threadIdx.x;
     const float mu = *a.mu, pw = a.p, e2 = 0.5f * a.p - 1.f, om = a.omega;
     const float gs = (GRAD && a.gscale) ? *a.gscale : 1.f;
@@ -76,11 +82,16 @@ __global__ void __launch_bounds__(WT) k_window(WinArgs a)
         const int t = i / K4, j = i - (i / K4) * K4;
         Ys[i] = j < K ? a.Y[j * n + t] : 0.f;
     }
-    // this thread's entries of the block's dY share: i = tid + WT q
-    constexpr int DQ = (K * NMAXW + WT - 1) / WT;
-    float dyacc[DQ];
+    // the block's dY share, register-tiled: thread tid sums the 2 x 4 block
+    // (columns 2 jp, 2 jp + 1; frames 4 tq .. 4 tq + 3) over the rows
+    // r = g (mod G) of every tile, with G = WT / NB row groups (threads with
+    // g >= G sit out); the groups are added in order at the end
+    const int TQ = (n + 3) / 4, NB = JP * TQ, G = WT / NB;
+    const int bb = tid % NB, g = tid / NB;
+    const int jp = bb / TQ, tq = bb - (bb / TQ) * TQ;
+    float dyacc[8];
 #pragma unroll
-    for (int q = 0; q < DQ; ++q) dyacc[q] = 0.f;
+    for (int q = 0; q < 8; ++q) dyacc[q] = 0.f;
     double cost = 0.0, dmu = 0.0;
     __syncthreads();
     const int64_t ntiles = (a.m + WT - 1) / WT;
@@ -149,18 +160,28 @@ __global__ void __launch_bounds__(WT) k_window(WinArgs a)
 #pragma unroll
                 for (int j = 0; j < K; ++j) a.dU[e * K + j] = gs * du[j];
 #pragma unroll
-            for (int j = 0; j < K; ++j) Us[tid * K + j] = u[j];
+            for (int j = 0; j < US; ++j) Us[tid * US + j] = j < K ? u[j] : 0.f;
             __syncthreads();
             const int rows = (int)min((int64_t)WT, a.m - tile * WT);
+            if (g < G) {
+                const int t0 = 4 * tq;
+                float s[8];
 #pragma unroll
-            for (int q = 0; q < DQ; ++q) {
-                const int i = tid + WT * q;
-                if (i < K * n) {
-                    const int j = i / n, t = i - (i / n) * n;
-                    float s = 0.f;
-                    for (int r = 0; r < rows; ++r) s = fmaf(Us[r * K + j], Hs[r * (n + 1) + t], s);
-                    dyacc[q] += s;
+                for (int q = 0; q < 8; ++q) s[q] = 0.f;
+                for (int r = g; r < rows; r += G) {
+                    const float2 uu = *reinterpret_cast<const float2 *>(Us + r * US + 2 * jp);
+                    const float *hr = Hs + r * (n + 1) + t0;
+                    float h[4];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) h[c] = t0 + c < n ? hr[c] : 0.f;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        s[c] = fmaf(uu.x, h[c], s[c]);
+                        s[4 + c] = fmaf(uu.y, h[c], s[4 + c]);
+                    }
                 }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dyacc[q] += s[q];
             }
             __syncthreads();
         }
@@ -168,10 +189,21 @@ __global__ void __launch_bounds__(WT) k_window(WinArgs a)
     // block partial: dY share, cost, dmu (the scalars reduced in FP64)
     double *part = a.partials + (size_t)blockIdx.x * (K * n + 2);
     if (GRAD) {
+        // the row groups' sums added in group order (the eta and row tiles
+        // are free now; the host sizes them to hold WT x 8 floats at least)
+        float *red8 = Hs;
+        if (g < G)
 #pragma unroll
-        for (int q = 0; q < DQ; ++q) {
-            const int i = tid + WT * q;
-            if (i < K * n) part[i] = (double)dyacc[q];
+            for (int q = 0; q < 8; ++q) red8[(g * NB + bb) * 8 + q] = dyacc[q];
+        __syncthreads();
+        if (g == 0) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float v = 0.f;
+                for (int gg = 0; gg < G; ++gg) v += red8[(gg * NB + bb) * 8 + q];
+                const int j = 2 * jp + q / 4, t = 4 * tq + (q & 3);
+                if (j < K && t < n) part[j * n + t] = (double)v;
+            }
         }
     }
     __shared__ double red[2][WT / 32];
@@ -511,7 +543,11 @@ extern "C" int prost_window_init(int64_t m, int32_t channels, int32_t k, int32_t
     w->nblocks = (int)(tiles < 2 * sms ? tiles : 2 * sms);
     w->nb_u = sms; // cooperative: one CTA per SM
     w->smem_cost = (size_t)((k + 3) / 4 * 4) * n * sizeof(float);
-    w->smem_grad = w->smem_cost + (size_t)WT * (n + 1) * sizeof(float) + (size_t)WT * k * sizeof(float);
+    // the gradient pass's eta tile (WT x (n + 1)) and row tile (WT x even k),
+    // at least WT x 8 floats: after the last tile that space holds the row
+    // groups' 2 x 4 dY blocks (G x NB <= WT blocks of 8)
+    const size_t grad_floats = std::max((size_t)WT * (n + 1) + (size_t)WT * ((k + 1) / 2 * 2), (size_t)WT * 8);
+    w->smem_grad = w->smem_cost + grad_floats * sizeof(float);
     auto bail = [&](int code) {
         g_win_err = w->err;
         win_free(w);

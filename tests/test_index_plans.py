@@ -411,26 +411,28 @@ def test_resampling_footprints_stay_in_the_input_and_cover_it_exactly(n_in, n_ou
 
 NMAXW = _const(WINDOW_CU, r"constexpr int NMAXW = (\d+);")
 assert "float *Hs = Ys + K4 * a.n;" in WINDOW_CU
-assert "float *Us = Hs + (GRAD ? WT * (a.n + 1) : 0); // WT x K" in WINDOW_CU
+assert "float *Us = Hs + (GRAD ? WT * (a.n + 1) : 0); // WT x US" in WINDOW_CU
 assert "w->smem_cost = (size_t)((k + 3) / 4 * 4) * n * sizeof(float);" in WINDOW_CU
-assert ("w->smem_grad = w->smem_cost + (size_t)WT * (n + 1) * sizeof(float) + (size_t)WT * k * sizeof(float);"
-        in WINDOW_CU)
+assert "w->smem_grad = w->smem_cost + grad_floats * sizeof(float);" in WINDOW_CU
 
 
 @pytest.mark.parametrize("k", range(1, KMAXW + 1))
 def test_window_shared_memory_carve_up_fits_the_launch(k):
-    """Ys (n x K4), then with gradients Hs (WT x (n + 1)) and Us (WT x k):
-    the carve-up ends inside the dynamic shared memory each launch asks for,
-    which stays inside the 227 KB a CTA may have."""
+    """Ys (n x K4), then with gradients Hs (WT x (n + 1)) and Us (WT x US, k
+    rounded up to even), at least WT x 8 floats after Ys: the carve-up ends
+    inside the dynamic shared memory each launch asks for, which stays inside
+    the 227 KB a CTA may have; Us starts 8-byte aligned for its pair loads."""
     k4 = (k + 3) // 4 * 4
+    us = (k + 1) // 2 * 2
     for n in range(1, NMAXW + 1):
         smem_cost = k4 * n * 4
-        smem_grad = smem_cost + WT * (n + 1) * 4 + WT * k * 4
+        smem_grad = smem_cost + max(WT * (n + 1) + WT * us, WT * 8) * 4
         ys_end = k4 * n
         assert ys_end * 4 <= smem_cost
         hs_end = ys_end + WT * (n + 1)
-        us_end = hs_end + WT * k
+        us_end = hs_end + WT * us
         assert us_end * 4 <= smem_grad <= 227 * 1024
+        assert (hs_end * 4) % 8 == 0
     assert (k4 * 4) % 16 == 0   # row t of Ys starts 16-byte aligned for its float4 loads
 
 
@@ -549,3 +551,39 @@ def test_wide_gram_tile_copy_covers_the_block(k):
                 assert r * RS + j < TILE_P * RS
                 seen[j, r] += 1
     assert np.all(seen[:k] == 1) and np.all(seen[k:] == 0)
+
+
+# ---- the window pass's register-tiled dY product (prost_window.cu) ----------------
+
+assert "constexpr int US = (K + 1) / 2 * 2, JP = US / 2;" in WINDOW_CU
+assert "const int TQ = (n + 3) / 4, NB = JP * TQ, G = WT / NB;" in WINDOW_CU
+assert "const int jp = bb / TQ, tq = bb - (bb / TQ) * TQ;" in WINDOW_CU
+assert "red8[(g * NB + bb) * 8 + q] = dyacc[q];" in WINDOW_CU
+assert "std::max((size_t)WT * (n + 1) + (size_t)WT * ((k + 1) / 2 * 2), (size_t)WT * 8)" in WINDOW_CU
+
+
+@pytest.mark.parametrize("k", range(1, KMAXW + 1))
+def test_window_dy_tiles_cover_every_entry_inside_the_scratch(k):
+    """Thread bb + NB g of the gradient pass sums the 2 x 4 dY block bb
+    (columns 2 jp, 2 jp + 1, frames 4 tq .. 4 tq + 3) over the rows r = g
+    (mod G); every (column < k, frame < n) entry is written once, the pair
+    loads stay inside the row tile, and the row groups' blocks (G x NB x 8
+    floats) fit the eta and row tiles as the host sizes them."""
+    us = (k + 1) // 2 * 2
+    jp_n = us // 2
+    for n in range(1, NMAXW + 1):
+        tq_n = (n + 3) // 4
+        nb = jp_n * tq_n
+        g_n = WT // nb
+        assert g_n >= 1
+        grad_floats = max(WT * (n + 1) + WT * us, WT * 8)
+        assert ((g_n - 1) * nb + nb - 1) * 8 + 7 < grad_floats
+        seen = np.zeros((k, n), np.int64)
+        for bb in range(nb):
+            jp, tq = bb // tq_n, bb % tq_n
+            assert 2 * jp + 1 < us
+            for q in range(8):
+                j, t = 2 * jp + q // 4, 4 * tq + (q & 3)
+                if j < k and t < n:
+                    seen[j, t] += 1
+        assert np.all(seen == 1)
