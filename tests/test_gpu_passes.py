@@ -280,3 +280,98 @@ def test_runs_are_reproducible_and_match_the_grid_form_at_k16():
     # the two forms sum in different orders: the same subspace to FP32 rounding
     assert _angle_max(Ua, Ug) < 1e-5
     assert np.linalg.norm(ya - yg) <= 1e-5 * np.linalg.norm(yg)
+
+
+def _wide(k=20, **over):
+    vid, wp = synth.make_workload("rgb640x480_k10", width=48, height=36, k=k, n_frames=12)
+    return vid, dict(wp, **over)
+
+
+def _sub(h, vid):
+    U = np.empty((vid.m, vid.k), np.float32)
+    y = np.empty(vid.k)
+    pg.prost_get_subspace(h, U, y)
+    return U, y
+
+
+@pytest.mark.parametrize("k", [17, 32])
+def test_initial_subspace_roundtrip_and_rank_check(k):
+    vid, wp = _wide(k)
+    hs = [pg.prost_init(gpu_params(wp, seed=s)) for s in (1, 1, 2)]
+    try:
+        Us = [_sub(h, vid) for h in hs]
+        for U, y in Us:
+            np.testing.assert_allclose(U.T.astype(np.float64) @ U, np.eye(k), atol=2e-6)
+            assert np.all(y == 0)
+        assert np.array_equal(Us[0][0], Us[1][0]) and not np.allclose(Us[0][0], Us[2][0])
+        U0 = synth.random_orthonormal(vid.m, k, 5).astype(np.float32)
+        y0 = np.arange(1.0, k + 1)
+        pg.prost_set_subspace(hs[0], U0, y0)
+        U, y = _sub(hs[0], vid)
+        np.testing.assert_allclose(U, U0, atol=1e-6)
+        np.testing.assert_allclose(U.astype(np.float64) @ y, U0.astype(np.float64) @ y0, atol=1e-5)
+        U0[:, 3] = 0.0
+        with pytest.raises(pg.ProstError) as ei:
+            pg.prost_set_subspace(hs[1], U0)
+        assert ei.value.code == pg.PROST_ENOTSPD
+    finally:
+        for h in hs:
+            pg.prost_destroy(h)
+
+
+def test_host_device_and_pipelined_paths_agree_bit_for_bit():
+    vid, wp = _wide(20)
+    host = [np.ascontiguousarray(vid.frame(t)[0]) for t in range(8)]
+    pinned = [torch.from_numpy(f).pin_memory() for f in host]
+    a, b, c = (pg.prost_init(gpu_params(wp, seed=3)) for _ in range(3))
+    try:
+        ma, mb, mc = [], [], []
+        for t in range(8):
+            m = np.empty(vid.P, np.uint8)
+            assert pg.prost_step(a, host[t], m) == pg.PROST_OK
+            ma.append(m)
+            fd = torch.from_numpy(host[t]).cuda()
+            md = torch.empty(vid.P, dtype=torch.uint8, device="cuda")
+            pg.prost_step(b, fd, md)
+            mb.append(md)
+        assert pg.prost_sync(b) == pg.PROST_OK
+        outs = [torch.empty(vid.P, dtype=torch.uint8).pin_memory() for _ in range(8)]
+        for t in range(8):
+            pg.prost_step_async(c, pinned[t], outs[t])
+            if t >= 1:
+                assert pg.prost_wait(c) == pg.PROST_OK
+        assert pg.prost_wait(c) == pg.PROST_OK
+        for t in range(8):
+            assert np.array_equal(ma[t], mb[t].cpu().numpy()) and np.array_equal(ma[t], outs[t].numpy())
+        (Ua, ya), (Ub, yb), (Uc, yc) = _sub(a, vid), _sub(b, vid), _sub(c, vid)
+        assert np.array_equal(Ua, Ub) and np.array_equal(Ua, Uc)
+        assert np.array_equal(ya, yb) and np.array_equal(ya, yc)
+    finally:
+        for h in (a, b, c):
+            pg.prost_destroy(h)
+
+
+def test_checkpoint_and_injection_limits_of_the_passes_form():
+    vid, wp = _wide(24)
+    a = pg.prost_init(gpu_params(wp, seed=4))
+    b = pg.prost_init(gpu_params(wp, seed=9))
+    try:
+        for t in range(3):
+            assert pg.prost_step(a, vid.frame(t)[0], np.empty(vid.P, np.uint8)) == pg.PROST_OK
+        state = pg.prost_get_state(a)
+        pg.prost_set_state(b, state)
+        for t in range(3, 6):
+            f = vid.frame(t)[0]
+            ma, mb = np.empty(vid.P, np.uint8), np.empty(vid.P, np.uint8)
+            assert pg.prost_step(a, f, ma) == pg.PROST_OK and pg.prost_step(b, f, mb) == pg.PROST_OK
+            assert np.array_equal(ma, mb)
+        (Ua, ya), (Ub, yb) = _sub(a, vid), _sub(b, vid)
+        assert np.array_equal(Ua, Ub) and np.array_equal(ya, yb)
+        # the passes form has no grid barrier to skew or stall
+        for call in (lambda: pg.prost_inject_barrier_skew(a, -1), lambda: pg.prost_inject_wait_timeout(a, 0, 1000)):
+            with pytest.raises(pg.ProstError) as ei:
+                call()
+            assert ei.value.code == pg.PROST_EINVAL
+    finally:
+        pg.prost_destroy(a)
+        pg.prost_destroy(b)
