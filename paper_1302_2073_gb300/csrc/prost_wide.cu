@@ -765,7 +765,8 @@ template <typename FT> cudaError_t frame_t(const WideArgs &w, cudaStream_t s)
     const int grid = row_grid(w.prm, sms);
     const int n_cg = w.prm.n_cg;
     static_assert(offsetof(KState, wproj) == offsetof(KState, wskip) + sizeof(int32_t), "flags side by side");
-    WCK(cudaMemsetAsync(&w.ks->wskip, 0, 2 * sizeof(int32_t), s)); // wskip, wproj
+    const cudaError_t e0 = cudaMemsetAsync(&w.ks->wskip, 0, 2 * sizeof(int32_t), s); // wskip, wproj
+    if (e0 != cudaSuccess) return e0;
     // each pass's last CTA takes the k-space step that follows it
     for (int pass = 0; pass < n_cg; ++pass) {
         WCK((k_wide_res<FT, 0><<<grid, WT, 0, s>>>(w, pass)));
