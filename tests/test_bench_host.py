@@ -67,6 +67,9 @@ def test_l2_roofline_arithmetic():
     assert r["frac"] == pytest.approx(2746.0 / r["peak"])
     # slices x sectors/cycle x bytes/sector x L2 clock, from the capture
     assert r["peak"] == pytest.approx(188 * 3 * 32 * 2.001746, rel=1e-4)
+    assert "measured_copy_gbs" not in r
+    m = bench.l2_roofline(2746.0, True, 20000.0)
+    assert m["measured_copy_gbs"] == 20000.0 and m["frac_of_measured_copy"] == pytest.approx(2746.0 / 20000.0)
     assert bench.l2_roofline(2746.0, False) is None
 
 
