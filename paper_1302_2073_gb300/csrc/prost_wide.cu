@@ -13,7 +13,8 @@
 // update pass (geodesic step, labels, weights) and a tiled Gram pass of the
 // new rows follow; one CTA then factors the Gram (Cholesky-QR, FP64).  Every
 // cross-CTA sum is a fixed-order sum by the last CTA to finish, so results are
-// reproducible run to run.  The k-space vectors live in KState between the
+// reproducible run to run, and that CTA then takes the k-space step that
+// follows the pass.  The k-space vectors live in KState between the
 // launches.  Arrays are KMAX wide; entries at and beyond k are zero.
 #include <stdint.h>
 #include <string.h>
