@@ -55,9 +55,12 @@ __device__ __forceinline__ int64_t overlap(int q, int n_out, int64_t lo, int64_t
 template <typename FT>
 __device__ __forceinline__ float resample_at(const FT *in, const PreGeom &g, int64_t e)
 {
-    const int per = g.h_out * g.w_out;
-    const int c = (int)(e / per);
-    const int r = (int)(e - (int64_t)c * per);
+    // n_out = C h_out w_out < 2^32 (planes of at most 2^30 pixels, C <= 4):
+    // a 32-bit unsigned division is exact
+    const uint32_t per = (uint32_t)g.h_out * (uint32_t)g.w_out;
+    const uint32_t eu = (uint32_t)e;
+    const int c = (int)(eu / per);
+    const int r = (int)(eu - (uint32_t)c * per);
     const int i = r / g.w_out, j = r - (r / g.w_out) * g.w_out;
     int y0, y1, x0, x1;
     int64_t ylo, yhi, xlo, xhi;
