@@ -802,6 +802,11 @@ def _config(args, vid, wp, steps, u_bytes=None):
 
 # ---- our implementation ------------------------------------------------------
 
+# the handle's kernel form (prost_stats.form) and the kernel that runs it
+FORM_NAME = {1: "grid", 2: "cluster", 3: "passes", 4: "resident"}
+FORM_KERNEL = {1: "k_frame", 2: "k_frame_cluster", 3: "k_wide_*", 4: "k_frame_res"}
+
+
 def run_ours(args, dist):
     import torch
 
@@ -856,6 +861,7 @@ def run_ours(args, dist):
                 i, f = which(t)
                 pg.prost_step(hs[i], frames[i][f], masks[t % 2])
         torch.cuda.synchronize()
+        form = pg.prost_get_stats(hs[0]).form
         dist.barrier(torch)
         torch.cuda.synchronize()
 
@@ -968,10 +974,10 @@ def run_ours(args, dist):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": n, "steps": K, "warmup": W,
            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": _config(args, vid, wp, K, u_bytes),
+           "config": dict(_config(args, vid, wp, K, u_bytes), form=FORM_NAME.get(form, str(form))),
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": achieved / peak, "traffic": profiled_traffic() if profiled else None,
-                        "kernel": f"k_frame<{k},{vid.dtype}> (whole frame, one launch)",
+                        "kernel": f"{FORM_KERNEL.get(form, 'k_frame')}<{k},{vid.dtype}> (whole frame, one launch)",
                         "bytes_per_launch": frame_bytes, "launch_ms": launch_ms,
                         "peak_source": f"{peak_src} hbm_gbs"},
            "roofline_l2": l2_roofline(achieved, profiled, l2_copy_gbs(torch, dev) if profiled else None),

@@ -91,11 +91,17 @@ extern "C" {
  * then the curvature sum_e c_e (u_e^T d)^2 of the line step), with k chosen at
  * run time; float32 storage only.  GRID and CLUSTER exist for
  * k <= PROST_MAX_K_SINGLE; PASSES for every k and the only form above it, which
- * AUTO then picks.  Failure injection (prost_inject_*) needs GRID. */
+ * AUTO then picks.  RESIDENT (k <= 10): the GRID form with each CTA owning
+ * a range of pixels of every channel, whose rows, frame entries and labels it
+ * keeps in shared memory after the first pass of a frame, so that the later
+ * passes stream from there and only the rows that do not fit come from L2
+ * again; AUTO picks it over GRID when at least half of the rows fit.
+ * Failure injection (prost_inject_*) needs GRID or RESIDENT. */
 #define PROST_FORM_AUTO 0
 #define PROST_FORM_GRID 1
 #define PROST_FORM_CLUSTER 2
 #define PROST_FORM_PASSES 3
+#define PROST_FORM_RESIDENT 4
 #define PROST_CLUSTER_MAX_U_BYTES (1u << 20)
 
 #define PROST_MAX_K 32        /* largest subspace dimension (PASSES form above PROST_MAX_K_SINGLE) */
@@ -119,8 +125,8 @@ typedef struct prost_params {
     int32_t frame_dtype;             /* PROST_U8 or PROST_F32 */
     int32_t u_dtype;                 /* PROST_F32 or PROST_BF16 (subspace storage) */
     int32_t mask_from;               /* PROST_MASK_POST_UPDATE or PROST_MASK_PRE_UPDATE */
-    int32_t form;                    /* kernel form: PROST_FORM_AUTO (0), PROST_FORM_GRID, PROST_FORM_CLUSTER
-                                        or PROST_FORM_PASSES */
+    int32_t form;                    /* kernel form: PROST_FORM_AUTO (0), PROST_FORM_GRID, PROST_FORM_CLUSTER,
+                                        PROST_FORM_PASSES or PROST_FORM_RESIDENT */
     uint64_t seed;                   /* seed of the random initial subspace (Section 3.4) */
 } prost_params;
 
@@ -148,7 +154,8 @@ typedef struct prost_stats {
                                         by an extra pass over U: the identity
                                         |pi(eta)|^2 = |eta|^2 - |U^T eta|^2 (Eq. gproject)
                                         loses its digits when |pi(eta)|^2 < |eta|^2 / 4 */
-    int32_t form;                    /* PROST_FORM_GRID, PROST_FORM_CLUSTER or PROST_FORM_PASSES: the handle's form */
+    int32_t form;                    /* PROST_FORM_GRID, PROST_FORM_CLUSTER, PROST_FORM_PASSES or
+                                        PROST_FORM_RESIDENT: the handle's form */
 } prost_stats;
 
 /* Sizes of the device state of a handle with these parameters (bytes, device
@@ -206,8 +213,8 @@ int prost_sync(prost_handle *h);
  * that gave up part-way leaves it.  The next frame launch finds the count
  * outside the range it expects and returns at once, leaving the state
  * untouched; on the host path prost_step() returns PROST_ETIMEOUT and leaves
- * its outputs unwritten.  Grid form only (PROST_EINVAL for the cluster and
- * passes forms, which have no software grid barrier).  The following prost_sync() reports PROST_ETIMEOUT
+ * its outputs unwritten.  Grid and resident forms only (PROST_EINVAL for the
+ * cluster and passes forms, which have no software grid barrier).  The following prost_sync() reports PROST_ETIMEOUT
  * and resets the barrier, and later frames run normally (the refused frame
  * does not count towards the periodic rebase).  A launch can only detect a
  * backward skew (delta < 0) or a forward one of at least the frame kernel's
@@ -223,8 +230,8 @@ int prost_inject_barrier_skew(prost_handle *h, int64_t delta);
  * second).  The bounded wait then runs out as it would on a stalled GPU: the
  * frame aborts with the state untouched (U, y, labels, frame counter), on the
  * host path prost_step() returns PROST_ETIMEOUT, and prost_sync() reports
- * PROST_ETIMEOUT and resets the barrier.  Applies to one launch.  Grid form
- * only.  Errors: PROST_EINVAL (NULL handle, pass or cycles out of range, the
+ * PROST_ETIMEOUT and resets the barrier.  Applies to one launch.  Grid and
+ * resident forms only.  Errors: PROST_EINVAL (NULL handle, pass or cycles out of range, the
  * cluster or passes form). */
 int prost_inject_wait_timeout(prost_handle *h, int32_t pass, int64_t cycles);
 

@@ -25,6 +25,8 @@ struct prost_handle {
     int num_sms;
     int grid_frame, grid_gram;
     int cluster_grid;      // > 0: the frame kernel runs as one cluster of this many CTAs
+    int grid_res;          // > 0: the frame kernel runs in the resident form on this many CTAs
+    int res_ns, res_smem;  // its row slots per CTA and dynamic shared memory (bytes)
     int wide;              // the passes form (a sequence of ordinary launches per frame)
     void *U;               // stored subspace (C x npt tile blocks of k x TILE_P float32 or bfloat16)
     uint8_t *labels;       // previous labels (Pp bytes)
@@ -136,7 +138,8 @@ int check_params(const prost_params *prm, DevParams *dp, std::string *why)
     if (p.frame_dtype != PROST_U8 && p.frame_dtype != PROST_F32) { *why = "frame_dtype must be PROST_U8 or PROST_F32"; return PROST_EINVAL; }
     if (p.u_dtype != PROST_F32 && p.u_dtype != PROST_BF16) { *why = "u_dtype must be PROST_F32 or PROST_BF16"; return PROST_EINVAL; }
     if (p.mask_from != PROST_MASK_POST_UPDATE && p.mask_from != PROST_MASK_PRE_UPDATE) { *why = "mask_from must be 0 or 1"; return PROST_EINVAL; }
-    if (p.form != PROST_FORM_AUTO && p.form != PROST_FORM_GRID && p.form != PROST_FORM_CLUSTER && p.form != PROST_FORM_PASSES) { *why = "form must be PROST_FORM_AUTO, PROST_FORM_GRID, PROST_FORM_CLUSTER or PROST_FORM_PASSES"; return PROST_EINVAL; }
+    if (p.form != PROST_FORM_AUTO && p.form != PROST_FORM_GRID && p.form != PROST_FORM_CLUSTER && p.form != PROST_FORM_PASSES && p.form != PROST_FORM_RESIDENT) { *why = "form must be PROST_FORM_AUTO, PROST_FORM_GRID, PROST_FORM_CLUSTER, PROST_FORM_PASSES or PROST_FORM_RESIDENT"; return PROST_EINVAL; }
+    if (p.form == PROST_FORM_RESIDENT && p.k > KREG) { *why = "the resident form needs k <= 10"; return PROST_EINVAL; }
     const bool passes = p.form == PROST_FORM_PASSES || p.k > KFRAME;
     if (p.k > KFRAME && p.form != PROST_FORM_AUTO && p.form != PROST_FORM_PASSES) { *why = "k > 16 runs in the passes form only (form AUTO or PROST_FORM_PASSES)"; return PROST_EINVAL; }
     if (passes && p.u_dtype != PROST_F32) { *why = "the passes form (every k > 16) stores the subspace in float32 only"; return PROST_EINVAL; }
@@ -369,9 +372,35 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
             }
         }
     }
+    // the resident form: every CTA keeps its rows in shared memory across the
+    // passes of a frame; AUTO takes it when at least half of them fit
+    h->grid_res = 0;
+    h->res_ns = 0;
+    h->res_smem = 0;
+    if (!wide && !h->cluster_grid && ops->res_plan &&
+        (prm->form == PROST_FORM_AUTO || prm->form == PROST_FORM_RESIDENT)) {
+        int64_t g = (int64_t)occ * h->num_sms;
+        if (g > res_units(dp.P)) g = res_units(dp.P); // every CTA gets at least one unit
+        if (g > max_frame_grid((int)partial_row(prm->k))) g = max_frame_grid((int)partial_row(prm->k));
+        int ns = 0, smem = 0;
+        if (g >= 1 && ops->res_plan(fdt, dp.P, dp.C, (int)g, &ns, &smem)) {
+            const int64_t nim = (int64_t)dp.C * res_npair_max(dp.P, (int)g);
+            if (prm->form == PROST_FORM_RESIDENT || 2 * (int64_t)ns >= nim) {
+                h->grid_res = (int)g;
+                h->res_ns = ns;
+                h->res_smem = smem;
+            }
+        }
+        (void)cudaGetLastError(); // a refused plan leaves no error behind
+        if (!h->grid_res && prm->form == PROST_FORM_RESIDENT) {
+            h->err = "the resident form does not fit this device";
+            return bail(PROST_EINVAL);
+        }
+    }
     // the Gram kernel's rows, or the frame kernel's two value-major buffers
     h->partial_floats = std::max((size_t)h->grid_gram * partial_row(prm->k),
-                                 (size_t)2 * col_stride(h->grid_frame) * partial_row(prm->k));
+                                 (size_t)2 * col_stride(std::max(h->grid_frame, h->grid_res)) *
+                                     partial_row(prm->k));
     if (wide) h->partial_floats = wide_partial_floats(dp, h->num_sms);
 
     CKI(cudaMalloc(&h->U, (size_t)prm->k * dp.C * dp.Pp * u_elem_bytes(dp)));
@@ -423,18 +452,22 @@ int launch_frame(prost_handle *h, const void *fptr, int64_t pitch, uint8_t *mask
     fa.bar_base = h->bar_base;
     fa.frame_pitch = pitch;
     const bool cl = h->cluster_grid > 0;
-    const int grid = cl ? h->cluster_grid : h->grid_frame;
+    const bool res = h->grid_res > 0;
+    const int grid = cl ? h->cluster_grid : (res ? h->grid_res : h->grid_frame);
     fa.col_stride = col_stride(grid);
     fa.grid = grid;
     fa.stall_at = h->stall_at;
     fa.stall_limit = h->stall_limit;
     fa.status_out = status_dev;
     fa.counter = h->counter;
+    fa.res_ns = h->res_ns;
     h->stall_at = 0; // one launch only
     fa.prm = h->dp;
     if (h->timing) CK(h, cudaEventRecord(h->ev[0], h->stream));
     if (cl)
         CK(h, h->ops->frame_cluster(fa, h->prm.frame_dtype, grid, h->stream));
+    else if (res)
+        CK(h, h->ops->frame_res(fa, h->prm.frame_dtype, grid, h->res_smem, h->stream));
     else
         CK(h, h->ops->frame(fa, h->prm.frame_dtype, grid, h->stream));
     if (h->timing) {
@@ -600,7 +633,7 @@ int prost_inject_barrier_skew(prost_handle *h, int64_t delta)
     // the launch cannot tell it from a healthy barrier
     if (h->cluster_grid > 0) return fail(h, PROST_EINVAL, "the cluster form has no grid barrier");
     if (h->wide) return fail(h, PROST_EINVAL, "the passes form has no grid barrier");
-    if (delta > 0 && delta < (int64_t)h->grid_frame)
+    if (delta > 0 && delta < (int64_t)(h->grid_res > 0 ? h->grid_res : h->grid_frame))
         return fail(h, PROST_EINVAL, "a forward skew below the grid size is not detectable");
     DeviceGuard dg(h->device);
     GridBar g;
@@ -735,7 +768,9 @@ int prost_get_stats(prost_handle *h, prost_stats *out)
     out->orth_err = ks.orth_err;
     out->eta_norm = ks.eta_norm;
     out->pi_explicit = ks.pi_explicit;
-    out->form = h->wide ? PROST_FORM_PASSES : (h->cluster_grid > 0 ? PROST_FORM_CLUSTER : PROST_FORM_GRID);
+    out->form = h->wide ? PROST_FORM_PASSES
+                        : (h->cluster_grid > 0 ? PROST_FORM_CLUSTER
+                                               : (h->grid_res > 0 ? PROST_FORM_RESIDENT : PROST_FORM_GRID));
     return PROST_OK;
 }
 

@@ -21,6 +21,21 @@ constexpr int RED_ROWS = 24;
 constexpr int RED_SCR = 1280;
 __host__ __device__ constexpr int max_frame_grid(int nv) { return RED_SCR / nv * RED_ROWS; }
 
+// The register form of the single-launch frame kernel (rows loaded straight
+// into registers) serves k <= KREG; the resident form is its variant.
+constexpr int KREG = 10;
+
+// The resident form deals the pixels of a plane to its CTAs in units of
+// RES_UNIT pixels (every CTA takes all channels of its pixels).
+constexpr int RES_UNIT = 64;
+__host__ __device__ constexpr size_t res_al16(size_t b) { return (b + 15) & ~(size_t)15; }
+__host__ __device__ inline int64_t res_units(int64_t P) { return (P + RES_UNIT - 1) / RES_UNIT; }
+// pixel pairs per channel of the CTA with the most units
+__host__ __device__ inline int res_npair_max(int64_t P, int G)
+{
+    return (int)((res_units(P) + G - 1) / G) * (RES_UNIT / 2);
+}
+
 // Grid-barrier arrivals of every frame-kernel CTA per frame: one per residual
 // pass (n_cg + 1), one for the projection pass (made at the end of the frame
 // when that pass does not run) and one at the end of the frame.
@@ -137,6 +152,7 @@ struct FrameArgs {
     long long stall_limit;
     int32_t *status_out;      // optional (device): the frame's status, as last_status
     unsigned int *counter;    // arrival counter of the pass-sequence form's reductions (zero between launches)
+    int res_ns;               // resident form: row slots (items) per CTA in shared memory
     DevParams prm;
 };
 
@@ -159,6 +175,11 @@ struct KernelOps {
     int vw;        // pixels per thread of the Gram kernel
     int tile;      // pixels per tile of the frame kernel
     int frame_threads;
+    // the resident form (k <= 10; null otherwise): its plan for P pixels of
+    // C channels on `grid` CTAs (the row slots per CTA and the dynamic shared
+    // memory; 0 when it cannot run), and its launch
+    int (*res_plan)(int frame_dtype, int64_t P, int C, int grid, int *ns, int *smem);
+    cudaError_t (*frame_res)(const FrameArgs &, int frame_dtype, int grid, int smem, cudaStream_t);
 };
 
 // kernels without a k template

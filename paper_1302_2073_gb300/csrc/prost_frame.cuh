@@ -32,6 +32,8 @@
 
 #include <string.h>
 
+#include <type_traits>
+
 #include "prost_kernels.cuh"
 #include "prost_stage.cuh"
 
@@ -46,7 +48,7 @@ template <int K, typename UT = float> struct FCfg {
     // shared memory: float32 8 warps of up to 255 registers; bfloat16 16 warps
     // of up to 128 registers (the products of the passes on tensor cores leave
     // a lane few sums).  One CTA per SM.
-    static constexpr bool STREAM = K >= 11;
+    static constexpr bool STREAM = K > KREG;
     static constexpr int THREADS = STREAM && sizeof(UT) == 4 ? 256 : 512;
     static constexpr int NW = THREADS / 32;
     static constexpr int TP = TILE_P;            // pixels per tile
@@ -1007,12 +1009,362 @@ __device__ __forceinline__ void proj_pass(const FrameArgs &a, const FrameTiles &
     }
 }
 
+// ---- the resident form (k <= 10) ------------------------------------------------
+// CTA b owns the pixels [pa, pa + 2 npair) of every channel plane, the planes
+// cut into units of RES_UNIT pixels dealt evenly over the grid; an item is two
+// consecutive pixels of one channel, items channel-major (item c npair + q).
+// The first residual pass of a frame reads every item's rows, frame entries
+// and labels from global memory and keeps them in shared memory: the frame
+// entries and labels of every item, and the rows of items [ng, nitems) in ns
+// slots (all of them when they fit).  The later passes of the frame read them
+// from there and stream only the rows of items [0, ng) from L2 again; those are
+// every thread's first items, so their load latency overlaps the other warps'
+// shared-memory items.  The update pass reads the old rows the same way and
+// writes the new ones to global memory.
+struct ResPart {
+    int64_t pa; // first pixel
+    int npair;  // pixel pairs per channel (the last may hold one pixel)
+    int nitems; // C npair
+    int ng;     // items whose rows stream from global memory in every pass
+    __device__ ResPart(const DevParams &prm, int G, int b, int ns)
+    {
+        const int64_t nu = res_units(prm.P);
+        const int64_t lo = nu * b / G, hi = nu * (b + 1) / G;
+        pa = lo * RES_UNIT;
+        const int64_t pb = hi * RES_UNIT < prm.P ? hi * RES_UNIT : prm.P;
+        const int npx = pb > pa ? (int)(pb - pa) : 0;
+        npair = (npx + 1) / 2;
+        nitems = prm.C * npair;
+        ng = nitems > ns ? nitems - ns : 0;
+    }
+};
+
+// a pair of consecutive stored entries: 8 bytes of float32, 4 of bfloat16
+template <typename UT> struct RPair;
+template <> struct RPair<float> {
+    using T = float2;
+    static __device__ __forceinline__ T ldg(const float *p) { return __ldcg(reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ float2 wide(T v) { return v; }
+    static __device__ __forceinline__ T pack(float a, float b) { return make_float2(a, b); }
+};
+template <> struct RPair<bf16> {
+    using T = uint32_t;
+    static __device__ __forceinline__ T ldg(const bf16 *p) { return __ldcg(reinterpret_cast<const unsigned int *>(p)); }
+    static __device__ __forceinline__ float2 wide(T w)
+    {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    // a and b already hold bfloat16 values (stochastically rounded): exact
+    static __device__ __forceinline__ T pack(float a, float b)
+    {
+        return (__float_as_uint(a) >> 16) | (__float_as_uint(b) & 0xffff0000u);
+    }
+};
+// a pair of consecutive frame entries, as stored (the plane and its pitch are
+// 16-byte aligned and p is even)
+template <typename FT> struct XPair;
+template <> struct XPair<uint8_t> {
+    using T = uchar2;
+    static __device__ __forceinline__ T ldg(const uint8_t *p, int nvalid)
+    {
+        if (nvalid == 2) return __ldg(reinterpret_cast<const uchar2 *>(p));
+        return make_uchar2(nvalid > 0 ? __ldg(p) : (uint8_t)0, (uint8_t)0);
+    }
+    static __device__ __forceinline__ float2 wide(T v) { return make_float2((float)v.x, (float)v.y); }
+};
+template <> struct XPair<float> {
+    using T = float2;
+    static __device__ __forceinline__ T ldg(const float *p, int nvalid)
+    {
+        if (nvalid == 2) return __ldg(reinterpret_cast<const float2 *>(p));
+        return make_float2(nvalid > 0 ? __ldg(p) : 0.f, 0.f);
+    }
+    static __device__ __forceinline__ float2 wide(T v) { return v; }
+};
+
+// bytes of dynamic shared memory: ns row slots, the frame entries and labels
+// of npm pixel pairs per channel
+template <int K, typename FT, typename UT>
+__host__ __device__ inline size_t res_smem_bytes(int C, int npm, int ns)
+{
+    return res_al16((size_t)K * ns * sizeof(typename RPair<UT>::T)) +
+           res_al16((size_t)C * npm * sizeof(typename XPair<FT>::T)) + res_al16((size_t)npm * sizeof(uchar2));
+}
+
+template <int K, typename FT, typename UT> struct ResSmem {
+    typename RPair<UT>::T *us; // rows: column j of slot s at us[j ns + s]
+    typename XPair<FT>::T *xs; // frame entries of item i at xs[i]
+    uchar2 *ls;                // labels of pixel pair q at ls[q]
+    int ns;
+    __device__ ResSmem(unsigned char *base, const DevParams &prm, int G, int ns_) : ns(ns_)
+    {
+        const int npm = res_npair_max(prm.P, G);
+        us = reinterpret_cast<typename RPair<UT>::T *>(base);
+        unsigned char *x = base + res_al16((size_t)K * ns * sizeof(typename RPair<UT>::T));
+        xs = reinterpret_cast<typename XPair<FT>::T *>(x);
+        ls = reinterpret_cast<uchar2 *>(x + res_al16((size_t)prm.C * npm * sizeof(typename XPair<FT>::T)));
+    }
+};
+
+// One pass of the resident form over this CTA's items.
+//   MODE 0: a CG pass (cost, U^T eta, |eta|^2, non-finite count, U^T diag(c) U)
+//   MODE 1: the final pass (the same without the matrix)
+//   MODE 2: the explicit projection pass, sum of pi(eta)_e^2 = (eta_e - u_e^T g)^2
+// FILL: the first pass of the frame, which reads everything from global memory
+// and fills the shared-memory copies.
+template <int K, typename FT, typename UT, int MODE, bool FILL, int NA>
+__device__ __forceinline__ void res_pass(const FrameArgs &a, const ResPart &rp, const ResSmem<K, FT, UT> &sm,
+                                         const SKState<K> &sk, float (&acc)[NA])
+{
+    using F = FCfg<K, UT>;
+    using RP = RPair<UT>;
+    using XP = XPair<FT>;
+    constexpr int TP = F::TP, NT = F::THREADS;
+    constexpr int NM = MODE == 0 ? F::NM : 0;
+    static_assert(!(FILL && MODE == 2), "the projection pass is never a frame's first");
+    const DevParams &prm = a.prm;
+    float y[K], tg[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        y[j] = sk.yf[j];
+        tg[j] = MODE == 2 ? sk.tg[j] : 0.f;
+    }
+    const float mu = prm.mu, e = prm.e, pw = prm.p, om = prm.omega;
+    const float sc = prm.in_scale, of = prm.in_offset;
+    const FT *frame = static_cast<const FT *>(a.frame);
+    const UT *U = static_cast<const UT *>(a.U);
+    const int np = rp.npair;
+    int c = 0, q = threadIdx.x;
+    while (q >= np && c < prm.C) {
+        q -= np;
+        ++c;
+    }
+    for (int it = threadIdx.x; it < rp.nitems; it += NT) {
+        const int64_t p = rp.pa + 2 * (int64_t)q;
+        const int nvalid = prm.P - p < 2 ? (int)(prm.P - p) : 2;
+        float u[K][2];
+        if (FILL || it < rp.ng) {
+            const int64_t pt = p / TP;
+            const UT *ub = U + (((int64_t)c * prm.npt + pt) * K) * TP + (p - pt * TP);
+            typename RP::T v[K];
+#pragma unroll
+            for (int j = 0; j < K; ++j) v[j] = RP::ldg(ub + j * TP);
+            if (FILL && it >= rp.ng) {
+#pragma unroll
+                for (int j = 0; j < K; ++j) sm.us[j * sm.ns + (it - rp.ng)] = v[j];
+            }
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const float2 w = RP::wide(v[j]);
+                u[j][0] = w.x;
+                u[j][1] = w.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const float2 w = RP::wide(sm.us[j * sm.ns + (it - rp.ng)]);
+                u[j][0] = w.x;
+                u[j][1] = w.y;
+            }
+        }
+        typename XP::T xr;
+        uchar2 lr;
+        if (FILL) {
+            xr = XP::ldg(frame + (int64_t)c * a.frame_pitch + p, nvalid);
+            lr = __ldg(reinterpret_cast<const uchar2 *>(a.labels + p));
+            sm.xs[it] = xr;
+            if (c == 0) sm.ls[q] = lr;
+        } else {
+            xr = sm.xs[it];
+            lr = sm.ls[q];
+        }
+        const float2 xw = XP::wide(xr);
+        const float xv[2] = {xw.x, xw.y};
+        const float lb[2] = {(float)lr.x, (float)lr.y};
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const bool valid = r < nvalid;
+            float uy = 0.f, ug = 0.f;
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                uy = fmaf(u[j][r], y[j], uy);
+                if (MODE == 2) ug = fmaf(u[j][r], tg[j], ug);
+            }
+            if constexpr (MODE != 2 && sizeof(FT) == 4) {
+                if (valid && !isfinite(xv[r])) acc[K + NM + 2] += 1.f;
+            }
+            const float res = valid ? fmaf(xv[r], sc, -of) - uy : 0.f;
+            const float z = fmaf(res, res, mu);
+            const float tz = __powf(z, e);
+            const float wv = valid ? (lb[r] != 0.f ? om : 1.f) : 0.f;
+            const float cw = wv * tz;
+            const float eta = -pw * cw * res;
+            if constexpr (MODE == 2) {
+                const float pe = valid ? eta - ug : 0.f;
+                acc[0] = fmaf(pe, pe, acc[0]);
+            } else {
+                acc[K + NM] = fmaf(cw, z, acc[K + NM]);
+                acc[K + NM + 1] = fmaf(eta, eta, acc[K + NM + 1]);
+#pragma unroll
+                for (int j = 0; j < K; ++j) acc[j] = fmaf(eta, u[j][r], acc[j]);
+                if constexpr (MODE == 0) {
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        const float cu = cw * u[j][r];
+#pragma unroll
+                        for (int l2 = j; l2 < K; ++l2)
+                            acc[K + tri<K>(j, l2)] = fmaf(cu, u[l2][r], acc[K + tri<K>(j, l2)]);
+                    }
+                }
+            }
+        }
+        q += NT;
+        while (q >= np && c < prm.C) {
+            q -= np;
+            ++c;
+        }
+    }
+}
+
+// The update pass of the resident form: a thread takes a pixel pair and its
+// channels in turn (the label of Step 3 is the maximum over the channels),
+// the old rows from shared memory (or L2 for items [0, ng)), and writes the
+// new rows, the labels and the optional outputs to global memory; per-thread
+// sums of the Gram of the written rows and of the foreground count.
+template <int K, typename FT, typename UT>
+__device__ __forceinline__ void res_update(const FrameArgs &a, const ResPart &rp, const ResSmem<K, FT, UT> &sm,
+                                           const SKState<K> &sk, float (&acc)[FCfg<K, UT>::NPU])
+{
+    using F = FCfg<K, UT>;
+    using RP = RPair<UT>;
+    using XP = XPair<FT>;
+    constexpr int TP = F::TP, NT = F::THREADS, NM = F::NM;
+    const DevParams &prm = a.prm;
+    const float cm1 = sk.cm1, snp = sk.snp, yn = sk.yn;
+    const float mu = prm.mu, e = prm.e, pw = prm.p, om = prm.omega, dl = prm.delta;
+    const float sc = prm.in_scale, of = prm.in_offset;
+    const bool pre = prm.mask_pre != 0;
+    const bool write = !sk.skip;
+    // the k-space vectors are read from shared memory at each use (broadcast
+    // loads) rather than held in registers
+    const volatile float *vy = sk.yf;
+    const volatile float *vv = sk.tv;
+    const volatile float *vg = sk.tg;
+    const volatile float *vw = sk.w;
+    UT *U = static_cast<UT *>(a.U);
+    const int C = prm.C, np = rp.npair;
+    const uint32_t sr_key = pcg_hash(prm.sr_seed ^ pcg_hash((uint32_t)sk.frame_index));
+    for (int q = threadIdx.x; q < np; q += NT) {
+        const int64_t p = rp.pa + 2 * (int64_t)q;
+        const int nvalid = prm.P - p < 2 ? (int)(prm.P - p) : 2;
+        const int64_t pt = p / TP;
+        const int r0 = (int)(p - pt * TP);
+        const uchar2 lr = sm.ls[q];
+        const float wv[2] = {nvalid > 0 ? (lr.x ? om : 1.f) : 0.f, nvalid > 1 ? (lr.y ? om : 1.f) : 0.f};
+        float mx[2] = {0.f, 0.f};
+        for (int c = 0; c < C; ++c) {
+            const int it = c * np + q;
+            UT *ub = U + (((int64_t)c * prm.npt + pt) * K) * TP + r0;
+            float u[K][2];
+            if (it < rp.ng) {
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const float2 w = RP::wide(RP::ldg(ub + j * TP));
+                    u[j][0] = w.x;
+                    u[j][1] = w.y;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const float2 w = RP::wide(sm.us[j * sm.ns + (it - rp.ng)]);
+                    u[j][0] = w.x;
+                    u[j][1] = w.y;
+                }
+            }
+            const float2 xw = XP::wide(sm.xs[it]);
+            const float xv[2] = {xw.x, xw.y};
+            // dots of the orthonormal rows u = T^T u_st through T y, T g, T v
+            float uy[2] = {0.f, 0.f}, ug[2] = {0.f, 0.f}, uv[2] = {0.f, 0.f};
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const float by = vy[j], bg = vg[j], bv = vv[j];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    uy[r] = fmaf(u[j][r], by, uy[r]);
+                    ug[r] = fmaf(u[j][r], bg, ug[r]);
+                    uv[r] = fmaf(u[j][r], bv, uv[r]);
+                }
+            }
+            float gam[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const bool valid = r < nvalid;
+                const float x = fmaf(xv[r], sc, -of);
+                const float res = valid ? x - uy[r] : 0.f;
+                const float z = fmaf(res, res, mu);
+                const float tz = __powf(z, e);
+                const float eta = -pw * wv[r] * tz * res;
+                // u <- u + ((cos(theta) - 1) u^T v - sin(theta) pi(eta)_e / |pi(eta)|) v
+                gam[r] = valid ? fmaf(cm1, uv[r], -snp * (eta - ug[r])) : 0.f;
+                const float rn = pre ? res : fmaf(-gam[r], yn, res);
+                if (valid) {
+                    mx[r] = fmaxf(mx[r], fabsf(rn));
+                    if (write && a.bg_out) a.bg_out[(int64_t)c * prm.P + p + r] = x - rn + of;
+                }
+            }
+            // stored rows of u + gamma v: u_st + gamma R^T v; a bfloat16 row
+            // is rounded stochastically (one hash per stored row, then the
+            // linear congruential step per entry) and its Gram taken of the
+            // stored values
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const float bw = vw[j];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) u[j][r] = fmaf(gam[r], bw, u[j][r]);
+            }
+            if constexpr (sizeof(UT) == 2) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    uint32_t rk = pcg_hash(sr_key ^ (uint32_t)(c * prm.Pp + p + r));
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        rk = rk * 1664525u + 1013904223u;
+                        u[j][r] = round_bf16_sr(u[j][r], rk >> 16);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+#pragma unroll
+                    for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[j][r], u[l2][r], acc[tri<K>(j, l2)]);
+            if (write) {
+#pragma unroll
+                for (int j = 0; j < K; ++j)
+                    *reinterpret_cast<typename RP::T *>(ub + j * TP) = RP::pack(u[j][0], u[j][1]);
+            }
+        }
+        const uint8_t nl0 = (nvalid > 0 && mx[0] >= dl) ? 1 : 0;
+        const uint8_t nl1 = (nvalid > 1 && mx[1] >= dl) ? 1 : 0;
+        acc[NM] += (float)(nl0 + nl1);
+        if (write) {
+            *reinterpret_cast<uchar2 *>(a.labels + p) = make_uchar2(nl0, nl1);
+            if (a.mask_out) {
+                if (nvalid > 0) a.mask_out[p] = nl0;
+                if (nvalid > 1) a.mask_out[p + 1] = nl1;
+            }
+        }
+    }
+}
+
 // The frame of one stream, by CTA b of the G CTAs working on it.
 // CL: the cluster form (the whole grid is one thread-block cluster, its
 // barriers are the hardware cluster barrier, CTA 0 ends the frame); else the
 // grid form (cooperative launch, bounded grid barriers, the last CTA to
-// arrive ends the frame).
-template <int K, typename FT, typename UT, bool CL = false>
+// arrive ends the frame).  RES: the resident form of the grid form (k <= 10),
+// rows, frame entries and labels kept in shared memory across the passes.
+template <int K, typename FT, typename UT, bool CL = false, bool RES = false>
 __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, const int b)
 {
     using F = FCfg<K, UT>;
@@ -1021,9 +1373,14 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     __shared__ float sred[NW * F::NPMAX];
     __shared__ float tot[F::NVR > F::NVU ? F::NVR : F::NVU];
     __shared__ float rscr[RED_SCR];
-    __shared__ ReorthScratch<K> rs;
     __shared__ SKState<K> sk;
-    extern __shared__ __align__(128) float stage_smem[]; // streaming form only
+    extern __shared__ __align__(128) float stage_smem[]; // streaming and resident forms only
+    static_assert(!(RES && (F::STREAM || CL)), "the resident form is a grid form of the register form");
+    // the end-of-frame scratch: in the resident form it takes the start of the
+    // dynamic shared memory, whose rows are dead once the update pass is done
+    __shared__ typename std::conditional<RES, char, ReorthScratch<K>>::type rs_slot;
+    ReorthScratch<K> &rs = *reinterpret_cast<ReorthScratch<K> *>(RES ? static_cast<void *>(stage_smem)
+                                                                          : static_cast<void *>(&rs_slot));
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const DevParams &prm = a.prm;
@@ -1047,7 +1404,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     for (int i = tid; i < K * K; i += NT) {
         sk.Tf[i] = a.ks->Tf[i];
         sk.Rf[i] = (float)a.ks->R[(i / K) * KMAX + (i % K)];
-        rs.Told[i] = a.ks->T[(i / K) * KMAX + (i % K)];
+        if constexpr (!RES) rs.Told[i] = a.ks->T[(i / K) * KMAX + (i % K)];
     }
     if (tid < K) {
         sk.y[tid] = a.ks->y[tid];
@@ -1068,6 +1425,8 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     unsigned char *const sbase = reinterpret_cast<unsigned char *>(stage_smem);
     unsigned char *wstage = sbase + (size_t)warp * SC::WARP_B;
     constexpr int RES_OFF = SC::D * SC::STAGE_B + SC::RES_B; // a warp's tensor-core result
+    const ResPart rpart(prm, G, b, a.res_ns);
+    const ResSmem<K, FT, UT> rsm(sbase, prm, G, a.res_ns);
     int buf = 0;
     unsigned long long target = a.bar_base;
     if (stats && tid == 0) a.ks->phase_ts[0] = global_ns();
@@ -1082,7 +1441,12 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             float acc[F::NPR];
 #pragma unroll
             for (int i = 0; i < F::NPR; ++i) acc[i] = 0.f;
-            if constexpr (F::STREAM)
+            if constexpr (RES) {
+                if (pass == 0)
+                    res_pass<K, FT, UT, 0, true>(a, rpart, rsm, sk, acc);
+                else
+                    res_pass<K, FT, UT, 0, false>(a, rpart, rsm, sk, acc);
+            } else if constexpr (F::STREAM)
                 stream_residual<K, FT, UT, true, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
             else
                 residual_pass<K, FT, UT, true>(a, tl, sk, acc, 0);
@@ -1108,7 +1472,12 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             float acc[F::NPF];
 #pragma unroll
             for (int i = 0; i < F::NPF; ++i) acc[i] = 0.f;
-            if constexpr (F::STREAM)
+            if constexpr (RES) {
+                if (pass == 0)
+                    res_pass<K, FT, UT, 1, true>(a, rpart, rsm, sk, acc);
+                else
+                    res_pass<K, FT, UT, 1, false>(a, rpart, rsm, sk, acc);
+            } else if constexpr (F::STREAM)
                 stream_residual<K, FT, UT, false, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
             else
                 residual_pass<K, FT, UT, false>(a, tl, sk, acc, 0);
@@ -1133,7 +1502,9 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         const float *pcols = a.partials + (size_t)buf * F::NVR * a.col_stride;
         target += (unsigned long long)G;
         float acc1[1] = {0.f};
-        if constexpr (F::STREAM)
+        if constexpr (RES)
+            res_pass<K, FT, UT, 2, false>(a, rpart, rsm, sk, acc1);
+        else if constexpr (F::STREAM)
             stream_residual<K, FT, UT, false, NW, 1, true>(a, tl.r0, tl.nres, sk.yf, wstage, acc1, sk.tg);
         else
             proj_pass<K, FT, UT>(a, tl, sk, acc1[0]);
@@ -1169,6 +1540,13 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         } else {
             cons_partials_tree<F::NVU, NW>(acc, F::NVU, ucol, sred, a.col_stride);
         }
+    } else if constexpr (RES) {
+        float acc[F::NPU];
+#pragma unroll
+        for (int i = 0; i < F::NPU; ++i) acc[i] = 0.f;
+        res_update<K, FT, UT>(a, rpart, rsm, sk, acc);
+        if (tid == 0 && stats) a.ks->sub_ts[5] = global_ns();
+        cons_partials<F::NPU, NW>(acc, F::NVU, ucol, sred, a.col_stride);
     } else {
     float acc[F::NPU];
 #pragma unroll
@@ -1304,6 +1682,10 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     cons_sync<NT>();
     if (tid == 0 && stats) a.ks->sub_ts[7] = global_ns();
     if (!sk.last) return;
+    if constexpr (RES) {
+        // every CTA's update pass is done: the dynamic shared memory is free
+        for (int i = tid; i < K * K; i += NT) rs.Told[i] = a.ks->T[(i / K) * KMAX + (i % K)];
+    }
     reduce_cols<NT>(ucols, G, a.col_stride, F::NVU, tot, rscr);
     if (tid == 0) a.ks->sub_ts[8] = global_ns();
     end_frame<K, NT>(sk, a.ks, tot, tot[NM], rs, a.status_out);
@@ -1323,6 +1705,13 @@ template <int K, typename FT, typename UT>
 __global__ void __launch_bounds__(FCfg<K, UT>::THREADS, 1) k_frame_cluster(const FrameArgs a)
 {
     frame_body<K, FT, UT, true>(a, (int)gridDim.x, (int)blockIdx.x);
+}
+
+// One stream: the whole grid, in the resident form (k <= 10).
+template <int K, typename FT, typename UT>
+__global__ void __launch_bounds__(FCfg<K, UT>::THREADS, 1) k_frame_res(const FrameArgs a)
+{
+    if constexpr (!FCfg<K, UT>::STREAM) frame_body<K, FT, UT, false, true>(a, (int)gridDim.x, (int)blockIdx.x);
 }
 
 // Several streams of one kernel family in one cooperative launch: each CTA
@@ -1440,6 +1829,62 @@ template <int K, typename UT> struct FrameOps {
     }
     // resident CTAs per SM (0: the kernel cannot run)
     static int prepare(int fdt) { return fdt == 0 ? prepare_t<uint8_t>() : prepare_t<float>(); }
+    // the resident form's plan on the current device: the largest dynamic
+    // shared memory its CTA can take (the opt-in limit less its static shared
+    // memory), then as many row slots as fit beside the frame entries and
+    // labels of the CTA with the most pixels
+    template <typename FT> static int res_plan_t(int64_t P, int C, int grid, int *ns, int *smem)
+    {
+        if constexpr (F::STREAM) {
+            return 0;
+        } else {
+            int dev = 0, optin = 0, n = 0;
+            cudaFuncAttributes fa;
+            if (cudaGetDevice(&dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+                cudaFuncGetAttributes(&fa, k_frame_res<K, FT, UT>) != cudaSuccess)
+                return 0;
+            const int64_t cap = ((int64_t)optin - (int64_t)fa.sharedSizeBytes) & ~(int64_t)15;
+            const int npm = res_npair_max(P, grid);
+            const int64_t nim = (int64_t)C * npm;
+            const int64_t fixed = (int64_t)res_smem_bytes<K, FT, UT>(C, npm, 0);
+            const int64_t slot = (int64_t)K * sizeof(typename RPair<UT>::T);
+            if (cap <= fixed) return 0;
+            int64_t nsl = (cap - fixed) / slot;
+            if (nsl > nim) nsl = nim;
+            int64_t bytes = (int64_t)res_smem_bytes<K, FT, UT>(C, npm, (int)nsl);
+            if (bytes < (int64_t)res_al16(sizeof(ReorthScratch<K>))) bytes = (int64_t)res_al16(sizeof(ReorthScratch<K>));
+            if (bytes > cap) return 0;
+            // the attribute is the largest size any handle asks for: always the cap
+            if (cudaFuncSetAttribute(k_frame_res<K, FT, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)cap) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_frame_res<K, FT, UT>, F::THREADS, (int)bytes) !=
+                    cudaSuccess ||
+                n < 1)
+                return 0;
+            *ns = (int)nsl;
+            *smem = (int)bytes;
+            return 1;
+        }
+    }
+    static int res_plan(int fdt, int64_t P, int C, int grid, int *ns, int *smem)
+    {
+        return fdt == 0 ? res_plan_t<uint8_t>(P, C, grid, ns, smem) : res_plan_t<float>(P, C, grid, ns, smem);
+    }
+    template <typename FT> static cudaError_t res_t(const FrameArgs &a, int grid, int smem, cudaStream_t s)
+    {
+        if constexpr (F::STREAM) {
+            return cudaErrorInvalidValue;
+        } else {
+            void *args[] = {const_cast<FrameArgs *>(&a)};
+            return cudaLaunchCooperativeKernel((void *)k_frame_res<K, FT, UT>, dim3(grid), dim3(F::THREADS), args,
+                                               smem, s);
+        }
+    }
+    static cudaError_t frame_res(const FrameArgs &a, int fdt, int grid, int smem, cudaStream_t s)
+    {
+        return fdt == 0 ? res_t<uint8_t>(a, grid, smem, s) : res_t<float>(a, grid, smem, s);
+    }
 };
 
 template <int K, typename UT> const KernelOps *kernel_table()
@@ -1448,7 +1893,9 @@ template <int K, typename UT> const KernelOps *kernel_table()
                                   &FrameOps<K, UT>::cluster, &FrameOps<K, UT>::cluster_fit,
                                   &Ops<K, UT>::gram,
                                   &Ops<K, UT>::export_u, &Ops<K, UT>::gram_occupancy, &Ops<K, UT>::rebase,
-                                  Cfg<K>::VW, FCfg<K, UT>::TP, FCfg<K, UT>::THREADS};
+                                  Cfg<K>::VW, FCfg<K, UT>::TP, FCfg<K, UT>::THREADS,
+                                  FCfg<K, UT>::STREAM ? nullptr : &FrameOps<K, UT>::res_plan,
+                                  FCfg<K, UT>::STREAM ? nullptr : &FrameOps<K, UT>::frame_res};
     return &ops;
 }
 

@@ -22,7 +22,7 @@ PROST_EBADFRAME, PROST_ETIMEOUT, PROST_ENOTSPD = -4, -5, -6
 PROST_U8, PROST_F32, PROST_BF16 = 0, 1, 2
 PROST_MASK_POST_UPDATE, PROST_MASK_PRE_UPDATE = 0, 1
 PROST_MAX_K, PROST_MAX_K_SINGLE, PROST_STATIC_MAX_K, PROST_MAX_CG = 32, 16, 16, 32
-PROST_FORM_AUTO, PROST_FORM_GRID, PROST_FORM_CLUSTER, PROST_FORM_PASSES = 0, 1, 2, 3
+PROST_FORM_AUTO, PROST_FORM_GRID, PROST_FORM_CLUSTER, PROST_FORM_PASSES, PROST_FORM_RESIDENT = 0, 1, 2, 3, 4
 PROST_CLUSTER_MAX_U_BYTES = 1 << 20
 
 HEADER = os.path.join(_build.INCLUDE, "prost.h")

@@ -106,8 +106,8 @@ int main(void)
     prm.k = 0;
     check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "k = 0 rejected");
     prm = valid_params();
-    prm.form = 4;
-    check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "form beyond the four forms");
+    prm.form = PROST_FORM_RESIDENT + 1;
+    check(prost_state_bytes(&prm, &bytes) == PROST_EINVAL, "form beyond the five forms");
     prm = valid_params();
     prm.k = PROST_MAX_K;
     check(prost_state_bytes(&prm, &bytes) == PROST_OK, "k = 32 in the passes form");

@@ -48,6 +48,8 @@ def test_state_bytes_of_valid_parameters():
     # k above the single-launch forms: the passes form only, float32 storage only
     dict(k=17, form=1), dict(k=20, form=2), dict(k=32, u_dtype="bf16"),
     dict(k=10, form=3, u_dtype="bf16"),
+    # the resident form serves the register form's k only
+    dict(k=11, form=4), dict(k=16, form=4),
 ])
 def test_parameter_validation(bad):
     prm = dict(_ok())
@@ -57,14 +59,15 @@ def test_parameter_validation(bad):
     assert ei.value.code == pg.PROST_EINVAL
 
 
-def test_form_field_takes_the_four_forms_only():
-    for form in (pg.PROST_FORM_AUTO, pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER, pg.PROST_FORM_PASSES):
-        p = pg.make_params(**_ok(), form=form)
+def test_form_field_takes_the_five_forms_only():
+    for form in (pg.PROST_FORM_AUTO, pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER, pg.PROST_FORM_PASSES,
+                 pg.PROST_FORM_RESIDENT):
+        p = pg.make_params(**dict(_ok(), k=min(_ok()["k"], 10)), form=form)
         assert pg.prost_state_bytes(p) > 0
     for k in (17, 32):
         for form in (pg.PROST_FORM_AUTO, pg.PROST_FORM_PASSES):
             assert pg.prost_state_bytes(pg.make_params(**dict(_ok(), k=k), form=form)) > 0
-    for form in (-1, 4):
+    for form in (-1, 5):
         p = pg.make_params(**_ok())
         p.form = form
         with pytest.raises(pg.ProstError):

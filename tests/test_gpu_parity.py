@@ -51,7 +51,12 @@ def _run_case(wp, vid, frames, device=True, seed=11, **gover):
     return errs
 
 
-FORMS = [pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER, pg.PROST_FORM_PASSES]
+FORMS = [pg.PROST_FORM_GRID, pg.PROST_FORM_CLUSTER, pg.PROST_FORM_PASSES, pg.PROST_FORM_RESIDENT]
+
+
+def _skip_unavailable(form, k):
+    if form == pg.PROST_FORM_RESIDENT and k > 10:
+        pytest.skip("the resident form serves k <= 10")
 
 
 @pytest.mark.parametrize("form", FORMS)
@@ -92,6 +97,7 @@ def test_rgb_64x48_k10_host_buffers_and_pre_update_labels():
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("k", [1, 2, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16])
 def test_subspace_dimensions(k, form):
+    _skip_unavailable(form, k)
     vid = synth.SyntheticVideo(50, 40, 1, k, n_frames=4, fg_fraction=0.05, seed=100 + k, dtype="f32")
     wp = synth.video._params(vid.m, k, "f32")
     wp.update(width=50, height=40, channels=1, frame_dtype="f32")
@@ -128,10 +134,13 @@ def test_stats_report_the_step_size_rule():
 
 
 def test_the_automatic_form_follows_the_subspace_size():
-    # cluster form up to PROST_CLUSTER_MAX_U_BYTES of stored subspace, grid form above
+    # cluster form up to PROST_CLUSTER_MAX_U_BYTES of stored subspace; above
+    # it the resident form for k <= 10 when at least half of a CTA's rows fit
+    # its shared memory, else the grid form
     for name, over, want in (("gray160x120_k5", {}, pg.PROST_FORM_CLUSTER),
                              ("rgb640x480_k10", {"width": 160, "height": 120, "k": 15}, pg.PROST_FORM_GRID),
-                             ("rgb640x480_k10", {}, pg.PROST_FORM_GRID)):
+                             ("rgb640x480_k10", {}, pg.PROST_FORM_RESIDENT),
+                             ("rgb640x480_k10", {"width": 1920, "height": 1080}, pg.PROST_FORM_GRID)):
         vid, wp = synth.make_workload(name, n_frames=1, **over)
         assert (vid.m * vid.k * 4 <= pg.PROST_CLUSTER_MAX_U_BYTES) == (want == pg.PROST_FORM_CLUSTER)
         h = pg.prost_init(gpu_params(wp))
@@ -144,13 +153,28 @@ def test_the_automatic_form_follows_the_subspace_size():
             pg.prost_destroy(h)
 
 
-def test_full_size_640x480_rgb_k10_in_the_benchmark_configuration():
+@pytest.mark.parametrize("form", [pg.PROST_FORM_AUTO, pg.PROST_FORM_GRID])
+def test_full_size_640x480_rgb_k10_in_the_benchmark_configuration(form):
     """The benchmarked workload (640x480 RGB, k = 10, uint8 frames in device
     memory, one prost_step per frame): teacher-forced parity of every output,
-    element by element, at frames 0 and 1 of an oracle trajectory."""
+    element by element, at frames 0 and 1 of an oracle trajectory.  AUTO runs
+    the resident form, whose CTAs hold about 86 % of their rows in shared
+    memory and stream the rest from L2 in every pass."""
     vid, wp = synth.make_workload("rgb640x480_k10", n_frames=3)
-    errs = _run_case(wp, vid, [0, 1])
+    errs = _run_case(wp, vid, [0, 1], form=form)
     print(errs)
+
+
+@pytest.mark.parametrize("w,h,c", [(1280, 720, 1), (1920, 1080, 3)])
+def test_resident_form_with_rows_beyond_shared_memory(w, h, c):
+    """The resident form where a CTA's rows do not all fit its shared memory:
+    1280x720 gray (about 84 % resident, one round of L2 items per thread) and
+    1080p RGB forced (about 4 % resident: the L2 items take many rounds)."""
+    vid = synth.SyntheticVideo(w, h, c, 10, n_frames=2, fg_fraction=0.08, shape="ellipse", jitter=2,
+                               seed=900 + c, dtype="u8")
+    wp = synth.video._params(vid.m, vid.k, "u8")
+    wp.update(width=w, height=h, channels=c, frame_dtype="u8")
+    _run_case(wp, vid, [0, 1], form=pg.PROST_FORM_RESIDENT)
 
 
 def _principal_angle_max(A, B):

@@ -46,7 +46,8 @@ SMS = 152
 
 # the rules restated below, as they read in the sources
 assert "static constexpr int THREADS = STREAM && sizeof(UT) == 4 ? 256 : 512;" in FRAME_CUH
-assert "static constexpr bool STREAM = K >= 11;" in FRAME_CUH
+KREG = _const(DEVICE_H, r"constexpr int KREG = (\d+);")
+assert KREG == 10 and "static constexpr bool STREAM = K > KREG;" in FRAME_CUH
 assert "return (size_t)k + (size_t)k * (k + 1) / 2 + 3;" in API_CU
 assert "r0 = (int)(NT * b / G);" in FRAME_CUH and "u0 = (int)((long long)prm.npt * b / G);" in FRAME_CUH
 
@@ -587,3 +588,109 @@ def test_window_dy_tiles_cover_every_entry_inside_the_scratch(k):
                 if j < k and t < n:
                     seen[j, t] += 1
         assert np.all(seen == 1)
+
+
+# ---- the resident form (k <= KREG): pixel units, item slots, shared memory ----
+
+RES_UNIT = _const(DEVICE_H, r"constexpr int RES_UNIT = (\d+);")
+assert "return (P + RES_UNIT - 1) / RES_UNIT;" in DEVICE_H
+assert "return (int)((res_units(P) + G - 1) / G) * (RES_UNIT / 2);" in DEVICE_H
+assert "const int64_t lo = nu * b / G, hi = nu * (b + 1) / G;" in FRAME_CUH
+assert "ng = nitems > ns ? nitems - ns : 0;" in FRAME_CUH
+assert "if (g > res_units(dp.P)) g = res_units(dp.P);" in API_CU
+# the partial-row buffers serve whichever of the grid and resident grids is larger
+assert "(size_t)2 * col_stride(std::max(h->grid_frame, h->grid_res)) *" in API_CU
+
+
+def res_units(P):
+    return (P + RES_UNIT - 1) // RES_UNIT
+
+
+def res_npair_max(P, G):
+    return -(-res_units(P) // G) * (RES_UNIT // 2)
+
+
+def al16(b):
+    return (b + 15) // 16 * 16
+
+
+def res_part(P, C, G, b, ns):
+    nu = res_units(P)
+    lo, hi = nu * b // G, nu * (b + 1) // G
+    pa = lo * RES_UNIT
+    pb = min(hi * RES_UNIT, P)
+    npair = (max(pb - pa, 0) + 1) // 2
+    nitems = C * npair
+    return pa, npair, nitems, max(nitems - ns, 0)
+
+
+def res_plan(P, C, k, usz, fsz, cap):
+    """Grid, row slots and dynamic shared memory as FrameOps::res_plan_t sizes them."""
+    G = min(SMS, res_units(P), RED_SCR // partial_row(k) * RED_ROWS)
+    npm = res_npair_max(P, G)
+    fixed = al16(C * npm * 2 * fsz) + al16(npm * 2)
+    if cap <= fixed:
+        return None
+    ns = min(C * npm, (cap - fixed) // (k * 2 * usz))
+    smem = al16(k * ns * 2 * usz) + fixed
+    assert smem <= cap
+    return G, ns, npm, smem
+
+
+RES_CASES = [(P, C) for P in (1, 2, 63, 64, 65, 1073, 2000, 19200, 76800, 307200, 921600, 2073600)
+             for C in (1, 3)]
+
+
+@pytest.mark.parametrize("P,C", RES_CASES)
+@pytest.mark.parametrize("k,usz,fsz", [(10, 4, 1), (10, 4, 4), (10, 2, 1), (5, 4, 4), (1, 4, 1)])
+@pytest.mark.parametrize("cap", [219648, 40000])
+def test_resident_plan_covers_every_entry_once_inside_its_buffers(P, C, k, usz, fsz, cap):
+    plan = res_plan(P, C, k, usz, fsz, cap)
+    if plan is None:
+        return
+    G, ns, npm, smem = plan
+    npt = npt_of(P)
+    Pp = npt * TILE_P
+    seen = np.zeros((C, P), dtype=np.int32)
+    nt = threads(k, usz == 2)
+    for b in range(G):
+        pa, npair, nitems, ng = res_part(P, C, G, b, ns)
+        assert npair <= npm and nitems <= C * npm
+        if nitems == 0:
+            continue
+        assert pa % 2 == 0
+        it = np.arange(nitems)
+        c, q = it // npair, it % npair
+        p = pa + 2 * q
+        nvalid = np.minimum(2, P - p)
+        assert (nvalid >= 1).all()
+        np.add.at(seen, (c, p), 1)
+        two = nvalid == 2
+        np.add.at(seen, (c[two], p[two] + 1), 1)
+        # global row pairs: 8 (float32) or 4 (bfloat16) bytes at an even entry of a tile column
+        pt = p // TILE_P
+        r = p - pt * TILE_P
+        base = (c * npt + pt) * k * TILE_P + r
+        assert (r % 2 == 0).all() and (r + 1 < TILE_P).all()
+        assert (base + (k - 1) * TILE_P + 1 < C * npt * k * TILE_P).all()
+        # frame pairs (16-byte aligned planes, pitch P or Pp) and label pairs
+        assert (p + 1 < Pp).all() and (p[two] + 1 < P).all()
+        # shared memory: slots of items [ng, nitems), frame entries of every item,
+        # labels of every pair; each region inside the dynamic allocation
+        s = it[it >= ng] - ng
+        assert (s < ns).all()
+        assert al16(k * ns * 2 * usz) + al16(C * npm * 2 * fsz) + npm * 2 <= smem
+        assert it.max() < C * npm and q.max() < npm
+        # each thread's incremental (c, q) walk lands on item c npair + q
+        for t in range(min(nt, nitems)):
+            cc, qq = 0, t
+            while qq >= npair and cc < C:
+                qq -= npair
+                cc += 1
+            for i in range(t, nitems, nt):
+                assert i == cc * npair + qq
+                qq += nt
+                while qq >= npair and cc < C:
+                    qq -= npair
+                    cc += 1
+    assert (seen == 1).all()

@@ -53,10 +53,10 @@ def _grid_size(h):
     raise AssertionError("no detectable skew found")
 
 
-def _pair(wp, frames, n_before):
-    # the grid form: the cluster form has no software barrier to disturb
-    a = pg.prost_init(gpu_params(wp, seed=3, form=pg.PROST_FORM_GRID))
-    b = pg.prost_init(gpu_params(wp, seed=3, form=pg.PROST_FORM_GRID))
+def _pair(wp, frames, n_before, form=pg.PROST_FORM_GRID):
+    # the grid or resident form: the cluster form has no software barrier to disturb
+    a = pg.prost_init(gpu_params(wp, seed=3, form=form))
+    b = pg.prost_init(gpu_params(wp, seed=3, form=form))
     mask = torch.empty(frames[0].numel() // wp["channels"], dtype=torch.uint8, device="cuda")
     for h in (a, b):
         for t in range(n_before):
@@ -90,11 +90,12 @@ def _inject(kind, h):
         raise ValueError(kind)
 
 
+@pytest.mark.parametrize("form", [pg.PROST_FORM_GRID, pg.PROST_FORM_RESIDENT])
 @pytest.mark.parametrize("kind", ["skew_forward", "skew_backward", "skew_grid", "stall0", "stall2", "stall5"])
-def test_fault_is_refused_reported_and_recovered(kind):
+def test_fault_is_refused_reported_and_recovered(kind, form):
     vid, wp = synth.make_workload("gray160x120_k5", n_frames=4)
     frames = [torch.from_numpy(vid.frame(t)[0]).cuda() for t in range(4)]
-    a, b, mask = _pair(wp, frames, 2)
+    a, b, mask = _pair(wp, frames, 2, form)
     try:
         U0, y0 = _export(a, vid)
         frames_before = pg.prost_get_stats(a).frames
