@@ -185,6 +185,26 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out);
 int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_out,
                float *background_out);
 
+/* Process n consecutive frames of the stream (Steps 1-3 of Section 3.3 for
+ * each in turn, the same results as n calls of prost_step()).  frames: n
+ * frames of m entries each, one after another; masks_out (nullable): n * P
+ * bytes, frame i's labels at i * P.  No background output.  In the resident
+ * form the frames of each rebase period run in one launch, whose CTAs keep
+ * their rows and labels in shared memory from one frame to the next, so only
+ * the first frame of the launch reads the subspace from global memory; the
+ * other forms make one launch per frame.  on_device = 1: device pointers,
+ * enqueue only (PROST_OK; device-detected errors by prost_sync()); frames
+ * whose planes do not start on 16-byte boundaries are first copied to a
+ * staging buffer that the handle allocates on first use and keeps.
+ * on_device = 0: host pointers, copied through that buffer; returns the last
+ * frame's status after the stream synchronised, with the masks copied back
+ * only when it completed (PROST_OK, PROST_ENOTSPD); a rejected frame before it
+ * (PROST_EBADFRAME) is reported by prost_sync().  A wait that runs out aborts
+ * the rest of the launch (PROST_ETIMEOUT, masks of the aborted frames
+ * unwritten).  Errors: PROST_EINVAL (NULL handle or frames, n < 1, frames of
+ * prost_step_async() in flight), PROST_ENOMEM, PROST_ECUDA. */
+int prost_step_many(prost_handle *h, const void *frames, int32_t n, int on_device, uint8_t *masks_out);
+
 /* Pipelined host frames (not in the paper).  prost_step_async() enqueues one
  * frame from host memory and returns without waiting: the frame is copied in
  * on a copy stream of the handle while the previous frame's kernel runs, the

@@ -37,6 +37,10 @@ struct prost_handle {
     uint32_t steps_since_rebase; // frame launches since the stored rows were last rebased
     unsigned long long bar_base; // bar->count before the next launch
     void *frame_buf;       // staging of host or unaligned frames (planes Pp entries apart)
+    void *many_buf;        // prost_step_many: staging of its frames (grown on demand)
+    size_t many_bytes;
+    uint8_t *many_mask;    // prost_step_many: device masks of host calls (grown on demand)
+    size_t many_mask_bytes;
     float *bg_buf;         // staging of the background for host outputs
     float *u_buf;          // staging of subspaces crossing the ABI from/to host memory
     int32_t *h_word;       // pinned scratch for small device -> host reads
@@ -196,6 +200,8 @@ void free_state(prost_handle *h)
     if (h->frame_buf) cudaFree(h->frame_buf);
     if (h->bg_buf) cudaFree(h->bg_buf);
     if (h->u_buf) cudaFree(h->u_buf);
+    if (h->many_buf) cudaFree(h->many_buf);
+    if (h->many_mask) cudaFree(h->many_mask);
     if (h->h_word) cudaFreeHost(h->h_word);
     for (int i = 0; i < 2; ++i) {
         if (h->af_buf[i]) cudaFree(h->af_buf[i]);
@@ -217,6 +223,7 @@ void free_state(prost_handle *h)
     for (int i = 0; i < CGMAX + 3; ++i) h->ev[i] = nullptr;
     h->U = nullptr; h->labels = nullptr; h->ks = nullptr; h->partials = nullptr;
     h->counter = nullptr; h->frame_buf = nullptr; h->bg_buf = nullptr; h->u_buf = nullptr;
+    h->many_buf = nullptr; h->many_bytes = 0; h->many_mask = nullptr; h->many_mask_bytes = 0;
     h->h_word = nullptr; h->bar = nullptr;
 }
 
@@ -319,6 +326,7 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     h->stream = (cudaStream_t)stream;
     h->U = nullptr; h->labels = nullptr; h->ks = nullptr; h->partials = nullptr;
     h->counter = nullptr; h->frame_buf = nullptr; h->bg_buf = nullptr; h->u_buf = nullptr;
+    h->many_buf = nullptr; h->many_bytes = 0; h->many_mask = nullptr; h->many_mask_bytes = 0;
     h->h_word = nullptr; h->bar = nullptr; h->bar_base = 0;
     h->steps_since_rebase = 0;
     h->stall_at = 0;
@@ -399,8 +407,10 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     }
     // the Gram kernel's rows, or the frame kernel's two value-major buffers
     h->partial_floats = std::max((size_t)h->grid_gram * partial_row(prm->k),
-                                 (size_t)2 * col_stride(std::max(h->grid_frame, h->grid_res)) *
-                                     partial_row(prm->k));
+                                 (size_t)2 * col_stride(h->grid_frame) * partial_row(prm->k));
+    // the resident form keeps RES_NREP copies of every pass's partial values
+    h->partial_floats = std::max(h->partial_floats,
+                                 (size_t)2 * RES_NREP * col_stride(h->grid_res) * partial_row(prm->k));
     if (wide) h->partial_floats = wide_partial_floats(dp, h->num_sms);
 
     CKI(cudaMalloc(&h->U, (size_t)prm->k * dp.C * dp.Pp * u_elem_bytes(dp)));
@@ -436,8 +446,11 @@ namespace {
 
 // Enqueue one frame launch on the handle's stream (and the periodic rebase):
 // frame planes at fptr, `pitch` entries apart; outputs and status optional.
+// nframes > 1 (resident form only): that many frames of the stream in one
+// launch, `stride` entries apart, their masks P bytes apart; the caller keeps
+// the run inside one rebase period.
 int launch_frame(prost_handle *h, const void *fptr, int64_t pitch, uint8_t *mask_dev, float *bg_dev,
-                 int32_t *status_dev)
+                 int32_t *status_dev, int nframes = 1, int64_t stride = 0)
 {
     FrameArgs fa;
     memset(&fa, 0, sizeof(fa));
@@ -461,6 +474,8 @@ int launch_frame(prost_handle *h, const void *fptr, int64_t pitch, uint8_t *mask
     fa.status_out = status_dev;
     fa.counter = h->counter;
     fa.res_ns = h->res_ns;
+    fa.nframes = nframes;
+    fa.frame_stride = stride;
     h->stall_at = 0; // one launch only
     fa.prm = h->dp;
     if (h->timing) CK(h, cudaEventRecord(h->ev[0], h->stream));
@@ -475,13 +490,16 @@ int launch_frame(prost_handle *h, const void *fptr, int64_t pitch, uint8_t *mask
         h->timed_frames += 1;
     }
     // the grid barrier's arrivals (the cluster form does not use it)
-    if (!cl && !h->wide) h->bar_base += (unsigned long long)grid * (unsigned long long)frame_arrivals(h->prm.n_cg);
+    if (!cl && !h->wide)
+        h->bar_base += (unsigned long long)nframes * (unsigned long long)grid *
+                       (unsigned long long)frame_arrivals(h->prm.n_cg);
     // The frame kernel updates the stored rows in the stored basis (U = U_st T);
     // every REBASE_EVERY frames the stored rows are moved onto the orthonormal
     // representative so that the conditioning of U_st cannot drift.  The
     // device counts the frames that completed, and the rebase runs only when
     // that count is due, so a refused frame does not shift the rebase.
-    if (++h->steps_since_rebase >= REBASE_EVERY) {
+    h->steps_since_rebase += (uint32_t)nframes;
+    if (h->steps_since_rebase >= REBASE_EVERY) {
         const int rc = rebase(h, 0);
         if (rc) return rc;
         h->steps_since_rebase = 0;
@@ -537,6 +555,78 @@ int prost_step(prost_handle *h, const void *frame, int on_device, uint8_t *mask_
         CK(h, cudaMemcpyAsync(background_out, h->bg_buf, (size_t)m * sizeof(float),
                               cudaMemcpyDeviceToHost, h->stream));
     if (mask_out || background_out) CK(h, cudaStreamSynchronize(h->stream));
+    return st;
+}
+
+int prost_step_many(prost_handle *h, const void *frames, int32_t n, int on_device, uint8_t *masks_out)
+{
+    if (!h) return PROST_EINVAL;
+    if (!frames) return fail(h, PROST_EINVAL, "frames is NULL");
+    if (n < 1) return fail(h, PROST_EINVAL, "n must be at least 1");
+    if (h->a_count > 0) return fail(h, PROST_EINVAL, "prost_step_many with frames of prost_step_async in flight");
+    DeviceGuard dg(h->device);
+    const DevParams &dp = h->dp;
+    const size_t eb = frame_elem_bytes(h->prm);
+    const size_t fbytes = (size_t)dp.C * dp.P * eb; // one frame as the caller lays it out
+    if (h->grid_res == 0) {
+        // the other forms: one launch per frame
+        for (int32_t i = 0; i < n; ++i) {
+            const int rc = prost_step(h, static_cast<const char *>(frames) + (size_t)i * fbytes, on_device,
+                                      masks_out ? masks_out + (size_t)i * dp.P : nullptr, nullptr);
+            if (rc) return rc;
+        }
+        return PROST_OK;
+    }
+    // the resident form: the frames of each rebase period in one launch
+    const void *fptr = frames;
+    int64_t pitch = dp.P, stride = (int64_t)dp.C * dp.P;
+    const bool direct = on_device && ((uintptr_t)frames % 16) == 0 && ((size_t)dp.P * eb) % 16 == 0;
+    if (!direct) {
+        const size_t need = (size_t)n * dp.C * dp.Pp * eb;
+        if (need > h->many_bytes) {
+            if (h->many_buf) CK(h, cudaFree(h->many_buf));
+            h->many_buf = nullptr;
+            h->many_bytes = 0;
+            CK(h, cudaMalloc(&h->many_buf, need));
+            h->many_bytes = need;
+        }
+        CK(h, cudaMemcpy2DAsync(h->many_buf, (size_t)dp.Pp * eb, frames, (size_t)dp.P * eb, (size_t)dp.P * eb,
+                                (size_t)n * dp.C, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                h->stream));
+        fptr = h->many_buf;
+        pitch = dp.Pp;
+        stride = (int64_t)dp.C * dp.Pp;
+    }
+    uint8_t *mdev = on_device ? masks_out : nullptr;
+    if (!on_device && masks_out) {
+        const size_t need = (size_t)n * dp.P;
+        if (need > h->many_mask_bytes) {
+            if (h->many_mask) CK(h, cudaFree(h->many_mask));
+            h->many_mask = nullptr;
+            h->many_mask_bytes = 0;
+            CK(h, cudaMalloc(&h->many_mask, need));
+            h->many_mask_bytes = need;
+        }
+        mdev = h->many_mask;
+    }
+    for (int32_t i0 = 0; i0 < n;) {
+        int32_t run = n - i0;
+        const int64_t left = (int64_t)REBASE_EVERY - (int64_t)h->steps_since_rebase;
+        if (left >= 1 && run > left) run = (int32_t)left;
+        const int rc = launch_frame(h, static_cast<const char *>(fptr) + (size_t)i0 * stride * eb, pitch,
+                                    mdev ? mdev + (size_t)i0 * dp.P : nullptr, nullptr, nullptr, run, stride);
+        if (rc) return rc;
+        i0 += run;
+    }
+    if (on_device) return PROST_OK;
+    int st = 0;
+    int rc = read_status(h, &st);
+    if (rc) return rc;
+    if (st != PROST_OK && st != PROST_ENOTSPD) return st;
+    if (masks_out) {
+        CK(h, cudaMemcpyAsync(masks_out, h->many_mask, (size_t)n * dp.P, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
     return st;
 }
 

@@ -28,6 +28,8 @@ constexpr int KREG = 10;
 // The resident form deals the pixels of a plane to its CTAs in units of
 // RES_UNIT pixels (every CTA takes all channels of its pixels).
 constexpr int RES_UNIT = 64;
+// copies of each CTA's partial values per residual pass in the resident form
+constexpr int RES_NREP = 8;
 __host__ __device__ constexpr size_t res_al16(size_t b) { return (b + 15) & ~(size_t)15; }
 __host__ __device__ inline int64_t res_units(int64_t P) { return (P + RES_UNIT - 1) / RES_UNIT; }
 // pixel pairs per channel of the CTA with the most units
@@ -153,6 +155,8 @@ struct FrameArgs {
     int32_t *status_out;      // optional (device): the frame's status, as last_status
     unsigned int *counter;    // arrival counter of the pass-sequence form's reductions (zero between launches)
     int res_ns;               // resident form: row slots (items) per CTA in shared memory
+    int nframes;              // resident form: frames of the stream in this launch (0 or 1: one)
+    int64_t frame_stride;     // entries from one frame of the launch to the next
     DevParams prm;
 };
 

@@ -32,8 +32,6 @@
 
 #include <string.h>
 
-#include <type_traits>
-
 #include "prost_kernels.cuh"
 #include "prost_stage.cuh"
 
@@ -261,10 +259,12 @@ __device__ __noinline__ void reduce_cols(const float *cols, int nrows, int cstri
 }
 
 // CTA sum of N per-thread values (all threads), the first nv written to
-// out[i * os].  The grid barrier that follows orders these stores before
-// its arrival (CTA barrier, then one fence by the arriving thread).
+// out[i * os] (and to nrep - 1 more copies, rstride floats apart).  The grid
+// barrier that follows orders these stores before its arrival (CTA barrier,
+// then one fence by the arriving thread).
 template <int N, int NCW>
-__device__ __forceinline__ void cons_partials(float (&v)[N], int nv, float *out, float *sred, int os)
+__device__ __forceinline__ void cons_partials(float (&v)[N], int nv, float *out, float *sred, int os, int nrep = 1,
+                                              size_t rstride = 0)
 {
     warp_split_reduce<N>(v);
     constexpr int PER = N / 32;
@@ -276,7 +276,7 @@ __device__ __forceinline__ void cons_partials(float (&v)[N], int nv, float *out,
         float a = 0.f;
 #pragma unroll
         for (int ww = 0; ww < NCW; ++ww) a += sred[ww * N + i];
-        out[(size_t)i * os] = a;
+        for (int r = 0; r < nrep; ++r) out[(size_t)i * os + r * rstride] = a;
     }
 }
 
@@ -284,7 +284,8 @@ __device__ __forceinline__ void cons_partials(float (&v)[N], int nv, float *out,
 // only): for the streaming form's long per-lane vectors, where the lane-
 // dependent selects of the split reduction would put the vector in local memory.
 template <int N, int NCW, int NA, int S0 = 0, int S1 = 0>
-__device__ __forceinline__ void cons_partials_tree(float (&v)[NA], int nv, float *out, float *sred, int os)
+__device__ __forceinline__ void cons_partials_tree(float (&v)[NA], int nv, float *out, float *sred, int os,
+                                                   int nrep = 1, size_t rstride = 0)
 {
     static_assert(N <= NA, "values beyond the array");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -302,7 +303,7 @@ __device__ __forceinline__ void cons_partials_tree(float (&v)[NA], int nv, float
         float a = 0.f;
 #pragma unroll
         for (int ww = 0; ww < NCW; ++ww) a += sred[ww * N + i];
-        out[(size_t)i * os] = a;
+        for (int r = 0; r < nrep; ++r) out[(size_t)i * os + r * rstride] = a;
     }
 }
 
@@ -1110,11 +1111,14 @@ template <int K, typename FT, typename UT> struct ResSmem {
 //   MODE 0: a CG pass (cost, U^T eta, |eta|^2, non-finite count, U^T diag(c) U)
 //   MODE 1: the final pass (the same without the matrix)
 //   MODE 2: the explicit projection pass, sum of pi(eta)_e^2 = (eta_e - u_e^T g)^2
-// FILL: the first pass of the frame, which reads everything from global memory
-// and fills the shared-memory copies.
-template <int K, typename FT, typename UT, int MODE, bool FILL, int NA>
-__device__ __forceinline__ void res_pass(const FrameArgs &a, const ResPart &rp, const ResSmem<K, FT, UT> &sm,
-                                         const SKState<K> &sk, float (&acc)[NA])
+// FILL: 0 in the later passes of a frame; 1 in the first pass of a launch,
+// which reads the rows, frame entries and labels from global memory and fills
+// the shared-memory copies; 2 in the first pass of a later frame of the same
+// launch, whose rows and labels the previous frame's update pass left in
+// shared memory: only the frame entries are read and kept.
+template <int K, typename FT, typename UT, int MODE, int FILL, int NA>
+__device__ __forceinline__ void res_pass(const FrameArgs &a, const FT *frame, const ResPart &rp,
+                                         const ResSmem<K, FT, UT> &sm, const SKState<K> &sk, float (&acc)[NA])
 {
     using F = FCfg<K, UT>;
     using RP = RPair<UT>;
@@ -1122,6 +1126,7 @@ __device__ __forceinline__ void res_pass(const FrameArgs &a, const ResPart &rp, 
     constexpr int TP = F::TP, NT = F::THREADS;
     constexpr int NM = MODE == 0 ? F::NM : 0;
     static_assert(!(FILL && MODE == 2), "the projection pass is never a frame's first");
+    static_assert(FILL >= 0 && FILL <= 2, "fill mode");
     const DevParams &prm = a.prm;
     float y[K], tg[K];
 #pragma unroll
@@ -1131,7 +1136,6 @@ __device__ __forceinline__ void res_pass(const FrameArgs &a, const ResPart &rp, 
     }
     const float mu = prm.mu, e = prm.e, pw = prm.p, om = prm.omega;
     const float sc = prm.in_scale, of = prm.in_offset;
-    const FT *frame = static_cast<const FT *>(a.frame);
     const UT *U = static_cast<const UT *>(a.U);
     const int np = rp.npair;
     int c = 0, q = threadIdx.x;
@@ -1143,13 +1147,13 @@ __device__ __forceinline__ void res_pass(const FrameArgs &a, const ResPart &rp, 
         const int64_t p = rp.pa + 2 * (int64_t)q;
         const int nvalid = prm.P - p < 2 ? (int)(prm.P - p) : 2;
         float u[K][2];
-        if (FILL || it < rp.ng) {
+        if (FILL == 1 || it < rp.ng) {
             const int64_t pt = p / TP;
             const UT *ub = U + (((int64_t)c * prm.npt + pt) * K) * TP + (p - pt * TP);
             typename RP::T v[K];
 #pragma unroll
             for (int j = 0; j < K; ++j) v[j] = RP::ldg(ub + j * TP);
-            if (FILL && it >= rp.ng) {
+            if (FILL == 1 && it >= rp.ng) {
 #pragma unroll
                 for (int j = 0; j < K; ++j) sm.us[j * sm.ns + (it - rp.ng)] = v[j];
             }
@@ -1169,13 +1173,16 @@ __device__ __forceinline__ void res_pass(const FrameArgs &a, const ResPart &rp, 
         }
         typename XP::T xr;
         uchar2 lr;
-        if (FILL) {
+        if (FILL != 0) {
             xr = XP::ldg(frame + (int64_t)c * a.frame_pitch + p, nvalid);
-            lr = __ldg(reinterpret_cast<const uchar2 *>(a.labels + p));
             sm.xs[it] = xr;
-            if (c == 0) sm.ls[q] = lr;
         } else {
             xr = sm.xs[it];
+        }
+        if (FILL == 1) {
+            lr = __ldg(reinterpret_cast<const uchar2 *>(a.labels + p));
+            if (c == 0) sm.ls[q] = lr;
+        } else {
             lr = sm.ls[q];
         }
         const float2 xw = XP::wide(xr);
@@ -1230,10 +1237,13 @@ __device__ __forceinline__ void res_pass(const FrameArgs &a, const ResPart &rp, 
 // channels in turn (the label of Step 3 is the maximum over the channels),
 // the old rows from shared memory (or L2 for items [0, ng)), and writes the
 // new rows, the labels and the optional outputs to global memory; per-thread
-// sums of the Gram of the written rows and of the foreground count.
+// sums of the Gram of the written rows and of the foreground count.  keep: a
+// later frame of the launch follows, so the new rows and labels also replace
+// the shared-memory copies it starts from.
 template <int K, typename FT, typename UT>
-__device__ __forceinline__ void res_update(const FrameArgs &a, const ResPart &rp, const ResSmem<K, FT, UT> &sm,
-                                           const SKState<K> &sk, float (&acc)[FCfg<K, UT>::NPU])
+__device__ __forceinline__ void res_update(const FrameArgs &a, uint8_t *mask_out, float *bg_out, bool keep,
+                                           const ResPart &rp, const ResSmem<K, FT, UT> &sm, const SKState<K> &sk,
+                                           float (&acc)[FCfg<K, UT>::NPU])
 {
     using F = FCfg<K, UT>;
     using RP = RPair<UT>;
@@ -1309,7 +1319,7 @@ __device__ __forceinline__ void res_update(const FrameArgs &a, const ResPart &rp
                 const float rn = pre ? res : fmaf(-gam[r], yn, res);
                 if (valid) {
                     mx[r] = fmaxf(mx[r], fabsf(rn));
-                    if (write && a.bg_out) a.bg_out[(int64_t)c * prm.P + p + r] = x - rn + of;
+                    if (write && bg_out) bg_out[(int64_t)c * prm.P + p + r] = x - rn + of;
                 }
             }
             // stored rows of u + gamma v: u_st + gamma R^T v; a bfloat16 row
@@ -1341,8 +1351,11 @@ __device__ __forceinline__ void res_update(const FrameArgs &a, const ResPart &rp
                     for (int l2 = j; l2 < K; ++l2) acc[tri<K>(j, l2)] = fmaf(u[j][r], u[l2][r], acc[tri<K>(j, l2)]);
             if (write) {
 #pragma unroll
-                for (int j = 0; j < K; ++j)
-                    *reinterpret_cast<typename RP::T *>(ub + j * TP) = RP::pack(u[j][0], u[j][1]);
+                for (int j = 0; j < K; ++j) {
+                    const typename RP::T v = RP::pack(u[j][0], u[j][1]);
+                    *reinterpret_cast<typename RP::T *>(ub + j * TP) = v;
+                    if (keep && it >= rp.ng) sm.us[j * sm.ns + (it - rp.ng)] = v;
+                }
             }
         }
         const uint8_t nl0 = (nvalid > 0 && mx[0] >= dl) ? 1 : 0;
@@ -1350,12 +1363,31 @@ __device__ __forceinline__ void res_update(const FrameArgs &a, const ResPart &rp
         acc[NM] += (float)(nl0 + nl1);
         if (write) {
             *reinterpret_cast<uchar2 *>(a.labels + p) = make_uchar2(nl0, nl1);
-            if (a.mask_out) {
-                if (nvalid > 0) a.mask_out[p] = nl0;
-                if (nvalid > 1) a.mask_out[p + 1] = nl1;
+            if (keep) sm.ls[q] = make_uchar2(nl0, nl1);
+            if (mask_out) {
+                if (nvalid > 0) mask_out[p] = nl0;
+                if (nvalid > 1) mask_out[p + 1] = nl1;
             }
         }
     }
+}
+
+// The k-space state a later frame of a resident-form launch takes from the
+// global state after its first grid barrier: the factors, y and the frame
+// counter the last CTA of the previous frame wrote (L2 loads: the values this
+// CTA read before may still sit in its L1).  The CTA barriers of the
+// reduction that follows order these stores before the k-space step.
+template <int K>
+__device__ __forceinline__ void reload_state(SKState<K> &sk, ReorthScratch<K> &rs, const KState *ks)
+{
+    const int tid = threadIdx.x;
+    for (int i = tid; i < K * K; i += blockDim.x) {
+        sk.Tf[i] = __ldcg(&ks->Tf[i]);
+        sk.Rf[i] = (float)__ldcg(&ks->R[(i / K) * KMAX + (i % K)]);
+        rs.Told[i] = __ldcg(&ks->T[(i / K) * KMAX + (i % K)]);
+    }
+    if (tid < K) sk.y[tid] = __ldcg(&ks->y[tid]);
+    if (tid == 0) sk.frame_index = __ldcg(&ks->frame_index);
 }
 
 // The frame of one stream, by CTA b of the G CTAs working on it.
@@ -1370,17 +1402,14 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     using F = FCfg<K, UT>;
     constexpr int TP = F::TP, RW = F::RW, IPT = F::IPT, NT = F::THREADS, NW = F::NW;
     constexpr int NM = F::NM;
+    constexpr int NREP = RES ? RES_NREP : 1; // copies of the partial values (see the pass loop)
     __shared__ float sred[NW * F::NPMAX];
     __shared__ float tot[F::NVR > F::NVU ? F::NVR : F::NVU];
     __shared__ float rscr[RED_SCR];
     __shared__ SKState<K> sk;
     extern __shared__ __align__(128) float stage_smem[]; // streaming and resident forms only
     static_assert(!(RES && (F::STREAM || CL)), "the resident form is a grid form of the register form");
-    // the end-of-frame scratch: in the resident form it takes the start of the
-    // dynamic shared memory, whose rows are dead once the update pass is done
-    __shared__ typename std::conditional<RES, char, ReorthScratch<K>>::type rs_slot;
-    ReorthScratch<K> &rs = *reinterpret_cast<ReorthScratch<K> *>(RES ? static_cast<void *>(stage_smem)
-                                                                          : static_cast<void *>(&rs_slot));
+    __shared__ ReorthScratch<K> rs;
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const DevParams &prm = a.prm;
@@ -1404,7 +1433,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     for (int i = tid; i < K * K; i += NT) {
         sk.Tf[i] = a.ks->Tf[i];
         sk.Rf[i] = (float)a.ks->R[(i / K) * KMAX + (i % K)];
-        if constexpr (!RES) rs.Told[i] = a.ks->T[(i / K) * KMAX + (i % K)];
+        rs.Told[i] = a.ks->T[(i / K) * KMAX + (i % K)];
     }
     if (tid < K) {
         sk.y[tid] = a.ks->y[tid];
@@ -1427,14 +1456,30 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     constexpr int RES_OFF = SC::D * SC::STAGE_B + SC::RES_B; // a warp's tensor-core result
     const ResPart rpart(prm, G, b, a.res_ns);
     const ResSmem<K, FT, UT> rsm(sbase, prm, G, a.res_ns);
+    // the partial buffers alternate over every pass of the launch, so the
+    // first pass of a frame never writes the buffer from which the last CTA
+    // of the frame before is still reading the update pass's sums
     int buf = 0;
-    unsigned long long target = a.bar_base;
+    // frames of this launch: one, or in the resident form nframes of the same
+    // stream in turn, each frame a_frame_stride entries after the one before
+    const int nfr = RES ? (a.nframes > 1 ? a.nframes : 1) : 1;
+    for (int fr = 0; fr < nfr; ++fr) {
+    const FT *fptr = static_cast<const FT *>(a.frame) + (int64_t)fr * a.frame_stride;
+    uint8_t *mask_out = a.mask_out ? a.mask_out + (int64_t)fr * prm.P : nullptr;
+    unsigned long long target =
+        a.bar_base + (unsigned long long)fr * (unsigned long long)G * (unsigned long long)frame_arrivals(prm.n_cg);
+    const int stall_at = fr == 0 ? a.stall_at : 0;
     if (stats && tid == 0) a.ks->phase_ts[0] = global_ns();
 
     for (int pass = 0; pass <= prm.n_cg; ++pass) {
         const int cs = a.col_stride;
-        const float *cols = a.partials + (size_t)buf * F::NVR * cs;
-        float *col = const_cast<float *>(cols) + b;
+        float *const bbase = a.partials + (size_t)buf * NREP * F::NVR * cs;
+        // the resident form writes NREP copies of each CTA's partial values and
+        // CTA b sums copy b % NREP, so that each L2 line of the partials serves
+        // G / NREP readers rather than all G at once
+        const float *cols = bbase + (size_t)(b % NREP) * F::NVR * cs;
+        float *col = bbase + b;
+        const size_t rstr = (size_t)F::NVR * cs;
         target += (unsigned long long)G;
         if (pass < prm.n_cg) {
             const bool trace = stats && tid == 0 && pass == 1;
@@ -1442,10 +1487,12 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
 #pragma unroll
             for (int i = 0; i < F::NPR; ++i) acc[i] = 0.f;
             if constexpr (RES) {
-                if (pass == 0)
-                    res_pass<K, FT, UT, 0, true>(a, rpart, rsm, sk, acc);
+                if (pass == 0 && fr == 0)
+                    res_pass<K, FT, UT, 0, 1>(a, fptr, rpart, rsm, sk, acc);
+                else if (pass == 0)
+                    res_pass<K, FT, UT, 0, 2>(a, fptr, rpart, rsm, sk, acc);
                 else
-                    res_pass<K, FT, UT, 0, false>(a, rpart, rsm, sk, acc);
+                    res_pass<K, FT, UT, 0, 0>(a, fptr, rpart, rsm, sk, acc);
             } else if constexpr (F::STREAM)
                 stream_residual<K, FT, UT, true, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
             else
@@ -1457,13 +1504,14 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             } else if constexpr (F::STREAM) {
                 cons_partials_tree<F::NVR, NW>(acc, F::NVR, col, sred, cs);
             } else {
-                cons_partials<F::NPR, NW>(acc, F::NVR, col, sred, cs);
+                cons_partials<F::NPR, NW>(acc, F::NVR, col, sred, cs, NREP, rstr);
             }
             if (trace) a.ks->sub_ts[1] = global_ns();
-            if (!pass_sync<CL, NT>(a.bar, target + (pass + 1 == a.stall_at ? 1ull : 0ull), &sk.err, a.ks,
-                                   a.status_out, pass + 1 == a.stall_at ? a.stall_limit : WAIT_LIMIT))
+            if (!pass_sync<CL, NT>(a.bar, target + (pass + 1 == stall_at ? 1ull : 0ull), &sk.err, a.ks,
+                                   a.status_out, pass + 1 == stall_at ? a.stall_limit : WAIT_LIMIT))
                 return;
             if (trace) a.ks->sub_ts[2] = global_ns();
+            if (RES && fr > 0 && pass == 0) reload_state(sk, rs, a.ks);
             reduce_cols<NT>(cols, G, cs, F::NVR, tot, rscr);
             if (trace) a.ks->sub_ts[3] = global_ns();
             if (warp == 0) kspace_cg<K, true>(sk, prm, tot, pass, a.ks, stats);
@@ -1473,10 +1521,12 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
 #pragma unroll
             for (int i = 0; i < F::NPF; ++i) acc[i] = 0.f;
             if constexpr (RES) {
-                if (pass == 0)
-                    res_pass<K, FT, UT, 1, true>(a, rpart, rsm, sk, acc);
+                if (pass == 0 && fr == 0)
+                    res_pass<K, FT, UT, 1, 1>(a, fptr, rpart, rsm, sk, acc);
+                else if (pass == 0)
+                    res_pass<K, FT, UT, 1, 2>(a, fptr, rpart, rsm, sk, acc);
                 else
-                    res_pass<K, FT, UT, 1, false>(a, rpart, rsm, sk, acc);
+                    res_pass<K, FT, UT, 1, 0>(a, fptr, rpart, rsm, sk, acc);
             } else if constexpr (F::STREAM)
                 stream_residual<K, FT, UT, false, NW>(a, tl.r0, tl.nres, sk.yf, wstage, acc);
             else
@@ -1484,10 +1534,11 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             if constexpr (F::STREAM)
                 cons_partials_tree<F::NVF, NW>(acc, F::NVF, col, sred, cs);
             else
-                cons_partials<F::NPF, NW>(acc, F::NVF, col, sred, cs);
-            if (!pass_sync<CL, NT>(a.bar, target + (pass + 1 == a.stall_at ? 1ull : 0ull), &sk.err, a.ks,
-                                   a.status_out, pass + 1 == a.stall_at ? a.stall_limit : WAIT_LIMIT))
+                cons_partials<F::NPF, NW>(acc, F::NVF, col, sred, cs, NREP, rstr);
+            if (!pass_sync<CL, NT>(a.bar, target + (pass + 1 == stall_at ? 1ull : 0ull), &sk.err, a.ks,
+                                   a.status_out, pass + 1 == stall_at ? a.stall_limit : WAIT_LIMIT))
                 return;
+            if (RES && fr > 0 && pass == 0) reload_state(sk, rs, a.ks);
             reduce_cols<NT>(cols, G, cs, F::NVF, tot, rscr);
             if (warp == 0) kspace_cg<K, false>(sk, prm, tot, pass, a.ks, stats);
         }
@@ -1499,16 +1550,17 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     // ---- |pi(eta)| by the explicit projection pass, where the norm identity
     // of the final pass cancels (the same decision in every CTA) ----
     if (sk.proj) {
-        const float *pcols = a.partials + (size_t)buf * F::NVR * a.col_stride;
+        float *const pbase = a.partials + (size_t)buf * NREP * F::NVR * a.col_stride;
+        const float *pcols = pbase + (size_t)(b % NREP) * F::NVR * a.col_stride;
         target += (unsigned long long)G;
         float acc1[1] = {0.f};
         if constexpr (RES)
-            res_pass<K, FT, UT, 2, false>(a, rpart, rsm, sk, acc1);
+            res_pass<K, FT, UT, 2, 0>(a, fptr, rpart, rsm, sk, acc1);
         else if constexpr (F::STREAM)
             stream_residual<K, FT, UT, false, NW, 1, true>(a, tl.r0, tl.nres, sk.yf, wstage, acc1, sk.tg);
         else
             proj_pass<K, FT, UT>(a, tl, sk, acc1[0]);
-        cons_partials_tree<1, NW, 1>(acc1, 1, const_cast<float *>(pcols) + b, sred, a.col_stride);
+        cons_partials_tree<1, NW, 1>(acc1, 1, pbase + b, sred, a.col_stride, NREP, (size_t)F::NVR * a.col_stride);
         if (!pass_sync<CL, NT>(a.bar, target, &sk.err, a.ks, a.status_out)) return;
         reduce_cols<NT>(pcols, G, a.col_stride, 1, tot, rscr);
         if (tid == 0) step_angle(sk, prm, sqrtf(fmaxf(tot[0], 0.f)), a.ks, stats);
@@ -1517,7 +1569,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     }
 
     // ---- update pass: Step 2 on every row, Step 3 labels, Gram of the new rows ----
-    const float *ucols = a.partials + (size_t)buf * F::NVR * a.col_stride;
+    const float *ucols = a.partials + (size_t)buf * NREP * F::NVR * a.col_stride; // one copy: the last CTA reads it
     float *ucol = const_cast<float *>(ucols) + b;
     if constexpr (F::STREAM) {
         float acc[F::NPU];
@@ -1544,7 +1596,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         float acc[F::NPU];
 #pragma unroll
         for (int i = 0; i < F::NPU; ++i) acc[i] = 0.f;
-        res_update<K, FT, UT>(a, rpart, rsm, sk, acc);
+        res_update<K, FT, UT>(a, mask_out, nfr == 1 ? a.bg_out : nullptr, fr + 1 < nfr, rpart, rsm, sk, acc);
         if (tid == 0 && stats) a.ks->sub_ts[5] = global_ns();
         cons_partials<F::NPU, NW>(acc, F::NVU, ucol, sred, a.col_stride);
     } else {
@@ -1676,21 +1728,43 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         __threadfence(); // the CTA's partial values before the arrival
         const unsigned long long inc = sk.proj ? 1ull : 2ull;
         const unsigned long long old = atomicAdd(&a.bar->count, inc);
-        sk.last = old + inc == a.bar_base + (unsigned long long)G * (unsigned long long)frame_arrivals(prm.n_cg);
+        sk.last = old + inc == a.bar_base + (unsigned long long)(fr + 1) * (unsigned long long)G *
+                                                (unsigned long long)frame_arrivals(prm.n_cg);
         __threadfence();
     }
     cons_sync<NT>();
     if (tid == 0 && stats) a.ks->sub_ts[7] = global_ns();
-    if (!sk.last) return;
-    if constexpr (RES) {
-        // every CTA's update pass is done: the dynamic shared memory is free
-        for (int i = tid; i < K * K; i += NT) rs.Told[i] = a.ks->T[(i / K) * KMAX + (i % K)];
+    if (sk.last) {
+        reduce_cols<NT>(ucols, G, a.col_stride, F::NVU, tot, rscr);
+        if (tid == 0) a.ks->sub_ts[8] = global_ns();
+        end_frame<K, NT>(sk, a.ks, tot, tot[NM], rs, a.status_out);
+        if (tid == 0) a.ks->sub_ts[9] = global_ns();
+        if (tid == 0) a.ks->phase_ts[prm.n_cg + 2] = global_ns();
     }
-    reduce_cols<NT>(ucols, G, a.col_stride, F::NVU, tot, rscr);
-    if (tid == 0) a.ks->sub_ts[8] = global_ns();
-    end_frame<K, NT>(sk, a.ks, tot, tot[NM], rs, a.status_out);
-    if (tid == 0) a.ks->sub_ts[9] = global_ns();
-    if (tid == 0) a.ks->phase_ts[prm.n_cg + 2] = global_ns();
+    if (fr + 1 < nfr) {
+        // the next frame of the launch starts at once in every CTA.  Its
+        // residual passes need only the stored-row coefficients T y: each CTA
+        // forms them from its own y and T_old with the operations of
+        // end_frame (bit-identical to what the last CTA stores), or keeps them
+        // after a rejected frame.  The new factors, y and frame counter, which
+        // the last CTA writes before its first arrival of the next frame, are
+        // read after the next frame's first grid barrier (reload_state).
+        cons_sync<NT>();
+        if (tid < K && !sk.skip) {
+            double ty = 0.0;
+            for (int q = tid; q < K; ++q) ty = dfma(rs.Told[tid * K + q], sk.y[q], ty);
+            sk.yf[tid] = (float)ty;
+        }
+        cons_sync<NT>();
+        if (tid == 0) {
+            sk.skip = 0;
+            sk.last = 0;
+            sk.proj = 0;
+        }
+        buf ^= 1;
+        cons_sync<NT>();
+    }
+    } // frames of the launch
 }
 
 // One stream: the whole grid.
@@ -1852,8 +1926,7 @@ template <int K, typename UT> struct FrameOps {
             if (cap <= fixed) return 0;
             int64_t nsl = (cap - fixed) / slot;
             if (nsl > nim) nsl = nim;
-            int64_t bytes = (int64_t)res_smem_bytes<K, FT, UT>(C, npm, (int)nsl);
-            if (bytes < (int64_t)res_al16(sizeof(ReorthScratch<K>))) bytes = (int64_t)res_al16(sizeof(ReorthScratch<K>));
+            const int64_t bytes = (int64_t)res_smem_bytes<K, FT, UT>(C, npm, (int)nsl);
             if (bytes > cap) return 0;
             // the attribute is the largest size any handle asks for: always the cap
             if (cudaFuncSetAttribute(k_frame_res<K, FT, UT>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -68,6 +68,7 @@ def lib():
         L.prost_state_bytes.argtypes = [P(prost_params), P(sz)]
         L.prost_init.argtypes = [P(prost_params), vp, P(vp)]
         L.prost_step.argtypes = [vp, vp, C.c_int, vp, vp]
+        L.prost_step_many.argtypes = [vp, vp, C.c_int32, C.c_int, vp]
         L.prost_sync.argtypes = [vp]
         L.prost_step_async.argtypes = [vp, vp, vp, vp]
         L.prost_wait.argtypes = [vp]
@@ -227,6 +228,15 @@ def prost_step(h, frame, mask_out=None, background_out=None):
     buffers: the frame's status; device buffers: PROST_OK once enqueued)."""
     od = _where(frame, mask_out, background_out)
     return _check(lib().prost_step(h, _ptr(frame), od, _ptr(mask_out), _ptr(background_out)), h,
+                  allow=(PROST_EBADFRAME,))
+
+
+def prost_step_many(h, frames, n, masks_out=None):
+    """Steps 1-3 for n consecutive frames (frames: n * m entries, masks_out:
+    n * P bytes); host buffers: the last frame's status, device buffers:
+    PROST_OK once enqueued."""
+    od = _where(frames, masks_out)
+    return _check(lib().prost_step_many(h, _ptr(frames), int(n), od, _ptr(masks_out)), h,
                   allow=(PROST_EBADFRAME,))
 
 

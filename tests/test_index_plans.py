@@ -598,8 +598,12 @@ assert "return (int)((res_units(P) + G - 1) / G) * (RES_UNIT / 2);" in DEVICE_H
 assert "const int64_t lo = nu * b / G, hi = nu * (b + 1) / G;" in FRAME_CUH
 assert "ng = nitems > ns ? nitems - ns : 0;" in FRAME_CUH
 assert "if (g > res_units(dp.P)) g = res_units(dp.P);" in API_CU
-# the partial-row buffers serve whichever of the grid and resident grids is larger
-assert "(size_t)2 * col_stride(std::max(h->grid_frame, h->grid_res)) *" in API_CU
+# the partial buffers: two per launch, and in the resident form RES_NREP copies
+# of each pass's partial values (CTA b writes every copy, reads copy b % RES_NREP)
+RES_NREP = _const(DEVICE_H, r"constexpr int RES_NREP = (\d+);")
+assert "(size_t)2 * RES_NREP * col_stride(h->grid_res) * partial_row(prm->k));" in API_CU
+assert "float *const bbase = a.partials + (size_t)buf * NREP * F::NVR * cs;" in FRAME_CUH
+assert "const float *cols = bbase + (size_t)(b % NREP) * F::NVR * cs;" in FRAME_CUH
 
 
 def res_units(P):
@@ -694,3 +698,12 @@ def test_resident_plan_covers_every_entry_once_inside_its_buffers(P, C, k, usz, 
                     qq -= npair
                     cc += 1
     assert (seen == 1).all()
+    # partial values of every pass: copy r of value c of CTA b inside the buffers
+    cs = (G + 3) // 4 * 4
+    nv = partial_row(k)
+    floats = 2 * RES_NREP * cs * nv
+    for buf in (0, 1):
+        base = buf * RES_NREP * nv * cs
+        top = max(base + r * nv * cs + c * cs + b for r in (0, RES_NREP - 1) for c in (0, nv - 1)
+                  for b in (0, G - 1))
+        assert top < floats
