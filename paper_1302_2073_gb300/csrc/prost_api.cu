@@ -390,6 +390,7 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
         int64_t g = (int64_t)occ * h->num_sms;
         if (g > res_units(dp.P)) g = res_units(dp.P); // every CTA gets at least one unit
         if (g > max_frame_grid((int)partial_row(prm->k))) g = max_frame_grid((int)partial_row(prm->k));
+        if (g > RES_MAX_GRID) g = RES_MAX_GRID; // the chunks of its cross-CTA sums
         int ns = 0, smem = 0;
         if (g >= 1 && ops->res_plan(fdt, dp.P, dp.C, (int)g, &ns, &smem)) {
             const int64_t nim = (int64_t)dp.C * res_npair_max(dp.P, (int)g);

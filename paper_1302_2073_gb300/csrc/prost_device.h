@@ -30,6 +30,12 @@ constexpr int KREG = 10;
 constexpr int RES_UNIT = 64;
 // copies of each CTA's partial values per residual pass in the resident form
 constexpr int RES_NREP = 8;
+// its cross-CTA sums (reduce_cols_warp): values per warp of a 512-thread CTA
+// (the largest partial row, k = 10: 10 + 55 + 3 = 68 <= 5 * 16) and 16-byte
+// chunks per lane (grids of at most RES_MAX_GRID = 4 * 32 * RES_CPL CTAs)
+constexpr int RES_VPW = 5;
+constexpr int RES_CPL = 2;
+constexpr int RES_MAX_GRID = 128 * RES_CPL;
 __host__ __device__ constexpr size_t res_al16(size_t b) { return (b + 15) & ~(size_t)15; }
 __host__ __device__ inline int64_t res_units(int64_t P) { return (P + RES_UNIT - 1) / RES_UNIT; }
 // pixel pairs per channel of the CTA with the most units

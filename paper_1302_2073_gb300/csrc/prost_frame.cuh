@@ -258,6 +258,50 @@ __device__ __noinline__ void reduce_cols(const float *cols, int nrows, int cstri
     cons_sync<NCONS>();
 }
 
+// The same sum for the resident form, by warps: warp w takes values w, w + NW,
+// ... (VPW at most), lane l the 16-byte chunks l, l + 32, ... (CPL at most) of
+// each value's row, so that every load instruction of a warp reads 512
+// contiguous bytes; all of a warp's loads are in flight before the first sum.
+// Each lane adds its entries below nrows in order, then a fixed shuffle tree
+// adds the 32 lane sums.  Plain FP32 (about log2(nrows) roundings per value)
+// in a fixed order: identical in every CTA and from run to run.  Needs
+// nv <= VPW * NT / 32 and nrows <= 128 * CPL.
+template <int NT, int VPW, int CPL>
+__device__ __noinline__ void reduce_cols_warp(const float *cols, int nrows, int cstride, int nv, float *tot)
+{
+    constexpr int NW = NT / 32;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nch = (nrows + 3) >> 2;
+    float4 v[VPW][CPL];
+#pragma unroll
+    for (int i = 0; i < VPW; ++i) {
+        const int c = w + i * NW;
+        const float4 *row = reinterpret_cast<const float4 *>(cols + (size_t)(c < nv ? c : 0) * cstride);
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int ch = lane + 32 * j;
+            v[i][j] = (c < nv && ch < nch) ? __ldcg(row + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < VPW; ++i) {
+        const int c = w + i * NW;
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < CPL; ++j) {
+            const int r = 4 * (lane + 32 * j);
+            s += r < nrows ? v[i][j].x : 0.f;
+            s += r + 1 < nrows ? v[i][j].y : 0.f;
+            s += r + 2 < nrows ? v[i][j].z : 0.f;
+            s += r + 3 < nrows ? v[i][j].w : 0.f;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(FULL, s, off);
+        if (lane == 0 && c < nv) tot[c] = s;
+    }
+    cons_sync<NT>();
+}
+
 // CTA sum of N per-thread values (all threads), the first nv written to
 // out[i * os] (and to nrep - 1 more copies, rstride floats apart).  The grid
 // barrier that follows orders these stores before its arrival (CTA barrier,
@@ -1409,6 +1453,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     __shared__ SKState<K> sk;
     extern __shared__ __align__(128) float stage_smem[]; // streaming and resident forms only
     static_assert(!(RES && (F::STREAM || CL)), "the resident form is a grid form of the register form");
+    static_assert(!RES || (F::NVR <= RES_VPW * NW && F::NVU <= RES_VPW * NW), "values per warp of the sums");
     __shared__ ReorthScratch<K> rs;
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -1512,7 +1557,10 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 return;
             if (trace) a.ks->sub_ts[2] = global_ns();
             if (RES && fr > 0 && pass == 0) reload_state(sk, rs, a.ks);
-            reduce_cols<NT>(cols, G, cs, F::NVR, tot, rscr);
+            if constexpr (RES)
+                reduce_cols_warp<NT, RES_VPW, RES_CPL>(cols, G, cs, F::NVR, tot);
+            else
+                reduce_cols<NT>(cols, G, cs, F::NVR, tot, rscr);
             if (trace) a.ks->sub_ts[3] = global_ns();
             if (warp == 0) kspace_cg<K, true>(sk, prm, tot, pass, a.ks, stats);
             if (trace) a.ks->sub_ts[4] = global_ns();
@@ -1539,7 +1587,10 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                                    a.status_out, pass + 1 == stall_at ? a.stall_limit : WAIT_LIMIT))
                 return;
             if (RES && fr > 0 && pass == 0) reload_state(sk, rs, a.ks);
-            reduce_cols<NT>(cols, G, cs, F::NVF, tot, rscr);
+            if constexpr (RES)
+                reduce_cols_warp<NT, RES_VPW, RES_CPL>(cols, G, cs, F::NVF, tot);
+            else
+                reduce_cols<NT>(cols, G, cs, F::NVF, tot, rscr);
             if (warp == 0) kspace_cg<K, false>(sk, prm, tot, pass, a.ks, stats);
         }
         cons_sync<NT>();
@@ -1562,7 +1613,10 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             proj_pass<K, FT, UT>(a, tl, sk, acc1[0]);
         cons_partials_tree<1, NW, 1>(acc1, 1, pbase + b, sred, a.col_stride, NREP, (size_t)F::NVR * a.col_stride);
         if (!pass_sync<CL, NT>(a.bar, target, &sk.err, a.ks, a.status_out)) return;
-        reduce_cols<NT>(pcols, G, a.col_stride, 1, tot, rscr);
+        if constexpr (RES)
+            reduce_cols_warp<NT, RES_VPW, RES_CPL>(pcols, G, a.col_stride, 1, tot);
+        else
+            reduce_cols<NT>(pcols, G, a.col_stride, 1, tot, rscr);
         if (tid == 0) step_angle(sk, prm, sqrtf(fmaxf(tot[0], 0.f)), a.ks, stats);
         cons_sync<NT>();
         buf ^= 1;
@@ -1735,7 +1789,10 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     cons_sync<NT>();
     if (tid == 0 && stats) a.ks->sub_ts[7] = global_ns();
     if (sk.last) {
-        reduce_cols<NT>(ucols, G, a.col_stride, F::NVU, tot, rscr);
+        if constexpr (RES)
+            reduce_cols_warp<NT, RES_VPW, RES_CPL>(ucols, G, a.col_stride, F::NVU, tot);
+        else
+            reduce_cols<NT>(ucols, G, a.col_stride, F::NVU, tot, rscr);
         if (tid == 0) a.ks->sub_ts[8] = global_ns();
         end_frame<K, NT>(sk, a.ks, tot, tot[NM], rs, a.status_out);
         if (tid == 0) a.ks->sub_ts[9] = global_ns();

@@ -628,9 +628,15 @@ def res_part(P, C, G, b, ns):
     return pa, npair, nitems, max(nitems - ns, 0)
 
 
+RES_CPL = _const(DEVICE_H, r"constexpr int RES_CPL = (\d+);")
+RES_VPW = _const(DEVICE_H, r"constexpr int RES_VPW = (\d+);")
+assert "constexpr int RES_MAX_GRID = 128 * RES_CPL;" in DEVICE_H
+assert "if (g > RES_MAX_GRID) g = RES_MAX_GRID;" in API_CU
+
+
 def res_plan(P, C, k, usz, fsz, cap):
     """Grid, row slots and dynamic shared memory as FrameOps::res_plan_t sizes them."""
-    G = min(SMS, res_units(P), RED_SCR // partial_row(k) * RED_ROWS)
+    G = min(SMS, res_units(P), RED_SCR // partial_row(k) * RED_ROWS, 128 * RES_CPL)
     npm = res_npair_max(P, G)
     fixed = al16(C * npm * 2 * fsz) + al16(npm * 2)
     if cap <= fixed:
@@ -698,6 +704,12 @@ def test_resident_plan_covers_every_entry_once_inside_its_buffers(P, C, k, usz, 
                     qq -= npair
                     cc += 1
     assert (seen == 1).all()
+    # the warps' cross-CTA sums: every value has a warp, every CTA's entry a
+    # lane's chunk, and each 16-byte chunk ends inside the value's row
+    nvals = partial_row(k)
+    assert nvals <= RES_VPW * (threads(k, usz == 2) // 32)
+    nch = (G + 3) // 4
+    assert nch <= 32 * RES_CPL and 4 * nch <= (G + 3) // 4 * 4
     # partial values of every pass: copy r of value c of CTA b inside the buffers
     cs = (G + 3) // 4 * 4
     nv = partial_row(k)
