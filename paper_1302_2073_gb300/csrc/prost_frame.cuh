@@ -119,6 +119,8 @@ template <int K> struct SKState {
     float Tf[K * K];   // T = R^{-1}, row-major upper triangular
     float Rf[K * K];   // R, row-major upper triangular
     float cm1, snp, yn;
+    float apend;       // resident form: the last CG step's alpha, its FP64 y update pending
+    int ypend;
     int proj;          // |pi(eta)| is formed by the explicit projection pass
     int skip;          // frame rejected (non-finite entry)
     int err;           // a grid barrier gave up
@@ -372,10 +374,21 @@ __device__ __forceinline__ void mma_row(const unsigned char *base, int warp_byte
     }
 }
 
+// Arrival at the grid barrier as one release reduction: the CTA barrier
+// before it orders the other threads' stores, and the release makes them
+// visible with the arrival (no separate fence, no returned value).
+__device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 // Grid barrier: arrive, wait (bounded) until all CTAs arrived.
 // A wait that gives up (or sees another CTA's abort) marks the frame timed
 // out: the abort flag, ERR_TIMEOUT and the frame's status PROST_ETIMEOUT.
-template <int NCONS>
+// REL (the resident form): the arrival is a release reduction and the acquire
+// load that ends the wait orders what follows; otherwise a fence, an atomic
+// add, and a fence after the wait.
+template <int NCONS, bool REL = false>
 __device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target, int *s_err, KState *ks,
                                           int32_t *st_out, long long limit = WAIT_LIMIT)
 {
@@ -383,8 +396,12 @@ __device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target
     if (threadIdx.x == 0) {
         int ok = *s_err == 0;
         if (ok) {
-            __threadfence(); // the CTA's partial values (ordered by the CTA barrier) before the arrival
-            atomicAdd(&gb->count, 1ull);
+            if constexpr (REL) {
+                red_release_add(&gb->count, 1ull);
+            } else {
+                __threadfence(); // the CTA's partial values (ordered by the CTA barrier) before the arrival
+                atomicAdd(&gb->count, 1ull);
+            }
             const long long t0 = clock64();
             unsigned it = 0;
             while (ld_acquire_u64(&gb->count) < target) {
@@ -403,7 +420,7 @@ __device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target
             if (st_out) *st_out = -5;
             *s_err = 1;
         }
-        __threadfence();
+        if (!REL || !ok) __threadfence();
     }
     cons_sync<NCONS>();
     return *(volatile int *)s_err == 0;
@@ -422,7 +439,7 @@ __device__ __forceinline__ void cluster_sync_all()
 // The synchronisation between a pass's partial values and their reduction:
 // the cluster barrier (cluster form) or the bounded grid barrier, whose
 // failure marks the frame timed out.
-template <bool CL, int NCONS>
+template <bool CL, int NCONS, bool REL = false>
 __device__ __forceinline__ bool pass_sync(GridBar *gb, unsigned long long target, int *s_err, KState *ks,
                                           int32_t *st_out, long long limit = WAIT_LIMIT)
 {
@@ -430,7 +447,7 @@ __device__ __forceinline__ bool pass_sync(GridBar *gb, unsigned long long target
         cluster_sync_all();
         return true;
     } else {
-        return grid_wait<NCONS>(gb, target, s_err, ks, st_out, limit);
+        return grid_wait<NCONS, REL>(gb, target, s_err, ks, st_out, limit);
     }
 }
 
@@ -497,7 +514,9 @@ __device__ __forceinline__ void step_angle(SKState<K> &sk, const DevParams &prm,
 // FP64 and the step size t (an exponential of the frame counter) is FP64.
 // GB300's FP64 pipe is narrow and long-latency, so FP64 stays off the chains.
 // CTA 0 also records the statistics in the global state.
-template <int K, bool WM>
+// DEFER (the resident form): the FP64 update of y is left to another warp at
+// the start of the next pass (sk.apend, sk.ypend), off this step's chain.
+template <int K, bool WM, bool DEFER = false>
 __device__ void kspace_cg(SKState<K> &sk, const DevParams &prm, const float *tot, int pass, KState *gks,
                           bool stats)
 {
@@ -551,10 +570,14 @@ __device__ void kspace_cg(SKState<K> &sk, const DevParams &prm, const float *tot
         const float alpha = den > 0.f ? -dg / den : 0.f;
         if (act) {
             // y in FP64; the stored-basis coefficients T y move along T d
-            sk.y[l] = fma((double)alpha, (double)dl, sk.y[l]);
+            if constexpr (!DEFER) sk.y[l] = fma((double)alpha, (double)dl, sk.y[l]);
             sk.yf[l] = fmaf(alpha, dst, sk.yf[l]);
             sk.d[l] = dl;
             sk.gprev[l] = gl;
+        }
+        if (DEFER && l == 0) {
+            sk.apend = alpha;
+            sk.ypend = 1;
         }
         if (stats && l == 0) gks->alpha[pass] = alpha;
     } else {
@@ -1473,6 +1496,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         sk.skip = 0;
         sk.last = 0;
         sk.proj = 0;
+        sk.ypend = 0;
         sk.frame_index = a.ks->frame_index;
     }
     for (int i = tid; i < K * K; i += NT) {
@@ -1526,6 +1550,15 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         float *col = bbase + b;
         const size_t rstr = (size_t)F::NVR * cs;
         target += (unsigned long long)G;
+        if constexpr (RES) {
+            // the previous CG step's FP64 update of y, by the last warp
+            if (warp == NW - 1 && sk.ypend) {
+                const int l = tid & 31;
+                if (l < K) sk.y[l] = fma((double)sk.apend, (double)sk.d[l], sk.y[l]);
+                __syncwarp();
+                if (l == 0) sk.ypend = 0;
+            }
+        }
         if (pass < prm.n_cg) {
             const bool trace = stats && tid == 0 && pass == 1;
             float acc[F::NPR];
@@ -1552,7 +1585,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 cons_partials<F::NPR, NW>(acc, F::NVR, col, sred, cs, NREP, rstr);
             }
             if (trace) a.ks->sub_ts[1] = global_ns();
-            if (!pass_sync<CL, NT>(a.bar, target + (pass + 1 == stall_at ? 1ull : 0ull), &sk.err, a.ks,
+            if (!pass_sync<CL, NT, RES>(a.bar, target + (pass + 1 == stall_at ? 1ull : 0ull), &sk.err, a.ks,
                                    a.status_out, pass + 1 == stall_at ? a.stall_limit : WAIT_LIMIT))
                 return;
             if (trace) a.ks->sub_ts[2] = global_ns();
@@ -1562,7 +1595,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             else
                 reduce_cols<NT>(cols, G, cs, F::NVR, tot, rscr);
             if (trace) a.ks->sub_ts[3] = global_ns();
-            if (warp == 0) kspace_cg<K, true>(sk, prm, tot, pass, a.ks, stats);
+            if (warp == 0) kspace_cg<K, true, RES>(sk, prm, tot, pass, a.ks, stats);
             if (trace) a.ks->sub_ts[4] = global_ns();
         } else {
             float acc[F::NPF];
@@ -1583,7 +1616,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 cons_partials_tree<F::NVF, NW>(acc, F::NVF, col, sred, cs);
             else
                 cons_partials<F::NPF, NW>(acc, F::NVF, col, sred, cs, NREP, rstr);
-            if (!pass_sync<CL, NT>(a.bar, target + (pass + 1 == stall_at ? 1ull : 0ull), &sk.err, a.ks,
+            if (!pass_sync<CL, NT, RES>(a.bar, target + (pass + 1 == stall_at ? 1ull : 0ull), &sk.err, a.ks,
                                    a.status_out, pass + 1 == stall_at ? a.stall_limit : WAIT_LIMIT))
                 return;
             if (RES && fr > 0 && pass == 0) reload_state(sk, rs, a.ks);
@@ -1612,7 +1645,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         else
             proj_pass<K, FT, UT>(a, tl, sk, acc1[0]);
         cons_partials_tree<1, NW, 1>(acc1, 1, pbase + b, sred, a.col_stride, NREP, (size_t)F::NVR * a.col_stride);
-        if (!pass_sync<CL, NT>(a.bar, target, &sk.err, a.ks, a.status_out)) return;
+        if (!pass_sync<CL, NT, RES>(a.bar, target, &sk.err, a.ks, a.status_out)) return;
         if constexpr (RES)
             reduce_cols_warp<NT, RES_VPW, RES_CPL>(pcols, G, a.col_stride, 1, tot);
         else
