@@ -1300,6 +1300,24 @@ __device__ __forceinline__ void res_pass(const FrameArgs &a, const FT *frame, co
     }
 }
 
+// The next frame's entries of this CTA's pixels, fetched into L2 ahead of the
+// next frame's first pass (a later frame of a resident-form launch reads them
+// from global memory there): one 128-byte line per thread, only addresses
+// inside the CTA's range of each plane.
+template <typename FT>
+__device__ __forceinline__ void res_prefetch_frame(const FT *next, int64_t pitch, const ResPart &rp, const DevParams &prm)
+{
+    const int64_t np = prm.P - rp.pa < 2 * (int64_t)rp.npair ? prm.P - rp.pa : 2 * (int64_t)rp.npair;
+    if (np <= 0) return;
+    const int64_t bytes = np * (int64_t)sizeof(FT);
+    const int nl = (int)((bytes + 127) / 128);
+    for (int i = threadIdx.x; i < prm.C * nl; i += blockDim.x) {
+        const int c = i / nl, l = i - c * nl;
+        const char *ad = reinterpret_cast<const char *>(next + (int64_t)c * pitch + rp.pa) + (int64_t)l * 128;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ad));
+    }
+}
+
 // The update pass of the resident form: a thread takes a pixel pair and its
 // channels in turn (the label of Step 3 is the maximum over the channels),
 // the old rows from shared memory (or L2 for items [0, ng)), and writes the
@@ -1683,6 +1701,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         float acc[F::NPU];
 #pragma unroll
         for (int i = 0; i < F::NPU; ++i) acc[i] = 0.f;
+        if (fr + 1 < nfr) res_prefetch_frame<FT>(fptr + a.frame_stride, a.frame_pitch, rpart, prm);
         res_update<K, FT, UT>(a, mask_out, nfr == 1 ? a.bg_out : nullptr, fr + 1 < nfr, rpart, rsm, sk, acc);
         if (tid == 0 && stats) a.ks->sub_ts[5] = global_ns();
         cons_partials<F::NPU, NW>(acc, F::NVU, ucol, sred, a.col_stride);
