@@ -388,12 +388,13 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     if (!wide && !h->cluster_grid && ops->res_plan &&
         (prm->form == PROST_FORM_AUTO || prm->form == PROST_FORM_RESIDENT)) {
         int64_t g = (int64_t)occ * h->num_sms;
-        if (g > res_units(dp.P)) g = res_units(dp.P); // every CTA gets at least one unit
+        // every CTA but the end CTA gets at least one unit
+        if (g > res_units(dp.P) + 1) g = res_units(dp.P) + 1;
         if (g > max_frame_grid((int)partial_row(prm->k))) g = max_frame_grid((int)partial_row(prm->k));
         if (g > RES_MAX_GRID) g = RES_MAX_GRID; // the chunks of its cross-CTA sums
         int ns = 0, smem = 0;
-        if (g >= 1 && ops->res_plan(fdt, dp.P, dp.C, (int)g, &ns, &smem)) {
-            const int64_t nim = (int64_t)dp.C * res_npair_max(dp.P, (int)g);
+        if (g >= 2 && ops->res_plan(fdt, dp.P, dp.C, (int)g, &ns, &smem)) {
+            const int64_t nim = (int64_t)dp.C * res_npair_max(dp.P, (int)g - 1);
             if (prm->form == PROST_FORM_RESIDENT || 2 * (int64_t)ns >= nim) {
                 h->grid_res = (int)g;
                 h->res_ns = ns;

@@ -388,7 +388,8 @@ __device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned 
 // REL (the resident form): the arrival is a release reduction and the acquire
 // load that ends the wait orders what follows; otherwise a fence, an atomic
 // add, and a fence after the wait.
-template <int NCONS, bool REL = false>
+// ARRIVE = false: wait only (the resident form's end CTA, which arrived already).
+template <int NCONS, bool REL = false, bool ARRIVE = true>
 __device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target, int *s_err, KState *ks,
                                           int32_t *st_out, long long limit = WAIT_LIMIT)
 {
@@ -396,7 +397,8 @@ __device__ __forceinline__ bool grid_wait(GridBar *gb, unsigned long long target
     if (threadIdx.x == 0) {
         int ok = *s_err == 0;
         if (ok) {
-            if constexpr (REL) {
+            if constexpr (!ARRIVE) {
+            } else if constexpr (REL) {
                 red_release_add(&gb->count, 1ull);
             } else {
                 __threadfence(); // the CTA's partial values (ordered by the CTA barrier) before the arrival
@@ -1541,8 +1543,10 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     unsigned char *const sbase = reinterpret_cast<unsigned char *>(stage_smem);
     unsigned char *wstage = sbase + (size_t)warp * SC::WARP_B;
     constexpr int RES_OFF = SC::D * SC::STAGE_B + SC::RES_B; // a warp's tensor-core result
-    const ResPart rpart(prm, G, b, a.res_ns);
-    const ResSmem<K, FT, UT> rsm(sbase, prm, G, a.res_ns);
+    // resident form: CTAs [0, G - 1) own the pixels, CTA G - 1 (the end CTA)
+    // owns none and ends every frame (see the end of the frame)
+    const ResPart rpart(prm, G - 1, b, a.res_ns);
+    const ResSmem<K, FT, UT> rsm(sbase, prm, G - 1, a.res_ns);
     // the partial buffers alternate over every pass of the launch, so the
     // first pass of a frame never writes the buffer from which the last CTA
     // of the frame before is still reading the update pass's sums
@@ -1827,6 +1831,20 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         // cluster form: every CTA's partial values, then CTA 0 ends the frame
         cluster_sync_all();
         if (tid == 0) sk.last = b == 0;
+    } else if constexpr (RES) {
+        // resident form: every CTA arrives with its partial values (the
+        // FRAME_ARRIVALS count as in the grid form) and goes on; the end CTA,
+        // which streams no rows, waits for all arrivals and ends the frame
+        // while the others run the next frame's first pass
+        if (tid == 0) {
+            red_release_add(&a.bar->count, sk.proj ? 1ull : 2ull);
+            sk.last = b == G - 1;
+        }
+        if (b == G - 1) {
+            const unsigned long long fend = a.bar_base + (unsigned long long)(fr + 1) * (unsigned long long)G *
+                                                             (unsigned long long)frame_arrivals(prm.n_cg);
+            if (!grid_wait<NT, true, false>(a.bar, fend, &sk.err, a.ks, a.status_out)) return;
+        }
     } else if (tid == 0) {
         // every CTA arrives FRAME_ARRIVALS(n_cg) times per frame: once per
         // residual pass, once at the projection barrier (counted here when that
@@ -2028,7 +2046,8 @@ template <int K, typename UT> struct FrameOps {
                 cudaFuncGetAttributes(&fa, k_frame_res<K, FT, UT>) != cudaSuccess)
                 return 0;
             const int64_t cap = ((int64_t)optin - (int64_t)fa.sharedSizeBytes) & ~(int64_t)15;
-            const int npm = res_npair_max(P, grid);
+            if (grid < 2) return 0;
+            const int npm = res_npair_max(P, grid - 1); // grid - 1 CTAs own the pixels
             const int64_t nim = (int64_t)C * npm;
             const int64_t fixed = (int64_t)res_smem_bytes<K, FT, UT>(C, npm, 0);
             const int64_t slot = (int64_t)K * sizeof(typename RPair<UT>::T);

@@ -597,7 +597,10 @@ assert "return (P + RES_UNIT - 1) / RES_UNIT;" in DEVICE_H
 assert "return (int)((res_units(P) + G - 1) / G) * (RES_UNIT / 2);" in DEVICE_H
 assert "const int64_t lo = nu * b / G, hi = nu * (b + 1) / G;" in FRAME_CUH
 assert "ng = nitems > ns ? nitems - ns : 0;" in FRAME_CUH
-assert "if (g > res_units(dp.P)) g = res_units(dp.P);" in API_CU
+assert "if (g > res_units(dp.P) + 1) g = res_units(dp.P) + 1;" in API_CU
+# CTAs [0, G - 1) own the pixels; the end CTA G - 1 owns none
+assert "const ResPart rpart(prm, G - 1, b, a.res_ns);" in FRAME_CUH
+assert "const int npm = res_npair_max(P, grid - 1);" in FRAME_CUH
 # the partial buffers: two per launch, and in the resident form RES_NREP copies
 # of each pass's partial values (CTA b writes every copy, reads copy b % RES_NREP)
 RES_NREP = _const(DEVICE_H, r"constexpr int RES_NREP = (\d+);")
@@ -636,8 +639,10 @@ assert "if (g > RES_MAX_GRID) g = RES_MAX_GRID;" in API_CU
 
 def res_plan(P, C, k, usz, fsz, cap):
     """Grid, row slots and dynamic shared memory as FrameOps::res_plan_t sizes them."""
-    G = min(SMS, res_units(P), RED_SCR // partial_row(k) * RED_ROWS, 128 * RES_CPL)
-    npm = res_npair_max(P, G)
+    G = min(SMS, res_units(P) + 1, RED_SCR // partial_row(k) * RED_ROWS, 128 * RES_CPL)
+    if G < 2:
+        return None
+    npm = res_npair_max(P, G - 1)
     fixed = al16(C * npm * 2 * fsz) + al16(npm * 2)
     if cap <= fixed:
         return None
@@ -664,8 +669,10 @@ def test_resident_plan_covers_every_entry_once_inside_its_buffers(P, C, k, usz, 
     seen = np.zeros((C, P), dtype=np.int32)
     nt = threads(k, usz == 2)
     for b in range(G):
-        pa, npair, nitems, ng = res_part(P, C, G, b, ns)
+        pa, npair, nitems, ng = res_part(P, C, G - 1, b, ns)
         assert npair <= npm and nitems <= C * npm
+        if b == G - 1:
+            assert nitems == 0  # the end CTA streams no rows
         if nitems == 0:
             continue
         assert pa % 2 == 0
