@@ -59,7 +59,7 @@ def parse():
                     help="run only the passes-form study (640x480 RGB, k = 16, 24, 32) and print its JSON")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the bfloat16 against float32 storage study")
-    ap.add_argument("--frames-per-call", type=int, default=8,
+    ap.add_argument("--frames-per-call", type=int, default=16,
                     help="frames of one stream per prost_step_many call in the timed region (1: one "
                          "prost_step per frame)")
     return ap.parse_args()

@@ -29,7 +29,7 @@ constexpr int KREG = 10;
 // RES_UNIT pixels (every CTA takes all channels of its pixels).
 constexpr int RES_UNIT = 64;
 // copies of each CTA's partial values per residual pass in the resident form
-constexpr int RES_NREP = 8;
+constexpr int RES_NREP = 2;
 // its cross-CTA sums (reduce_cols_warp): values per warp of a 512-thread CTA
 // (the largest partial row, k = 10: 10 + 55 + 3 = 68 <= 5 * 16) and 16-byte
 // chunks per lane (grids of at most RES_MAX_GRID = 4 * 32 * RES_CPL CTAs)

@@ -1538,7 +1538,11 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         return;
     }
 
+    // CTA 0 stamps the trace; the statistics of the k-space steps (FP64
+    // conversions and stores) come from CTA 0, or in the resident form from
+    // the end CTA, which streams no rows and so waits at every barrier anyway
     const bool stats = b == 0;
+    const bool kstats = RES ? b == G - 1 : stats;
     using SC = StageCfg<K, FT, UT>;
     unsigned char *const sbase = reinterpret_cast<unsigned char *>(stage_smem);
     unsigned char *wstage = sbase + (size_t)warp * SC::WARP_B;
@@ -1617,7 +1621,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             else
                 reduce_cols<NT>(cols, G, cs, F::NVR, tot, rscr);
             if (trace) a.ks->sub_ts[3] = global_ns();
-            if (warp == 0) kspace_cg<K, true, RES>(sk, prm, tot, pass, a.ks, stats);
+            if (warp == 0) kspace_cg<K, true, RES>(sk, prm, tot, pass, a.ks, kstats);
             if (trace) a.ks->sub_ts[4] = global_ns();
         } else {
             float acc[F::NPF];
@@ -1646,7 +1650,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 reduce_cols_warp<NT, RES_VPW, RES_CPL>(cols, G, cs, F::NVF, tot);
             else
                 reduce_cols<NT>(cols, G, cs, F::NVF, tot, rscr);
-            if (warp == 0) kspace_cg<K, false>(sk, prm, tot, pass, a.ks, stats);
+            if (warp == 0) kspace_cg<K, false>(sk, prm, tot, pass, a.ks, kstats);
         }
         cons_sync<NT>();
         if (stats && tid == 0) a.ks->phase_ts[pass + 1] = global_ns();
@@ -1672,7 +1676,7 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
             reduce_cols_warp<NT, RES_VPW, RES_CPL>(pcols, G, a.col_stride, 1, tot);
         else
             reduce_cols<NT>(pcols, G, a.col_stride, 1, tot, rscr);
-        if (tid == 0) step_angle(sk, prm, sqrtf(fmaxf(tot[0], 0.f)), a.ks, stats);
+        if (tid == 0) step_angle(sk, prm, sqrtf(fmaxf(tot[0], 0.f)), a.ks, kstats);
         cons_sync<NT>();
         buf ^= 1;
     }
