@@ -37,7 +37,7 @@ UNIT = "frames/s"
 WORKLOAD = "rgb640x480_k10"
 FLUSH_BYTES = 256 << 20  # larger than the 126.5 MB L2
 NTR = 4  # streams advanced round-robin in the timed region (4 x 36.9 MB of subspaces > L2)
-PROFILE = os.path.join(ROOT, "profiles", "k_frame_rgb640x480_k10.md")
+PROFILE = os.path.join(ROOT, "profiles", "k_frame_res_rgb640x480_k10.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_1302_2073_gb300", "csrc", "prost_frame.cuh")
 
 
@@ -188,11 +188,15 @@ def profiled_traffic():
     return profiled_value("dram_bytes_per_launch_full_size")
 
 
+PROFILED_FRAMES_PER_CALL = 16  # the captured launch advanced a stream by 16 frames
+
+
 def is_profiled_case(args, k):
     """The committed summary covers the default workload's kernel only: float32
-    storage at the workload's own k."""
+    storage at the workload's own k, 16 frames per call."""
     import synth
-    return args.workload == WORKLOAD and args.u_dtype == "f32" and k == synth.WORKLOADS[WORKLOAD]["video"]["k"]
+    return (args.workload == WORKLOAD and args.u_dtype == "f32" and k == synth.WORKLOADS[WORKLOAD]["video"]["k"]
+            and getattr(args, "frames_per_call", PROFILED_FRAMES_PER_CALL) == PROFILED_FRAMES_PER_CALL)
 
 
 def l2_roofline(achieved, profiled, copy_gbs=None):

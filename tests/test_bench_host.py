@@ -59,6 +59,9 @@ def test_profiled_case_is_the_default_workload_in_float32_only():
     assert not bench.is_profiled_case(A(workload=bench.WORKLOAD, u_dtype="bf16"), 10)
     assert not bench.is_profiled_case(A(workload=bench.WORKLOAD, u_dtype="f32"), 12)
     assert not bench.is_profiled_case(A(workload="rgb1920x1080_k15", u_dtype="f32"), 15)
+    # the capture advanced a stream by 16 frames per launch
+    assert bench.is_profiled_case(A(workload=bench.WORKLOAD, u_dtype="f32", frames_per_call=16), 10)
+    assert not bench.is_profiled_case(A(workload=bench.WORKLOAD, u_dtype="f32", frames_per_call=1), 10)
 
 
 def test_l2_roofline_arithmetic():
@@ -66,7 +69,7 @@ def test_l2_roofline_arithmetic():
     assert r["bound"] == "l2" and r["unit"] == "GB/s"
     assert r["frac"] == pytest.approx(2746.0 / r["peak"])
     # slices x sectors/cycle x bytes/sector x L2 clock, from the capture
-    assert r["peak"] == pytest.approx(188 * 3 * 32 * 2.001746, rel=1e-4)
+    assert r["peak"] == pytest.approx(188 * 3 * 32 * 2.011017, rel=1e-4)
     assert "measured_copy_gbs" not in r
     m = bench.l2_roofline(2746.0, True, 20000.0)
     assert m["measured_copy_gbs"] == 20000.0 and m["frac_of_measured_copy"] == pytest.approx(2746.0 / 20000.0)
