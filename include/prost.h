@@ -223,6 +223,23 @@ int prost_step_many(prost_handle *h, const void *frames, int32_t n, int on_devic
 int prost_step_async(prost_handle *h, const void *frame, uint8_t *mask_out, float *background_out);
 int prost_wait(prost_handle *h);
 
+/* Pipelined host calls of n frames (not in the paper): prost_step_many() as a
+ * prost_step_async() call.  frames: n * m host entries, one frame after
+ * another; masks_out (nullable): n * P host bytes.  The frames are copied in
+ * on the handle's copy stream while the previous call's kernels run, the
+ * frames run as prost_step_many() runs them (one launch per rebase period in
+ * the resident form), and the masks are copied out while the next call's
+ * kernels run.  Each call takes one of the two slots that prost_step_async()
+ * uses (at most two calls of either kind in flight), and prost_wait() returns
+ * the status of its last frame; a rejected frame before it is reported by
+ * prost_sync().  The handle keeps device room for the largest n seen per slot
+ * (allocated on demand; growing a slot first waits for the call that used it
+ * two calls before).  Buffers stay owned by the caller and must stay valid,
+ * frames unchanged, until prost_wait() has returned the call; page-locked
+ * memory lets the copies overlap the kernels.  Errors: PROST_EINVAL (NULL
+ * handle or frames, n < 1, two calls in flight), PROST_ENOMEM, PROST_ECUDA. */
+int prost_step_many_async(prost_handle *h, const void *frames, int32_t n, uint8_t *masks_out);
+
 /* Synchronise the handle's stream.  Returns PROST_EBADFRAME if a frame was
  * skipped since the previous prost_sync(), PROST_ENOTSPD / PROST_ETIMEOUT if
  * one of those was raised, else PROST_OK, and clears these flags. */

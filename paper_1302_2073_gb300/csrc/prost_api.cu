@@ -52,6 +52,9 @@ struct prost_handle {
     cudaStream_t s_in, s_out;     // host-to-device and device-to-host copy streams
     void *af_buf[2];
     uint8_t *am_buf[2];
+    void *mf_buf[2];              // prost_step_many_async: each slot's frames and masks,
+    uint8_t *mm_buf[2];           // room for mcap[slot] frames (grown on demand)
+    int32_t mcap[2];
     float *ab_buf[2];
     int32_t *ast_dev;             // 2 device status words
     int32_t *ast_host;            // 2 pinned status words
@@ -206,6 +209,9 @@ void free_state(prost_handle *h)
     for (int i = 0; i < 2; ++i) {
         if (h->af_buf[i]) cudaFree(h->af_buf[i]);
         if (h->am_buf[i]) cudaFree(h->am_buf[i]);
+        if (h->mf_buf[i]) cudaFree(h->mf_buf[i]);
+        if (h->mm_buf[i]) cudaFree(h->mm_buf[i]);
+        h->mf_buf[i] = nullptr; h->mm_buf[i] = nullptr; h->mcap[i] = 0;
         if (h->ab_buf[i]) cudaFree(h->ab_buf[i]);
         if (h->ev_in[i]) cudaEventDestroy(h->ev_in[i]);
         if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
@@ -632,6 +638,87 @@ int prost_step_many(prost_handle *h, const void *frames, int32_t n, int on_devic
     return st;
 }
 
+namespace {
+
+// The copy streams, events, status words and one-frame buffers of the
+// pipelined host calls (created by the first such call on a handle).
+int async_setup(prost_handle *h)
+{
+    if (h->s_in) return PROST_OK;
+    const DevParams &dp = h->dp;
+    const size_t eb = frame_elem_bytes(h->prm);
+    CK(h, cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
+    CK(h, cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
+    CK(h, cudaMalloc(&h->ast_dev, 2 * sizeof(int32_t)));
+    CK(h, cudaMallocHost(&h->ast_host, 2 * sizeof(int32_t)));
+    for (int i = 0; i < 2; ++i) {
+        CK(h, cudaMalloc(&h->af_buf[i], (size_t)dp.C * dp.Pp * eb));
+        CK(h, cudaMalloc(&h->am_buf[i], (size_t)dp.Pp));
+        CK(h, cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming));
+    }
+    return PROST_OK;
+}
+
+} // namespace
+
+int prost_step_many_async(prost_handle *h, const void *frames, int32_t n, uint8_t *masks_out)
+{
+    if (!h) return PROST_EINVAL;
+    if (!frames) return fail(h, PROST_EINVAL, "frames is NULL");
+    if (n < 1) return fail(h, PROST_EINVAL, "n must be at least 1");
+    if (h->a_count >= 2) return fail(h, PROST_EINVAL, "two calls in flight: call prost_wait first");
+    DeviceGuard dg(h->device);
+    const DevParams &dp = h->dp;
+    const size_t eb = frame_elem_bytes(h->prm);
+    int rc = async_setup(h);
+    if (rc) return rc;
+    const int slot = (h->a_head + h->a_count) & 1;
+    if (n > h->mcap[slot]) {
+        // the slot's earlier call (two calls ago) must be done with its buffers
+        if (h->a_used[slot]) CK(h, cudaEventSynchronize(h->ev_out[slot]));
+        if (h->mf_buf[slot]) CK(h, cudaFree(h->mf_buf[slot]));
+        if (h->mm_buf[slot]) CK(h, cudaFree(h->mm_buf[slot]));
+        h->mf_buf[slot] = nullptr;
+        h->mm_buf[slot] = nullptr;
+        h->mcap[slot] = 0;
+        CK(h, cudaMalloc(&h->mf_buf[slot], (size_t)n * dp.C * dp.Pp * eb));
+        CK(h, cudaMalloc(&h->mm_buf[slot], (size_t)n * dp.P));
+        h->mcap[slot] = n;
+    }
+    // as prost_step_async: the copy in waits for the slot's previous kernel,
+    // the kernel for the copy in and for the slot's previous copies out
+    if (h->a_used[slot]) CK(h, cudaStreamWaitEvent(h->s_in, h->ev_done[slot], 0));
+    CK(h, cudaMemcpy2DAsync(h->mf_buf[slot], (size_t)dp.Pp * eb, frames, (size_t)dp.P * eb, (size_t)dp.P * eb,
+                            (size_t)n * dp.C, cudaMemcpyHostToDevice, h->s_in));
+    CK(h, cudaEventRecord(h->ev_in[slot], h->s_in));
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_in[slot], 0));
+    if (h->a_used[slot]) CK(h, cudaStreamWaitEvent(h->stream, h->ev_out[slot], 0));
+    const int64_t stride = (int64_t)dp.C * dp.Pp;
+    for (int32_t i0 = 0; i0 < n;) {
+        int32_t run = 1;
+        if (h->grid_res > 0) { // the resident form: the frames of each rebase period in one launch
+            run = n - i0;
+            const int64_t left = (int64_t)REBASE_EVERY - (int64_t)h->steps_since_rebase;
+            if (left >= 1 && run > left) run = (int32_t)left;
+        }
+        rc = launch_frame(h, static_cast<char *>(h->mf_buf[slot]) + (size_t)i0 * stride * eb, dp.Pp,
+                          h->mm_buf[slot] + (size_t)i0 * dp.P, nullptr, h->ast_dev + slot, run, stride);
+        if (rc) return rc;
+        i0 += run;
+    }
+    CK(h, cudaEventRecord(h->ev_done[slot], h->stream));
+    CK(h, cudaStreamWaitEvent(h->s_out, h->ev_done[slot], 0));
+    if (masks_out)
+        CK(h, cudaMemcpyAsync(masks_out, h->mm_buf[slot], (size_t)n * dp.P, cudaMemcpyDeviceToHost, h->s_out));
+    CK(h, cudaMemcpyAsync(h->ast_host + slot, h->ast_dev + slot, sizeof(int32_t), cudaMemcpyDeviceToHost, h->s_out));
+    CK(h, cudaEventRecord(h->ev_out[slot], h->s_out));
+    h->a_used[slot] = 1;
+    h->a_count += 1;
+    return PROST_OK;
+}
+
 int prost_step_async(prost_handle *h, const void *frame, uint8_t *mask_out, float *background_out)
 {
     if (!h) return PROST_EINVAL;
@@ -641,18 +728,9 @@ int prost_step_async(prost_handle *h, const void *frame, uint8_t *mask_out, floa
     const DevParams &dp = h->dp;
     const int64_t m = m_of(h->prm);
     const size_t eb = frame_elem_bytes(h->prm);
-    if (!h->s_in) {
-        CK(h, cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking));
-        CK(h, cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking));
-        CK(h, cudaMalloc(&h->ast_dev, 2 * sizeof(int32_t)));
-        CK(h, cudaMallocHost(&h->ast_host, 2 * sizeof(int32_t)));
-        for (int i = 0; i < 2; ++i) {
-            CK(h, cudaMalloc(&h->af_buf[i], (size_t)dp.C * dp.Pp * eb));
-            CK(h, cudaMalloc(&h->am_buf[i], (size_t)dp.Pp));
-            CK(h, cudaEventCreateWithFlags(&h->ev_in[i], cudaEventDisableTiming));
-            CK(h, cudaEventCreateWithFlags(&h->ev_done[i], cudaEventDisableTiming));
-            CK(h, cudaEventCreateWithFlags(&h->ev_out[i], cudaEventDisableTiming));
-        }
+    {
+        const int rs = async_setup(h);
+        if (rs) return rs;
     }
     const int slot = (h->a_head + h->a_count) & 1;
     if (background_out && !h->ab_buf[slot]) CK(h, cudaMalloc(&h->ab_buf[slot], (size_t)m * sizeof(float)));
@@ -684,7 +762,7 @@ int prost_step_async(prost_handle *h, const void *frame, uint8_t *mask_out, floa
 int prost_wait(prost_handle *h)
 {
     if (!h) return PROST_EINVAL;
-    if (h->a_count == 0) return fail(h, PROST_EINVAL, "no frame of prost_step_async in flight");
+    if (h->a_count == 0) return fail(h, PROST_EINVAL, "no call of prost_step_async or prost_step_many_async in flight");
     DeviceGuard dg(h->device);
     const int slot = h->a_head;
     CK(h, cudaEventSynchronize(h->ev_out[slot]));

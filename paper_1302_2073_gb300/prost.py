@@ -69,6 +69,7 @@ def lib():
         L.prost_init.argtypes = [P(prost_params), vp, P(vp)]
         L.prost_step.argtypes = [vp, vp, C.c_int, vp, vp]
         L.prost_step_many.argtypes = [vp, vp, C.c_int32, C.c_int, vp]
+        L.prost_step_many_async.argtypes = [vp, vp, C.c_int32, vp]
         L.prost_sync.argtypes = [vp]
         L.prost_step_async.argtypes = [vp, vp, vp, vp]
         L.prost_wait.argtypes = [vp]
@@ -248,6 +249,16 @@ def prost_step_async(h, frame, mask_out=None, background_out=None):
         if b is not None and _is_torch(b) and b.is_cuda:
             raise ProstError(PROST_EINVAL, "prost_step_async takes host buffers")
     return _check(lib().prost_step_async(h, _ptr(frame), _ptr(mask_out), _ptr(background_out)), h)
+
+
+def prost_step_many_async(h, frames, n, masks_out=None):
+    """Enqueue n host frames (numpy arrays or CPU tensors, page-locked for
+    overlap) as one pipelined call and return at once; prost_wait returns
+    the call's last frame's status."""
+    for b in (frames, masks_out):
+        if b is not None and _is_torch(b) and b.is_cuda:
+            raise ProstError(PROST_EINVAL, "prost_step_many_async takes host buffers")
+    return _check(lib().prost_step_many_async(h, _ptr(frames), int(n), _ptr(masks_out)), h)
 
 
 def prost_wait(h):

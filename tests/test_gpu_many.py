@@ -174,3 +174,49 @@ def test_other_forms_run_one_launch_per_frame():
     finally:
         pg.prost_destroy(a)
         pg.prost_destroy(b)
+
+
+@pytest.mark.parametrize("form", [pg.PROST_FORM_RESIDENT, pg.PROST_FORM_GRID])
+def test_pipelined_many_frame_calls_equal_the_synchronous_calls(form):
+    """prost_step_many_async with page-locked host frames, two calls in flight
+    and growing call sizes, against prost_step_many on the same frames: masks,
+    subspace, coefficients and statistics bit for bit, statuses in order."""
+    vid, wp = synth.make_workload("rgb640x480_k10", width=160, height=120, n_frames=14)
+    a = pg.prost_init(gpu_params(wp, form=form, seed=7))
+    b = pg.prost_init(gpu_params(wp, form=form, seed=7))
+    try:
+        host = torch.from_numpy(np.ascontiguousarray(vid.frames(0, 14))).pin_memory()
+        sizes = [2, 4, 4, 3, 1]  # 14 frames; the slots grow from 2 to 4
+        outs, starts = [], []
+        f0 = 0
+        for i, n in enumerate(sizes):
+            mo = torch.empty((n, vid.P), dtype=torch.uint8).pin_memory()
+            outs.append(mo)
+            starts.append(f0)
+            assert pg.prost_step_many_async(a, host[f0:f0 + n], n, mo) == pg.PROST_OK
+            if i >= 1:
+                assert pg.prost_wait(a) == pg.PROST_OK
+            f0 += n
+        assert pg.prost_wait(a) == pg.PROST_OK
+        with pytest.raises(pg.ProstError):
+            pg.prost_wait(a)
+        ref = np.empty((14, vid.P), np.uint8)
+        f0 = 0
+        for n in sizes:
+            assert pg.prost_step_many(b, host[f0:f0 + n].numpy(), n, ref[f0:f0 + n]) == pg.PROST_OK
+            f0 += n
+        for mo, s0, n in zip(outs, starts, sizes):
+            assert np.array_equal(mo.numpy(), ref[s0:s0 + n])
+        assert pg.prost_sync(a) == pg.PROST_OK and pg.prost_sync(b) == pg.PROST_OK
+        _compare(a, b, vid.m, vid.k)
+        # a third call while two are in flight is refused
+        m1 = torch.empty((2, vid.P), dtype=torch.uint8).pin_memory()
+        pg.prost_step_many_async(a, host[:2], 2, m1)
+        pg.prost_step_many_async(a, host[2:4], 2, m1)
+        with pytest.raises(pg.ProstError) as ei:
+            pg.prost_step_many_async(a, host[4:6], 2, m1)
+        assert ei.value.code == pg.PROST_EINVAL
+        assert pg.prost_wait(a) == pg.PROST_OK and pg.prost_wait(a) == pg.PROST_OK
+    finally:
+        pg.prost_destroy(a)
+        pg.prost_destroy(b)
