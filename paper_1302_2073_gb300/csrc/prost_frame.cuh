@@ -1342,12 +1342,12 @@ __device__ __forceinline__ void res_update(const FrameArgs &a, uint8_t *mask_out
     const float sc = prm.in_scale, of = prm.in_offset;
     const bool pre = prm.mask_pre != 0;
     const bool write = !sk.skip;
-    // the k-space vectors are read from shared memory at each use (broadcast
-    // loads) rather than held in registers
-    const volatile float *vy = sk.yf;
-    const volatile float *vv = sk.tv;
-    const volatile float *vg = sk.tg;
-    const volatile float *vw = sk.w;
+    // the k-space vectors, read from shared memory (broadcast loads); they do
+    // not change during the pass, so the compiler may keep them in registers
+    const float *vy = sk.yf;
+    const float *vv = sk.tv;
+    const float *vg = sk.tg;
+    const float *vw = sk.w;
     UT *U = static_cast<UT *>(a.U);
     const int C = prm.C, np = rp.npair;
     const uint32_t sr_key = pcg_hash(prm.sr_seed ^ pcg_hash((uint32_t)sk.frame_index));
