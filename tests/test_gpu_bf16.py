@@ -60,16 +60,20 @@ def test_bf16_initial_subspace_is_orthonormal(k):
     np.testing.assert_allclose(U.T.astype(np.float64) @ U, np.eye(k), atol=5e-6)
 
 
-@pytest.mark.parametrize("k", [10, 15])  # the register form (k <= 10) and the streaming form
-def test_bf16_teacher_forced_step(k):
-    vid, wp = synth.make_workload("rgb640x480_k10", width=160, height=120, n_frames=4, k=k)
+@pytest.mark.parametrize("k,w,h,form", [
+    (10, 160, 120, pg.PROST_FORM_AUTO),       # the resident form, every row in shared memory
+    (15, 160, 120, pg.PROST_FORM_AUTO),       # the streaming form
+    (10, 1280, 720, pg.PROST_FORM_RESIDENT),  # the resident form with rows streaming from L2
+])
+def test_bf16_teacher_forced_step(k, w, h, form):
+    vid, wp = synth.make_workload("rgb640x480_k10", width=w, height=h, n_frames=4, k=k)
     prm_o = oracle_params(wp)
     st = oracle.initial_state(synth.random_orthonormal(vid.m, vid.k, 21), vid.P)
     for t in range(3):
         oracle.frame_step(prm_o, st, vid.frame(t)[0])
     f, _ = vid.frame(3)
     U32, U64, y64 = matched_start(st.U, st.y)
-    h = pg.prost_init(gpu_params(wp, u_dtype="bf16"))
+    h = pg.prost_init(gpu_params(wp, u_dtype="bf16", form=form))
     try:
         pg.prost_set_subspace(h, U32, y64)
         pg.prost_set_labels(h, st.labels)

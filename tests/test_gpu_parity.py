@@ -165,6 +165,16 @@ def test_full_size_640x480_rgb_k10_in_the_benchmark_configuration(form):
     print(errs)
 
 
+@pytest.mark.parametrize("w,h,c,k", [(8, 8, 1, 3), (5, 3, 3, 2), (16, 9, 3, 10)])
+def test_resident_form_on_the_smallest_grids(w, h, c, k):
+    """One 64-pixel unit or less: one CTA owns every pixel, the end CTA none
+    (a grid of two), ragged pairs at the plane ends."""
+    vid = synth.SyntheticVideo(w, h, c, k, n_frames=3, fg_fraction=0.1, seed=70 + w, dtype="f32")
+    wp = synth.video._params(vid.m, k, "f32")
+    wp.update(width=w, height=h, channels=c, frame_dtype="f32")
+    _run_case(wp, vid, [0, 2], form=pg.PROST_FORM_RESIDENT)
+
+
 @pytest.mark.parametrize("w,h,c", [(1280, 720, 1), (1920, 1080, 3)])
 def test_resident_form_with_rows_beyond_shared_memory(w, h, c):
     """The resident form where a CTA's rows do not all fit its shared memory:
