@@ -123,6 +123,8 @@ int main(void)
     check(prost_inject_barrier_skew(NULL, 1) == PROST_EINVAL, "injection without a handle");
     check(prost_inject_wait_timeout(NULL, 0, 1000) == PROST_EINVAL, "wait injection without a handle");
     check(prost_step_async(NULL, NULL, NULL, NULL) == PROST_EINVAL, "pipelined step without a handle");
+    check(prost_step_many(NULL, NULL, 1, 1, NULL) == PROST_EINVAL, "frames of a stream without a handle");
+    check(prost_step_many_async(NULL, NULL, 1, NULL) == PROST_EINVAL, "pipelined frames without a handle");
     check(prost_wait(NULL) == PROST_EINVAL, "wait without a handle");
     check(prost_pre_get_state(NULL, NULL, NULL) == PROST_EINVAL, "pre-processor checkpoint without a handle");
     check(prost_pre_set_state(NULL, NULL, 0) == PROST_EINVAL, "pre-processor restore without a handle");
