@@ -367,6 +367,8 @@ int prost_init(const prost_params *prm, void *stream, prost_handle **out)
     if (gf > dp.npt) gf = dp.npt;  // every CTA gets at least one pixel tile
     // the cross-CTA reduction's unit sums fit its shared scratch
     if (gf > max_frame_grid((int)partial_row(prm->k))) gf = max_frame_grid((int)partial_row(prm->k));
+    // the register form's cross-CTA sums take one or two 16-byte chunks per lane
+    if (prm->k <= KREG && gf > RES_MAX_GRID) gf = RES_MAX_GRID;
     h->grid_frame = (int)(gf > 0 ? gf : 1);
     h->grid_gram = grid_of(ops->gram_occupancy(), h->num_sms, (int64_t)dp.C * dp.npt * (TILE_P / ops->vw));
     // the cluster form for small subspaces: one cluster of up to 16 CTAs (a
@@ -1239,6 +1241,8 @@ int plan_ctas(prost_batch *b)
             prost_handle *h = b->h[b->order[g.first + i]];
             w[i] = pow((double)h->dp.C * (double)h->dp.P, (double)b->alpha);
             cap[i] = h->dp.npt;
+            // the register form's cross-CTA sums cover at most RES_MAX_GRID CTAs
+            if (h->prm.k <= KREG && cap[i] > RES_MAX_GRID) cap[i] = RES_MAX_GRID;
         }
         if (prost_batch_split(budget, g.count, w.data(), cap.data(), n.data()) != PROST_OK)
             return bfail(b, PROST_EINVAL, "CTA split");

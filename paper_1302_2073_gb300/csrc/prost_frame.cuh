@@ -304,6 +304,14 @@ __device__ __noinline__ void reduce_cols_warp(const float *cols, int nrows, int 
     cons_sync<NT>();
 }
 
+// The same out of line: the register form's grid launches keep more live
+// values around their sums than the resident form, which inlines them.
+template <int NT, int VPW, int CPL>
+__device__ __noinline__ void reduce_cols_warp_call(const float *cols, int nrows, int cstride, int nv, float *tot)
+{
+    reduce_cols_warp<NT, VPW, CPL>(cols, nrows, cstride, nv, tot);
+}
+
 // CTA sum of N per-thread values (all threads), the first nv written to
 // out[i * os] (and to nrep - 1 more copies, rstride floats apart).  The grid
 // barrier that follows orders these stores before its arrival (CTA barrier,
@@ -1497,6 +1505,16 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     extern __shared__ __align__(128) float stage_smem[]; // streaming and resident forms only
     static_assert(!(RES && (F::STREAM || CL)), "the resident form is a grid form of the register form");
     static_assert(!RES || (F::NVR <= RES_VPW * NW && F::NVU <= RES_VPW * NW), "values per warp of the sums");
+    // the register form's grid launches (k <= KREG: one stream, or a batch's
+    // streams) share the resident form's warp sums and release arrivals
+    constexpr bool WSUM = RES || (!F::STREAM && !CL);
+    auto reduce_warp_sums = [](const float *c, int nr, int st, int nv, float *t) {
+        if constexpr (RES)
+            reduce_cols_warp<NT, RES_VPW, RES_CPL>(c, nr, st, nv, t);
+        else
+            reduce_cols_warp_call<NT, RES_VPW, RES_CPL>(c, nr, st, nv, t);
+    };
+    static_assert(!WSUM || (F::NVR <= RES_VPW * NW && F::NVU <= RES_VPW * NW), "values per warp of the sums");
     __shared__ ReorthScratch<K> rs;
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -1611,13 +1629,13 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 cons_partials<F::NPR, NW>(acc, F::NVR, col, sred, cs, NREP, rstr);
             }
             if (trace) a.ks->sub_ts[1] = global_ns();
-            if (!pass_sync<CL, NT, RES>(a.bar, target + (pass + 1 == stall_at ? 1ull : 0ull), &sk.err, a.ks,
+            if (!pass_sync<CL, NT, WSUM>(a.bar, target + (pass + 1 == stall_at ? 1ull : 0ull), &sk.err, a.ks,
                                    a.status_out, pass + 1 == stall_at ? a.stall_limit : WAIT_LIMIT))
                 return;
             if (trace) a.ks->sub_ts[2] = global_ns();
             if (RES && fr > 0 && pass == 0) reload_state(sk, rs, a.ks);
-            if constexpr (RES)
-                reduce_cols_warp<NT, RES_VPW, RES_CPL>(cols, G, cs, F::NVR, tot);
+            if constexpr (WSUM)
+                reduce_warp_sums(cols, G, cs, F::NVR, tot);
             else
                 reduce_cols<NT>(cols, G, cs, F::NVR, tot, rscr);
             if (trace) a.ks->sub_ts[3] = global_ns();
@@ -1642,12 +1660,12 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
                 cons_partials_tree<F::NVF, NW>(acc, F::NVF, col, sred, cs);
             else
                 cons_partials<F::NPF, NW>(acc, F::NVF, col, sred, cs, NREP, rstr);
-            if (!pass_sync<CL, NT, RES>(a.bar, target + (pass + 1 == stall_at ? 1ull : 0ull), &sk.err, a.ks,
+            if (!pass_sync<CL, NT, WSUM>(a.bar, target + (pass + 1 == stall_at ? 1ull : 0ull), &sk.err, a.ks,
                                    a.status_out, pass + 1 == stall_at ? a.stall_limit : WAIT_LIMIT))
                 return;
             if (RES && fr > 0 && pass == 0) reload_state(sk, rs, a.ks);
-            if constexpr (RES)
-                reduce_cols_warp<NT, RES_VPW, RES_CPL>(cols, G, cs, F::NVF, tot);
+            if constexpr (WSUM)
+                reduce_warp_sums(cols, G, cs, F::NVF, tot);
             else
                 reduce_cols<NT>(cols, G, cs, F::NVF, tot, rscr);
             if (warp == 0) kspace_cg<K, false>(sk, prm, tot, pass, a.ks, kstats);
@@ -1671,9 +1689,9 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
         else
             proj_pass<K, FT, UT>(a, tl, sk, acc1[0]);
         cons_partials_tree<1, NW, 1>(acc1, 1, pbase + b, sred, a.col_stride, NREP, (size_t)F::NVR * a.col_stride);
-        if (!pass_sync<CL, NT, RES>(a.bar, target, &sk.err, a.ks, a.status_out)) return;
-        if constexpr (RES)
-            reduce_cols_warp<NT, RES_VPW, RES_CPL>(pcols, G, a.col_stride, 1, tot);
+        if (!pass_sync<CL, NT, WSUM>(a.bar, target, &sk.err, a.ks, a.status_out)) return;
+        if constexpr (WSUM)
+            reduce_warp_sums(pcols, G, a.col_stride, 1, tot);
         else
             reduce_cols<NT>(pcols, G, a.col_stride, 1, tot, rscr);
         if (tid == 0) step_angle(sk, prm, sqrtf(fmaxf(tot[0], 0.f)), a.ks, kstats);
@@ -1863,8 +1881,8 @@ __device__ __forceinline__ void frame_body(const FrameArgs &a, const int G, cons
     cons_sync<NT>();
     if (tid == 0 && stats) a.ks->sub_ts[7] = global_ns();
     if (sk.last) {
-        if constexpr (RES)
-            reduce_cols_warp<NT, RES_VPW, RES_CPL>(ucols, G, a.col_stride, F::NVU, tot);
+        if constexpr (WSUM)
+            reduce_warp_sums(ucols, G, a.col_stride, F::NVU, tot);
         else
             reduce_cols<NT>(ucols, G, a.col_stride, F::NVU, tot, rscr);
         if (tid == 0) a.ks->sub_ts[8] = global_ns();
