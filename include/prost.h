@@ -21,6 +21,9 @@
  * (Eqs. smoothlpnorm, weightedLPnorm, spcacost).  After each frame the
  * representative U is re-orthonormalised by Cholesky-QR (U <- U R^{-1},
  * y <- R y); this is not in the paper and is the identity in exact arithmetic.
+ * prost_step_many() runs the same steps for n consecutive frames of the
+ * stream (in one launch where the kernel form allows, U staying on chip
+ * between the frames) with the results of n prost_step() calls.
  *
  * Layouts.  A frame is channel-planar: channels planes of height x width
  * pixels, row-major, so entry e = c*P + q for pixel q of channel c (the colour
