@@ -726,3 +726,56 @@ def test_resident_plan_covers_every_entry_once_inside_its_buffers(P, C, k, usz, 
         top = max(base + r * nv * cs + c * cs + b for r in (0, RES_NREP - 1) for c in (0, nv - 1)
                   for b in (0, G - 1))
         assert top < floats
+
+
+# ---- the resident form's multi-frame launches --------------------------------
+
+assert "const int64_t np = prm.P - rp.pa < 2 * (int64_t)rp.npair ? prm.P - rp.pa : 2 * (int64_t)rp.npair;" in FRAME_CUH
+assert "const int nl = (int)((bytes + 127) / 128);" in FRAME_CUH
+assert "if (left >= 1 && run > left) run = (int32_t)left;" in API_CU
+
+
+@pytest.mark.parametrize("P,C", [(1, 1), (15, 3), (1073, 3), (19200, 1), (307200, 3)])
+@pytest.mark.parametrize("fsz", [1, 4])
+def test_next_frame_prefetch_stays_in_the_next_frame(P, C, fsz):
+    """res_prefetch_frame: one 128-byte line per (channel, line of the CTA's
+    pixels), each address inside the CTA's range of that plane of the next
+    frame, for planes P (direct) or Pp (staged) entries apart."""
+    G = min(SMS, res_units(P) + 1)
+    for pitch in {P, npt_of(P) * TILE_P}:
+        for b in range(G):
+            pa, npair, _, _ = res_part(P, C, G - 1, b, 0)
+            n = min(P - pa, 2 * npair)
+            if n <= 0:
+                continue
+            nl = (n * fsz + 127) // 128
+            for c in range(C):
+                lines = pa * fsz + c * pitch * fsz + 128 * np.arange(nl)
+                assert lines.min() >= (c * pitch + pa) * fsz
+                assert lines.max() < (c * pitch + pa + n) * fsz
+
+
+@pytest.mark.parametrize("since", [0, 1, 1000, 1023])
+@pytest.mark.parametrize("n", [1, 16, 25, 2049])
+def test_multi_frame_calls_split_at_the_rebase(since, n):
+    """prost_step_many / prost_step_many_async: runs of frames in one launch
+    each, none crossing the every-1,024-frames rebase; together they cover the
+    call's frames in order."""
+    rebase = _const(DEVICE_H, r"constexpr uint32_t REBASE_EVERY = (\d+);")
+    s, i0, runs = since, 0, []
+    while i0 < n:
+        run = n - i0
+        left = rebase - s
+        if left >= 1 and run > left:
+            run = left
+        runs.append((i0, run))
+        s += run
+        if s >= rebase:
+            s = 0
+        i0 += run
+    assert sum(r for _, r in runs) == n and all(r >= 1 for _, r in runs)
+    # every run ends at or before the next rebase
+    s = since
+    for _, run in runs:
+        assert s + run <= rebase
+        s = (s + run) % rebase
