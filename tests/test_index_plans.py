@@ -779,3 +779,14 @@ def test_multi_frame_calls_split_at_the_rebase(since, n):
     for _, run in runs:
         assert s + run <= rebase
         s = (s + run) % rebase
+
+
+def test_next_frame_coefficients_repeat_the_end_of_frame_fold():
+    """The resident form's CTAs form the next frame's stored-row coefficients
+    T_old y themselves, with the same FP64 operations in the same order as
+    end_frame, so that a multi-frame launch reproduces one launch per frame
+    bit for bit (the GPU test of that is tests/test_gpu_many.py)."""
+    handover = "for (int q = tid; q < K; ++q) ty = dfma(rs.Told[tid * K + q], sk.y[q], ty);"
+    fold = "for (int q = t; q < K; ++q) ty = dfma(rs.Told[t * K + q], sk.y[q], ty);"
+    assert handover in FRAME_CUH and fold in FRAME_CUH
+    assert "sk.yf[tid] = (float)ty;" in FRAME_CUH and "ks->yf[t] = (float)rs.ty[t];" in FRAME_CUH
